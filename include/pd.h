@@ -1,0 +1,187 @@
+/*
+ * pd.h -- C ABI of libpd, a GB300 (sm_103a) library for the stiffness product
+ * K u of linear bond-based peridynamics on a uniform grid, and for the static
+ * solve, the velocity-Verlet crack loop and the gradients built around it.
+ *
+ * The operator follows "A fast computational framework for the linear
+ * bond-based peridynamic model" (arXiv 2301.11828):
+ *   - the nodal force of Eq. mat:f1, f_p = sum_q mu_pq C(x_q - x_p)(u_q - u_p) lambda_q V_q,
+ *     with the micromodulus tensor of Eq. ker:e1, the constant alpha of Sec. 2.1
+ *     and the partial-volume factor of Eq. fac:e1;
+ *   - written as f = A u with A = A^ + D^e + D^f (Sec. 3.2-3.5, Sec. 4): a
+ *     Toeplitz-block-Toeplitz part A^ (TBTBT in 3D), the edge self-term D^e
+ *     (Eq. mat:se) and the broken-bond correction D^f (Eq. df).
+ * This library returns the stiffness product  K u := -A u  (symmetric positive
+ * semidefinite; -A u = b is the static problem of Eq. mat:e2).
+ *
+ * Conventions shared by every call
+ *   - Nodes sit at x = h (i + 1/2, j + 1/2[, k + 1/2]), 0-based, and are
+ *     numbered p = i + n[0] (j + n[1] k) (Sec. 3 and Sec. 4 numbering).
+ *   - A per-node vector is structure-of-arrays, component-major:
+ *     v[c * N + p], c < dim, N = n[0] n[1] (n[2]); contiguous.
+ *   - Vector arguments are DEVICE pointers owned by the caller unless the
+ *     comment says host.  The library never frees caller memory.
+ *   - Every call is ordered on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  Calls that return values to the
+ *     host (counts, statistics) synchronise that stream.
+ *   - Every call returns a pd_status; nothing aborts.  pd_last_error() holds a
+ *     message for the last failure on the calling thread.
+ *   - A pd_grid may be used by one host thread / stream at a time.
+ *   - The horizon is delta = M h with an integer M >= 1 (Eq. band gives the
+ *     neighbour set |o|^2 <= M^2 in grid offsets o).
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pd_grid pd_grid;
+
+typedef enum {
+    PD_OK = 0,
+    PD_ERR_INVALID = 1,        /* bad argument, shape, flag or state */
+    PD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    PD_ERR_OOM = 3,            /* device allocation failed */
+    PD_ERR_NOT_CONVERGED = 4,  /* iteration cap reached; outputs hold the last iterate */
+    PD_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out */
+    PD_ERR_STATE = 6           /* call not valid in the grid's current state */
+} pd_status;
+
+/* ---- flags for pd_matvec / pd_matvec_batch / pd_break_bonds ---- */
+#define PD_F32            0x1u   /* vectors are float  */
+#define PD_F64            0x2u   /* vectors are double */
+#define PD_METHOD_AUTO    0x00u  /* fastest measured method for (dim, M, dtype) */
+#define PD_METHOD_STENCIL 0x10u  /* direct neighbour sum (Eq. mat:f1), shared-memory tiled */
+#define PD_METHOD_FFT     0x20u  /* TBT part by FFT with the symbol product fused (Algorithms 3/4) */
+#define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
+#define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
+
+/* ---- modes for pd_cg_solve ---- */
+#define PD_CG_F64   0x1u  /* plain CG, FP64 vectors and FP64 matvec */
+#define PD_CG_MIXED 0x2u  /* FP32-matvec CG inside FP64 iterative refinement */
+
+typedef struct {
+    int dim;          /* 2 or 3 */
+    int M;            /* horizon in grid units */
+    int nnb;          /* number of neighbour offsets (28 for 2D M = 3) */
+    int mask_words;   /* 32-bit words per node in the bond mask */
+    int64_t n[3];     /* grid extents (n[2] = 1 in 2D) */
+    int64_t N;        /* number of nodes */
+    double h, delta, alpha;  /* spacing, horizon, micromodulus constant at the set modulus */
+    int64_t n_broken_nodes;  /* nodes with at least one broken bond (Omega_br) */
+} pd_grid_info;
+
+typedef struct {
+    int iterations;        /* total inner (matvec) iterations */
+    int outer;             /* refinement passes (1 for PD_CG_F64) */
+    int f64_matvecs;       /* FP64 operator applications */
+    double rel_residual;   /* ||P(b - K u)|| / ||P b||, FP64, recomputed at the end */
+    double seconds;        /* wall time of the solve, device-synchronised */
+} pd_cg_stats;
+
+typedef struct {
+    int64_t steps;            /* steps taken */
+    int64_t newly_broken;     /* bonds broken during the call */
+    int64_t broken_total;     /* bonds broken so far on this grid */
+} pd_step_stats;
+
+/* Creates a grid of n[0] x n[1] (x n[2]) nodes with spacing h and horizon
+ * delta = M h (Sec. 3, Sec. 4).  constrained: HOST uint8 [dim][N], nonzero
+ * marks a component in the volume-constrained set Omega_c (Sec. 3.3, and the
+ * per-component remark of Sec. 3.4); NULL = none.  Sets E = 1, rho = 1,
+ * thickness = 1, s0 = 0 (no breaking); every bond intact.
+ * Errors: PD_ERR_INVALID (dim not 2/3, n < 1, h <= 0, delta/h not an integer
+ * >= 1, M beyond the compiled maximum), PD_ERR_OOM, PD_ERR_CUDA. */
+int pd_create_grid(int dim, const int64_t n[3], double h, double delta,
+                   const uint8_t *constrained, pd_grid **out);
+
+/* Material (Sec. 2.1): E Young's modulus, rho density, thickness t (2D alpha =
+ * 9E/(pi delta^3 t), 3D alpha = 12E/(pi delta^4)), s0 critical stretch (Eq. mu;
+ * s0 <= 0 disables breaking).  E_field: DEVICE double [N] per-node modulus or
+ * NULL; with a field, bond (p,q) uses (E_p + E_q)/2 and the scalar E is
+ * ignored.  The field is copied.  Errors: PD_ERR_INVALID (E, rho, t <= 0 or a
+ * field value <= 0). */
+int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s0,
+                    const double *E_field);
+
+/* out = K u = -A u (or P K P u with PD_PROJECT), u and out DEVICE [dim][N] of
+ * the dtype in flags; u and out must not overlap.  Broken bonds are honoured
+ * unless PD_IGNORE_BROKEN.  Errors: PD_ERR_INVALID (dtype flag missing, FFT
+ * with a modulus field). */
+int pd_matvec(pd_grid *g, const void *u, void *out, uint32_t flags, void *stream);
+
+/* The same for `batch` independent vectors stored back to back:
+ * u[b * dim * N + c * N + p].  One launch serves the whole batch. */
+int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags,
+                    void *stream);
+
+/* Solves P K P u = P b (Eq. mat:e2 with h = 0 on Omega_c) by conjugate
+ * gradients.  b, u: DEVICE double [dim][N]; u is the initial guess on entry
+ * and the solution on exit (its constrained components are set to 0).
+ * mode: PD_CG_F64 or PD_CG_MIXED.  Stops when ||P(b - K u)|| <= rtol ||P b||
+ * in FP64.  stats may be NULL.  Returns PD_ERR_NOT_CONVERGED after max_iter
+ * inner iterations with u holding the last iterate and stats filled. */
+int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter,
+                uint32_t mode, pd_cg_stats *stats, void *stream);
+
+/* Velocity-Verlet (Algorithm 2) with acceleration a = (f + b)/rho, f = A(mu) u,
+ * and bond breaking (Eqs. mu, fra:s1) after each drift.  u, v: DEVICE double
+ * [dim][N], updated in place; b: DEVICE double [dim][N] or NULL.
+ * v_prescribed: DEVICE double [dim][N] or NULL: constrained components move
+ * with this velocity (u += dt v_p, v = v_p) -- the prescribed-velocity layers
+ * of Sec. 5.2.  Each call first evaluates f at the incoming u.
+ * break_step: DEVICE int32 [N * nnb] or NULL: where bond (p, k) breaks during
+ * the call its entry receives step_base + the 1-based step index (used by the
+ * adjoint to replay mu).  */
+int pd_step(pd_grid *g, double *u, double *v, const double *b, int nsteps, double dt,
+            const double *v_prescribed, int32_t *break_step, int32_t step_base,
+            pd_step_stats *stats, void *stream);
+
+/* One breaking pass: every intact bond with stretch s >= s0 (Eq. fra:s1,
+ * evaluated in FP64 as X = xi + (u_q - u_p), s = (|X| - |xi|)/|xi|, xi = h o,
+ * no contraction) is broken in both directions.  u: DEVICE [dim][N] of the
+ * dtype in flags (converted to double).  n_newly_broken: host, may be NULL. */
+int pd_break_bonds(pd_grid *g, const void *u, uint32_t flags, int64_t *n_newly_broken,
+                   void *stream);
+
+/* Breaks every bond whose segment x_p -> x_q meets the closed segment
+ * (seg[0], seg[1]) - (seg[2], seg[3]) / den, in units of h from the grid
+ * corner (2D only; the pre-notch of Sec. 5.2).  Exact integer geometry. */
+int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_broken,
+                     void *stream);
+
+/* Reads grid facts (host struct). */
+int pd_get_info(pd_grid *g, pd_grid_info *info);
+
+/* Neighbour offsets (HOST int32 [nnb][3], lexicographic (oz, oy, ox) order;
+ * offset k and nnb-1-k are opposite).  cap = rows available. */
+int pd_get_offsets(pd_grid *g, int32_t *off, int cap);
+
+/* Bond mask, DEVICE uint32 [mask_words][N]: bit (k % 32) of word k / 32 of
+ * node p is 1 while bond (p, p + o_k) is intact (out-of-grid bits are 1). */
+int pd_get_bond_mask(pd_grid *g, uint32_t *mask, void *stream);
+int pd_set_bond_mask(pd_grid *g, const uint32_t *mask, void *stream);
+
+/* Modulus gradient of a loss through a static solve (Sec. 2.1 model with the
+ * bond modulus (E_p + E_q)/2): given the solution u and the adjoint lam
+ * (P K P lam = P dL/du), grad[r] += scale * sum_{q intact} (lam_q - lam_r)^T
+ * C1(q - r) (u_q - u_r), C1 the bond block at E = 1.  u, lam: DEVICE double
+ * [dim][N]; grad: DEVICE double [N].  scale = -1/2 gives dL/dE. */
+int pd_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale,
+                    double *grad, void *stream);
+
+/* Destroys the grid and frees its device memory.  NULL is accepted. */
+int pd_destroy(pd_grid *g);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_H */

@@ -1,0 +1,453 @@
+// pd_api.cu -- grid lifecycle, operator tables and the C entry points of libpd.
+//
+// Tables built here (once per grid, FP64 on the host, then copied):
+//   - the neighbour offsets o with |o|^2 <= M^2 (Eq. band), canonical order;
+//   - the unit-modulus bond blocks c1(o) = alpha1 lambda(o) h^(d-1) o o^T / |o|^3
+//     (Eqs. ker:e1, frb:e1 in 2D, thm:e2 in 3D; lambda of Eq. fac:e1);
+//   - the diagonal-block table Kd(class) = sum over in-grid offsets of c(o), i.e.
+//     the full-horizon sum minus the edge term D^e of Eq. mat:se, for every class
+//     of clipped distances to the faces.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pd_internal.cuh"
+
+namespace pd {
+
+static thread_local std::string t_err;
+
+void set_error(const std::string &msg) { t_err = msg; }
+
+int fail(int code, const std::string &msg)
+{
+    t_err = msg;
+    return code;
+}
+
+// lambda of Eq. fac:e1 for an offset with |o|^2 = d2 (grid units, delta = M):
+// 1 when |o| <= M - 1/2 (tested exactly as 4 d2 <= (2M - 1)^2), M + 1/2 - |o| on
+// the shell M - 1/2 < |o| <= M.
+static double lambda_of(int d2, int M)
+{
+    if (4 * d2 <= (2 * M - 1) * (2 * M - 1)) return 1.0;
+    return (double)M + 0.5 - std::sqrt((double)d2);
+}
+
+static double alpha_of(int dim, double E, double delta, double thickness)
+{
+    const double pi = 3.14159265358979323846;
+    if (dim == 2) return 9.0 * E / (pi * delta * delta * delta * thickness);
+    return 12.0 * E / (pi * delta * delta * delta * delta);
+}
+
+static void build_coefs(pd_grid *g)
+{
+    const int nc = ncoef(g->dim);
+    g->alpha1 = alpha_of(g->dim, 1.0, g->delta, g->thickness);
+    g->alpha = g->alpha1 * g->E;
+    g->coef1.assign((size_t)g->nnb * nc, 0.0);
+    const double hp = (g->dim == 2) ? g->h : g->h * g->h;
+    for (int k = 0; k < g->nnb; ++k) {
+        const int32_t *o = &g->off[3 * k];
+        const int d2 = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+        const double r = std::sqrt((double)d2);
+        const double w = g->alpha1 * lambda_of(d2, g->M) * hp / (r * r * r);
+        double *c = &g->coef1[(size_t)nc * k];
+        if (g->dim == 2) {
+            c[0] = w * o[0] * o[0];
+            c[1] = w * o[0] * o[1];
+            c[2] = w * o[1] * o[1];
+        } else {
+            c[0] = w * o[0] * o[0];
+            c[1] = w * o[0] * o[1];
+            c[2] = w * o[0] * o[2];
+            c[3] = w * o[1] * o[1];
+            c[4] = w * o[1] * o[2];
+            c[5] = w * o[2] * o[2];
+        }
+    }
+}
+
+// Kd tables at the current modulus: entry index (a0, a1, b0, b1[, c0, c1]) with
+// each value the clipped distance (0..M) to the low / high face along x, y[, z].
+static int build_kd(pd_grid *g)
+{
+    const int M = g->M, B = M + 1, nc = ncoef(g->dim);
+    int64_t entries = 1;
+    for (int i = 0; i < 2 * g->dim; ++i) entries *= B;
+    std::vector<double> kd((size_t)entries * nc, 0.0);
+    for (int64_t e = 0; e < entries; ++e) {
+        int d[6] = {0, 0, 0, 0, 0, 0};
+        int64_t t = e;
+        for (int i = 2 * g->dim - 1; i >= 0; --i) {
+            d[i] = (int)(t % B);
+            t /= B;
+        }
+        for (int k = 0; k < g->nnb; ++k) {
+            const int32_t *o = &g->off[3 * k];
+            bool in = (-o[0] <= d[0]) && (o[0] <= d[1]) && (-o[1] <= d[2]) && (o[1] <= d[3]);
+            if (g->dim == 3) in = in && (-o[2] <= d[4]) && (o[2] <= d[5]);
+            if (!in) continue;
+            for (int c = 0; c < nc; ++c) kd[(size_t)e * nc + c] += g->coef1[(size_t)k * nc + c] * g->E;
+        }
+    }
+    std::vector<float> kd32(kd.begin(), kd.end());
+    if (!g->d_kd64) {
+        PD_CUDA(cudaMalloc(&g->d_kd64, kd.size() * sizeof(double)));
+        PD_CUDA(cudaMalloc(&g->d_kd32, kd.size() * sizeof(float)));
+    }
+    PD_CUDA(cudaMemcpy(g->d_kd64, kd.data(), kd.size() * sizeof(double), cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(g->d_kd32, kd32.data(), kd32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    g->kd_entries = entries;
+    return PD_OK;
+}
+
+static void free_grid(pd_grid *g)
+{
+    if (!g) return;
+    cudaFree(g->d_cons);
+    cudaFree(g->d_E);
+    cudaFree(g->d_mask);
+    cudaFree(g->d_brlist);
+    cudaFree(g->d_brflag);
+    cudaFree(g->d_count);
+    cudaFree(g->d_kd64);
+    cudaFree(g->d_kd32);
+    cudaFree(g->d_sym64);
+    cudaFree(g->d_sym32);
+    cudaFree(g->d_off);
+    cudaFree(g->d_coef);
+    cudaFree(g->d_coef1);
+    cudaFree(g->ws);
+    if (g->h_pinned) cudaFreeHost(g->h_pinned);
+    delete g;
+}
+
+static int check_grid(pd_grid *g)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    int dev = -1;
+    PD_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(PD_ERR_STATE, "current CUDA device differs from the grid's device");
+    return PD_OK;
+}
+
+// Device copies of the offsets and of the bond blocks (current modulus and unit modulus),
+// used by the sparse kernels (D^f gather, breaking, gradient).
+int upload_coefs(pd_grid *g)
+{
+    const int nc = ncoef(g->dim);
+    if (!g->d_off) {
+        PD_CUDA(cudaMalloc(&g->d_off, sizeof(int32_t) * 3 * (size_t)g->nnb));
+        PD_CUDA(cudaMalloc(&g->d_coef, sizeof(double) * nc * (size_t)g->nnb));
+        PD_CUDA(cudaMalloc(&g->d_coef1, sizeof(double) * nc * (size_t)g->nnb));
+        PD_CUDA(cudaMemcpy(g->d_off, g->off.data(), sizeof(int32_t) * 3 * (size_t)g->nnb, cudaMemcpyHostToDevice));
+    }
+    std::vector<double> cE(g->coef1);
+    for (double &v : cE) v *= g->E;
+    PD_CUDA(cudaMemcpy(g->d_coef1, g->coef1.data(), sizeof(double) * nc * (size_t)g->nnb, cudaMemcpyHostToDevice));
+    PD_CUDA(cudaMemcpy(g->d_coef, cE.data(), sizeof(double) * nc * (size_t)g->nnb, cudaMemcpyHostToDevice));
+    return PD_OK;
+}
+
+// ------------------------------------------------------------------ matvec front end
+// out = scale * K u (K = -A) for `batch` vectors; optional fused FP64 dot
+// dot_out[b] = sum_p u_p . out_p (u projected when PD_PROJECT).
+int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, cudaStream_t s,
+           double *dot_partial, double *dot_out, unsigned int *retire, double scale)
+{
+    const bool f32 = flags & PD_F32, f64 = flags & PD_F64;
+    if (f32 == f64) return fail(PD_ERR_INVALID, "exactly one of PD_F32 / PD_F64 must be set");
+    if (!u || !out) return fail(PD_ERR_INVALID, "u and out must be device pointers");
+    if (u == out) return fail(PD_ERR_INVALID, "u and out must not alias");
+    const uint32_t method = flags & (PD_METHOD_STENCIL | PD_METHOD_FFT);
+    if (method == (PD_METHOD_STENCIL | PD_METHOD_FFT)) return fail(PD_ERR_INVALID, "two methods requested");
+    const bool need_mu = !(flags & PD_IGNORE_BROKEN) && (g->broken_total > 0 || (flags & kForceMu));
+
+    MatvecArgs a{};
+    a.u = u;
+    a.out = out;
+    a.batch = batch;
+    a.project = (flags & PD_PROJECT) && g->has_cons;
+    a.scale = scale;
+
+    if (g->has_E) {
+        if (g->dim != 2) return fail(PD_ERR_INVALID, "a per-node modulus field is supported in 2D");
+        if (method == PD_METHOD_FFT)
+            return fail(PD_ERR_INVALID, "the FFT method needs a constant modulus (no field)");
+        a.use_E = true;
+        a.use_mu = need_mu;
+        a.dot_partial = dot_partial;
+        a.dot_out = dot_out;
+        a.retire = retire;
+        return launch_stencil(g, f64, a, s);
+    }
+    bool use_fft = (method == PD_METHOD_FFT);
+    if (method == 0) use_fft = (g->auto_choice[f64 ? 1 : 0] == 2);
+    if (use_fft && g->dim != 2) return fail(PD_ERR_INVALID, "the FFT method is built for 2D grids");
+    if (dot_partial && need_mu) return fail(PD_ERR_INVALID, "internal: fused dot with broken bonds");
+    a.dot_partial = dot_partial;
+    a.dot_out = dot_out;
+    a.retire = retire;
+    int rc = use_fft ? launch_fft_tile(g, f64, a, s) : launch_stencil(g, f64, a, s);
+    if (rc != PD_OK) return rc;
+    if (need_mu) return launch_df_gather(g, f64, u, out, batch, a.project, scale, s);
+    return PD_OK;
+}
+
+}  // namespace pd
+
+using namespace pd;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *pd_last_error(void) { return t_err.c_str(); }
+
+int pd_create_grid(int dim, const int64_t n[3], double h, double delta, const uint8_t *constrained,
+                   pd_grid **out)
+{
+    if (!out) return fail(PD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(PD_ERR_INVALID, "dim must be 2 or 3");
+    if (!n) return fail(PD_ERR_INVALID, "n is NULL");
+    for (int i = 0; i < dim; ++i)
+        if (n[i] < 1 || n[i] > (1 << 20)) return fail(PD_ERR_INVALID, "grid extents must be in [1, 2^20]");
+    if (!(h > 0) || !(delta > 0) || !std::isfinite(h) || !std::isfinite(delta))
+        return fail(PD_ERR_INVALID, "h and delta must be positive");
+    const double ratio = delta / h;
+    const int M = (int)std::lround(ratio);
+    if (M < 1 || std::fabs(ratio - M) > 1e-9 * std::max(1.0, ratio))
+        return fail(PD_ERR_INVALID, "delta / h must be an integer >= 1");
+    if ((dim == 2 && M > kMaxM2) || (dim == 3 && M > kMaxM3))
+        return fail(PD_ERR_INVALID, "horizon M beyond the compiled maximum (2D 8, 3D 4)");
+    const int64_t N = n[0] * n[1] * (dim == 3 ? n[2] : 1);
+    if (N > ((int64_t)1 << 31) - 1) return fail(PD_ERR_INVALID, "more than 2^31 - 1 nodes");
+
+    pd_grid *g = new (std::nothrow) pd_grid();
+    if (!g) return fail(PD_ERR_OOM, "host allocation failed");
+    g->dim = dim;
+    g->M = M;
+    g->h = h;
+    g->delta = M * h;
+    g->n[0] = n[0];
+    g->n[1] = n[1];
+    g->n[2] = (dim == 3) ? n[2] : 1;
+    g->N = N;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        delete g;
+        return fail(PD_ERR_CUDA, "no CUDA device");
+    }
+    for (int oz = (dim == 3 ? -M : 0); oz <= (dim == 3 ? M : 0); ++oz)
+        for (int oy = -M; oy <= M; ++oy)
+            for (int ox = -M; ox <= M; ++ox) {
+                const int d2 = ox * ox + oy * oy + oz * oz;
+                if (d2 == 0 || d2 > M * M) continue;
+                g->off.push_back(ox);
+                g->off.push_back(oy);
+                g->off.push_back(oz);
+            }
+    g->nnb = (int)(g->off.size() / 3);
+    g->W = (g->nnb + 31) / 32;
+    build_coefs(g);
+
+    auto bail = [&](int code, const char *msg) {
+        free_grid(g);
+        return fail(code, msg);
+    };
+    if (cudaMalloc(&g->d_mask, sizeof(uint32_t) * (size_t)g->W * N) != cudaSuccess) return bail(PD_ERR_OOM, "mask");
+    if (cudaMemset(g->d_mask, 0xff, sizeof(uint32_t) * (size_t)g->W * N) != cudaSuccess)
+        return bail(PD_ERR_CUDA, "mask init");
+    if (cudaMalloc(&g->d_brlist, sizeof(int32_t) * (size_t)N) != cudaSuccess) return bail(PD_ERR_OOM, "list");
+    if (cudaMalloc(&g->d_brflag, sizeof(uint32_t) * (size_t)N) != cudaSuccess) return bail(PD_ERR_OOM, "flags");
+    if (cudaMemset(g->d_brflag, 0, sizeof(uint32_t) * (size_t)N) != cudaSuccess) return bail(PD_ERR_CUDA, "flags");
+    if (cudaMalloc(&g->d_count, sizeof(unsigned long long) * 8) != cudaSuccess) return bail(PD_ERR_OOM, "counters");
+    if (cudaMemset(g->d_count, 0, sizeof(unsigned long long) * 8) != cudaSuccess)
+        return bail(PD_ERR_CUDA, "counters");
+    if (cudaMallocHost(&g->h_pinned, 4096) != cudaSuccess) return bail(PD_ERR_OOM, "pinned mailbox");
+    if (constrained) {
+        std::vector<uint8_t> bits((size_t)N, 0);
+        bool any = false;
+        for (int c = 0; c < dim; ++c)
+            for (int64_t p = 0; p < N; ++p)
+                if (constrained[(size_t)c * N + p]) {
+                    bits[p] |= (uint8_t)(1u << c);
+                    any = true;
+                }
+        g->has_cons = any;
+        if (cudaMalloc(&g->d_cons, (size_t)N) != cudaSuccess) return bail(PD_ERR_OOM, "constraint mask");
+        if (cudaMemcpy(g->d_cons, bits.data(), (size_t)N, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(PD_ERR_CUDA, "constraint mask copy");
+    }
+    int rc = build_kd(g);
+    if (rc == PD_OK) rc = upload_coefs(g);
+    if (rc != PD_OK) {
+        std::string m = t_err;
+        free_grid(g);
+        return fail(rc, m);
+    }
+    *out = g;
+    return PD_OK;
+}
+
+int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s0, const double *E_field)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!(E > 0) || !(rho > 0) || !(thickness > 0) || !std::isfinite(E) || !std::isfinite(rho) ||
+        !std::isfinite(thickness) || !std::isfinite(s0))
+        return fail(PD_ERR_INVALID, "E, rho and thickness must be positive and finite");
+    if (E_field && g->dim != 2) return fail(PD_ERR_INVALID, "a modulus field is supported in 2D");
+    g->E = E;
+    g->rho = rho;
+    g->thickness = thickness;
+    g->s0 = s0;
+    build_coefs(g);
+    if (E_field) {
+        if (!g->d_E) PD_CUDA(cudaMalloc(&g->d_E, sizeof(double) * (size_t)g->N));
+        PD_CUDA(cudaMemcpy(g->d_E, E_field, sizeof(double) * (size_t)g->N, cudaMemcpyDeviceToDevice));
+        std::vector<double> hE((size_t)g->N);
+        PD_CUDA(cudaMemcpy(hE.data(), g->d_E, sizeof(double) * (size_t)g->N, cudaMemcpyDeviceToHost));
+        for (double v : hE)
+            if (!(v > 0) || !std::isfinite(v)) {
+                g->has_E = false;
+                return fail(PD_ERR_INVALID, "modulus field values must be positive and finite");
+            }
+        g->has_E = true;
+    } else {
+        g->has_E = false;
+    }
+    rc = build_kd(g);
+    if (rc) return rc;
+    rc = upload_coefs(g);
+    if (rc) return rc;
+    g->auto_choice[0] = g->auto_choice[1] = 0;
+    if (g->d_sym32) return fft_prepare(g);
+    return PD_OK;
+}
+
+int pd_matvec(pd_grid *g, const void *u, void *out, uint32_t flags, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    return matvec(g, 1, u, out, flags, (cudaStream_t)stream);
+}
+
+int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (batch < 1) return fail(PD_ERR_INVALID, "batch must be >= 1");
+    return matvec(g, batch, u, out, flags, (cudaStream_t)stream);
+}
+
+int pd_get_info(pd_grid *g, pd_grid_info *info)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!info) return fail(PD_ERR_INVALID, "info is NULL");
+    info->dim = g->dim;
+    info->M = g->M;
+    info->nnb = g->nnb;
+    info->mask_words = g->W;
+    for (int i = 0; i < 3; ++i) info->n[i] = g->n[i];
+    info->N = g->N;
+    info->h = g->h;
+    info->delta = g->delta;
+    info->alpha = g->alpha;
+    unsigned long long cnt = 0;
+    PD_CUDA(cudaMemcpy(&cnt, g->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
+    info->n_broken_nodes = (int64_t)cnt;
+    return PD_OK;
+}
+
+int pd_get_offsets(pd_grid *g, int32_t *off, int cap)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (!off || cap < g->nnb) return fail(PD_ERR_INVALID, "offset buffer too small");
+    std::memcpy(off, g->off.data(), sizeof(int32_t) * 3 * (size_t)g->nnb);
+    return PD_OK;
+}
+
+int pd_get_bond_mask(pd_grid *g, uint32_t *mask, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!mask) return fail(PD_ERR_INVALID, "mask is NULL");
+    PD_CUDA(cudaMemcpyAsync(mask, g->d_mask, sizeof(uint32_t) * (size_t)g->W * g->N, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    return PD_OK;
+}
+
+int pd_set_bond_mask(pd_grid *g, const uint32_t *mask, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!mask) return fail(PD_ERR_INVALID, "mask is NULL");
+    PD_CUDA(cudaMemcpyAsync(g->d_mask, mask, sizeof(uint32_t) * (size_t)g->W * g->N, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    return refresh_broken_nodes(g, (cudaStream_t)stream);
+}
+
+int pd_break_bonds(pd_grid *g, const void *u, uint32_t flags, int64_t *n_newly_broken, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    const bool f32 = flags & PD_F32, f64 = flags & PD_F64;
+    if (f32 == f64) return fail(PD_ERR_INVALID, "exactly one of PD_F32 / PD_F64 must be set");
+    if (!u) return fail(PD_ERR_INVALID, "u is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    PD_CUDA(cudaMemsetAsync(g->d_count + 2, 0, sizeof(unsigned long long), s));
+    rc = launch_break(g, u, f64, nullptr, 0, s);
+    if (rc) return rc;
+    PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    g->broken_total = (int64_t)g->h_pinned[1];
+    if (n_newly_broken) *n_newly_broken = (int64_t)g->h_pinned[2];
+    return PD_OK;
+}
+
+int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_broken, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (g->dim != 2) return fail(PD_ERR_INVALID, "segments are supported in 2D");
+    if (!seg || den < 1) return fail(PD_ERR_INVALID, "bad segment");
+    const int64_t lim = (int64_t)1 << 28;
+    for (int i = 0; i < 4; ++i)
+        if (seg[i] < -lim || seg[i] > lim) return fail(PD_ERR_INVALID, "segment coordinates out of range");
+    if (den * (2 * std::max(g->n[0], g->n[1]) + 1) > lim)
+        return fail(PD_ERR_INVALID, "segment denominator too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    PD_CUDA(cudaMemsetAsync(g->d_count + 2, 0, sizeof(unsigned long long), s));
+    rc = launch_break_segment(g, seg, den, s);
+    if (rc) return rc;
+    PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    g->broken_total = (int64_t)g->h_pinned[1];
+    if (n_broken) *n_broken = (int64_t)g->h_pinned[2];
+    return PD_OK;
+}
+
+int pd_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale, double *grad, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!u || !lam || !grad) return fail(PD_ERR_INVALID, "NULL vector");
+    return launch_grad_modulus(g, u, lam, scale, grad, (cudaStream_t)stream);
+}
+
+int pd_destroy(pd_grid *g)
+{
+    if (!g) return PD_OK;
+    free_grid(g);
+    return PD_OK;
+}
+
+}  // extern "C"

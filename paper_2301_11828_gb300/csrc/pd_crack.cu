@@ -1,0 +1,438 @@
+// pd_crack.cu -- broken bonds and the explicit dynamic loop.
+//
+//   * D^f gather (Eqs. df, tea:fr): for every node of Omega_br, one warp walks
+//     the node's bond mask and removes the terms of its broken bonds from K u:
+//         (K u)_p -= scale * sum_{q in v_p} c(q - p) (u_p - u_q).
+//     The node list and its length live on the device, so the launch needs no
+//     host round trip; an empty list costs one tiny launch.
+//   * Breaking (Eqs. mu, fra:s1): one thread per node tests the bonds to nodes
+//     with a larger index (offsets of the upper half of the canonical list), in
+//     FP64 with explicitly rounded operations (no contraction), and clears the
+//     bit at both ends.  Broken bonds never heal.
+//   * Pre-notch: bonds whose segment meets a given segment, exact integers.
+//   * Velocity-Verlet (Algorithm 2) with a = (f + b) / rho.
+//   * Modulus gradient: bond sum of (lam_q - lam_r)^T C1 (u_q - u_r).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "pd_internal.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr int kBlk = 256;
+
+__device__ __forceinline__ void node_coords(int64_t p, int nx, int ny, int &i, int &j, int &k)
+{
+    i = (int)(p % nx);
+    j = (int)((p / nx) % ny);
+    k = (int)(p / ((int64_t)nx * ny));
+}
+
+__device__ __forceinline__ void mark_broken_node(int64_t x, uint32_t *brflag, int32_t *brlist,
+                                                 unsigned long long *count)
+{
+    if (atomicExch(&brflag[x], 1u) == 0u) {
+        const unsigned long long idx = atomicAdd(&count[0], 1ull);
+        brlist[idx] = (int32_t)x;
+    }
+}
+
+// ------------------------------------------------------------------ D^f gather
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kBlk)
+k_df_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int ny, int nz, int nnb,
+            const int32_t *__restrict__ brlist, const unsigned long long *__restrict__ count,
+            const uint32_t *__restrict__ mask, const int32_t *__restrict__ off, const double *__restrict__ coef,
+            const uint8_t *__restrict__ cons, int project, double scale, int64_t batch)
+{
+    const int64_t cnt = (int64_t)*count;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp; w < cnt * batch; w += nwarps) {
+        const int64_t b = w / cnt;
+        const int64_t p = brlist[w - b * cnt];
+        const T *ub = u + b * DIM * N;
+        T *ob = out + b * DIM * N;
+        int i, j, k;
+        node_coords(p, nx, ny, i, j, k);
+        const uint8_t cm = project ? cons[p] : 0;
+        double up[DIM], acc[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+            up[c] = ((cm >> c) & 1) ? 0.0 : (double)ub[c * N + p];
+            acc[c] = 0.0;
+        }
+        for (int kk = lane; kk < nnb; kk += 32) {
+            const uint32_t word = mask[(int64_t)(kk >> 5) * N + p];
+            if ((word >> (kk & 31)) & 1u) continue;
+            const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1], qk = k + off[3 * kk + 2];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
+            const int64_t q = ((int64_t)qk * ny + qj) * nx + qi;
+            const uint8_t qm = project ? cons[q] : 0;
+            double d[DIM];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) d[c] = up[c] - (((qm >> c) & 1) ? 0.0 : (double)ub[c * N + q]);
+            if (DIM == 2) {
+                const double *cf = coef + 3 * kk;
+                acc[0] += cf[0] * d[0] + cf[1] * d[1];
+                acc[1] += cf[1] * d[0] + cf[2] * d[DIM - 1];
+            } else {
+                const double *cf = coef + 6 * kk;
+                acc[0] += cf[0] * d[0] + cf[1] * d[1] + cf[2] * d[DIM - 1];
+                acc[1] += cf[1] * d[0] + cf[3] * d[1] + cf[4] * d[DIM - 1];
+                acc[DIM - 1] += cf[2] * d[0] + cf[4] * d[1] + cf[5] * d[DIM - 1];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < DIM; ++c)
+                if (!((cm >> c) & 1)) ob[c * N + p] = (T)((double)ob[c * N + p] - scale * acc[c]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ breaking
+template <int DIM, typename TU>
+__global__ void __launch_bounds__(kBlk)
+k_break(const TU *__restrict__ u, int64_t N, int nx, int ny, int nz, int nnb, const int32_t *__restrict__ off,
+        uint32_t *mask, double h, double s0, int32_t *break_step, int32_t step_id, uint32_t *brflag,
+        int32_t *brlist, unsigned long long *count)
+{
+    unsigned long long newly = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        node_coords(p, nx, ny, i, j, k);
+        double up[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) up[c] = (double)u[c * N + p];
+        for (int kk = nnb / 2; kk < nnb; ++kk) {
+            uint32_t *wp = mask + (int64_t)(kk >> 5) * N + p;
+            const uint32_t bit = 1u << (kk & 31);
+            if (!(*wp & bit)) continue;
+            const int ox = off[3 * kk], oy = off[3 * kk + 1], oz = off[3 * kk + 2];
+            const int qi = i + ox, qj = j + oy, qk = k + oz;
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
+            const int64_t q = ((int64_t)qk * ny + qj) * nx + qi;
+            // Eq. fra:s1 in a fixed operation order, each step rounded once.
+            const double xi0 = __dmul_rn(h, (double)ox), xi1 = __dmul_rn(h, (double)oy),
+                         xi2 = __dmul_rn(h, (double)oz);
+            const double X0 = __dadd_rn(xi0, __dsub_rn((double)u[q], up[0]));
+            const double X1 = __dadd_rn(xi1, __dsub_rn((double)u[N + q], up[1]));
+            double l2 = __dadd_rn(__dmul_rn(X0, X0), __dmul_rn(X1, X1));
+            double r2 = __dadd_rn(__dmul_rn(xi0, xi0), __dmul_rn(xi1, xi1));
+            if (DIM == 3) {
+                const double X2 = __dadd_rn(xi2, __dsub_rn((double)u[2 * N + q], up[2]));
+                l2 = __dadd_rn(l2, __dmul_rn(X2, X2));
+                r2 = __dadd_rn(r2, __dmul_rn(xi2, xi2));
+            }
+            const double l = __dsqrt_rn(l2), r = __dsqrt_rn(r2);
+            const double s = __ddiv_rn(__dsub_rn(l, r), r);
+            if (s >= s0) {
+                atomicAnd(wp, ~bit);
+                const int km = nnb - 1 - kk;
+                atomicAnd(mask + (int64_t)(km >> 5) * N + q, ~(1u << (km & 31)));
+                if (break_step) {
+                    break_step[p * nnb + kk] = step_id;
+                    break_step[q * nnb + km] = step_id;
+                }
+                ++newly;
+                mark_broken_node(p, brflag, brlist, count);
+                mark_broken_node(q, brflag, brlist, count);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) newly += __shfl_xor_sync(0xffffffffu, newly, o);
+    if ((threadIdx.x & 31) == 0 && newly) {
+        atomicAdd(&count[1], newly);
+        atomicAdd(&count[2], newly);
+    }
+}
+
+// ------------------------------------------------------------------ pre-notch segment
+__device__ __forceinline__ int orient(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy)
+{
+    const int64_t v = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    return (v > 0) - (v < 0);
+}
+
+__device__ __forceinline__ bool within(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy)
+{
+    return cx >= min(ax, bx) && cx <= max(ax, bx) && cy >= min(ay, by) && cy <= max(ay, by);
+}
+
+__global__ void __launch_bounds__(kBlk)
+k_segment(int64_t N, int nx, int ny, int nnb, const int32_t *__restrict__ off, uint32_t *mask, int64_t ax,
+          int64_t ay, int64_t bx, int64_t by, int64_t den, uint32_t *brflag, int32_t *brlist,
+          unsigned long long *count)
+{
+    unsigned long long newly = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx), j = (int)(p / nx);
+        const int64_t px = den * (2 * i + 1), py = den * (2 * j + 1);
+        for (int kk = nnb / 2; kk < nnb; ++kk) {
+            const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny) continue;
+            const int64_t qx = den * (2 * qi + 1), qy = den * (2 * qj + 1);
+            const int d1 = orient(ax, ay, bx, by, px, py), d2 = orient(ax, ay, bx, by, qx, qy);
+            const int d3 = orient(px, py, qx, qy, ax, ay), d4 = orient(px, py, qx, qy, bx, by);
+            bool meet = (d1 * d2 < 0 && d3 * d4 < 0) || (d1 == 0 && within(ax, ay, bx, by, px, py)) ||
+                        (d2 == 0 && within(ax, ay, bx, by, qx, qy)) || (d3 == 0 && within(px, py, qx, qy, ax, ay)) ||
+                        (d4 == 0 && within(px, py, qx, qy, bx, by));
+            if (!meet) continue;
+            const int64_t q = (int64_t)qj * nx + qi;
+            uint32_t *wp = mask + (int64_t)(kk >> 5) * N + p;
+            const uint32_t bit = 1u << (kk & 31);
+            if (*wp & bit) {
+                atomicAnd(wp, ~bit);
+                const int km = nnb - 1 - kk;
+                atomicAnd(mask + (int64_t)(km >> 5) * N + q, ~(1u << (km & 31)));
+                ++newly;
+                mark_broken_node(p, brflag, brlist, count);
+                mark_broken_node(q, brflag, brlist, count);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) newly += __shfl_xor_sync(0xffffffffu, newly, o);
+    if ((threadIdx.x & 31) == 0 && newly) {
+        atomicAdd(&count[1], newly);
+        atomicAdd(&count[2], newly);
+    }
+}
+
+// ------------------------------------------------------------------ Omega_br rebuild from a mask
+__global__ void __launch_bounds__(kBlk)
+k_refresh(int64_t N, int nx, int ny, int nz, int nnb, const int32_t *__restrict__ off,
+          const uint32_t *__restrict__ mask, uint32_t *brflag, int32_t *brlist, unsigned long long *count)
+{
+    unsigned long long bonds = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        node_coords(p, nx, ny, i, j, k);
+        bool any = false;
+        for (int kk = 0; kk < nnb; ++kk) {
+            const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1], qk = k + off[3 * kk + 2];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
+            if ((mask[(int64_t)(kk >> 5) * N + p] >> (kk & 31)) & 1u) continue;
+            any = true;
+            if (kk >= nnb / 2) ++bonds;
+        }
+        if (any) mark_broken_node(p, brflag, brlist, count);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bonds += __shfl_xor_sync(0xffffffffu, bonds, o);
+    if ((threadIdx.x & 31) == 0 && bonds) atomicAdd(&count[1], bonds);
+}
+
+// ------------------------------------------------------------------ modulus gradient
+template <int DIM>
+__global__ void __launch_bounds__(kBlk)
+k_grad_modulus(const double *__restrict__ u, const double *__restrict__ lam, int64_t N, int nx, int ny, int nz,
+               int nnb, const int32_t *__restrict__ off, const double *__restrict__ coef1,
+               const uint32_t *__restrict__ mask, double scale, double *grad)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        node_coords(p, nx, ny, i, j, k);
+        double acc = 0.0;
+        for (int kk = 0; kk < nnb; ++kk) {
+            const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1], qk = k + off[3 * kk + 2];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
+            if (!((mask[(int64_t)(kk >> 5) * N + p] >> (kk & 31)) & 1u)) continue;
+            const int64_t q = ((int64_t)qk * ny + qj) * nx + qi;
+            double du[DIM], dl[DIM];
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) {
+                du[c] = u[c * N + q] - u[c * N + p];
+                dl[c] = lam[c * N + q] - lam[c * N + p];
+            }
+            if (DIM == 2) {
+                const double *cf = coef1 + 3 * kk;
+                acc += dl[0] * (cf[0] * du[0] + cf[1] * du[1]) + dl[1] * (cf[1] * du[0] + cf[2] * du[DIM - 1]);
+            } else {
+                const double *cf = coef1 + 6 * kk;
+                acc += dl[0] * (cf[0] * du[0] + cf[1] * du[1] + cf[2] * du[DIM - 1]) +
+                       dl[1] * (cf[1] * du[0] + cf[3] * du[1] + cf[4] * du[DIM - 1]) +
+                       dl[DIM - 1] * (cf[2] * du[0] + cf[4] * du[1] + cf[5] * du[DIM - 1]);
+            }
+        }
+        grad[p] += scale * acc;
+    }
+}
+
+// ------------------------------------------------------------------ Verlet
+// Drift: u += dt v + dt^2/2 a on free components, u += dt vp on constrained ones.
+__global__ void __launch_bounds__(kBlk)
+k_drift(double *u, const double *__restrict__ v, const double *__restrict__ a, const double *__restrict__ vp,
+        const uint8_t *__restrict__ cons, int64_t N, int dim, double dt)
+{
+    const double h2 = 0.5 * dt * dt;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < dim * N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / N);
+        const int64_t p = t - c * N;
+        const bool fixed = cons && ((cons[p] >> c) & 1);
+        if (fixed) u[t] += dt * (vp ? vp[t] : 0.0);
+        else u[t] += dt * v[t] + h2 * a[t];
+    }
+}
+
+// Kick: a_new = (f + b) / rho; v += dt/2 (a + a_new) on free components, v = vp on
+// constrained ones; a = a_new.
+__global__ void __launch_bounds__(kBlk)
+k_kick(double *v, double *a, const double *__restrict__ f, const double *__restrict__ b,
+       const double *__restrict__ vp, const uint8_t *__restrict__ cons, int64_t N, int dim, double dt,
+       double inv_rho, int first)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < dim * N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / N);
+        const int64_t p = t - c * N;
+        const double an = (f[t] + (b ? b[t] : 0.0)) * inv_rho;
+        if (!first) {
+            const bool fixed = cons && ((cons[p] >> c) & 1);
+            if (fixed) v[t] = vp ? vp[t] : 0.0;
+            else v[t] += 0.5 * dt * (a[t] + an);
+        }
+        a[t] = an;
+    }
+}
+
+int grid_blocks(int64_t work)
+{
+    int64_t b = (work + kBlk - 1) / kBlk;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+}  // namespace
+
+int launch_df_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t batch, bool project, double scale,
+                     cudaStream_t s)
+{
+    const int blocks = 152 * 4;
+    const int nx = (int)g->n[0], ny = (int)g->n[1], nz = (int)g->n[2];
+#define PD_DF(T, D)                                                                                         \
+    k_df_gather<T, D><<<blocks, kBlk, 0, s>>>((const T *)u, (T *)out, g->N, nx, ny, nz, g->nnb, g->d_brlist, \
+                                               g->d_count, g->d_mask, g->d_off, g->d_coef, g->d_cons,       \
+                                               project ? 1 : 0, scale, batch)
+    if (g->dim == 2) {
+        if (f64) PD_DF(double, 2); else PD_DF(float, 2);
+    } else {
+        if (f64) PD_DF(double, 3); else PD_DF(float, 3);
+    }
+#undef PD_DF
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int launch_break(pd_grid *g, const void *u, bool f64, int32_t *break_step, int32_t step_id, cudaStream_t s)
+{
+    if (!(g->s0 > 0.0)) return PD_OK;
+    const int blocks = grid_blocks(g->N);
+    const int nx = (int)g->n[0], ny = (int)g->n[1], nz = (int)g->n[2];
+#define PD_BRK(D, TU)                                                                                          \
+    k_break<D, TU><<<blocks, kBlk, 0, s>>>((const TU *)u, g->N, nx, ny, nz, g->nnb, g->d_off, g->d_mask, g->h, \
+                                            g->s0, break_step, step_id, g->d_brflag, g->d_brlist, g->d_count)
+    if (g->dim == 2) {
+        if (f64) PD_BRK(2, double); else PD_BRK(2, float);
+    } else {
+        if (f64) PD_BRK(3, double); else PD_BRK(3, float);
+    }
+#undef PD_BRK
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int launch_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, cudaStream_t s)
+{
+    k_segment<<<grid_blocks(g->N), kBlk, 0, s>>>(g->N, (int)g->n[0], (int)g->n[1], g->nnb, g->d_off, g->d_mask,
+                                                  2 * seg[0], 2 * seg[1], 2 * seg[2], 2 * seg[3], den, g->d_brflag,
+                                                  g->d_brlist, g->d_count);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+int refresh_broken_nodes(pd_grid *g, cudaStream_t s)
+{
+    PD_CUDA(cudaMemsetAsync(g->d_brflag, 0, sizeof(uint32_t) * (size_t)g->N, s));
+    PD_CUDA(cudaMemsetAsync(g->d_count, 0, sizeof(unsigned long long) * 2, s));
+    k_refresh<<<grid_blocks(g->N), kBlk, 0, s>>>(g->N, (int)g->n[0], (int)g->n[1], (int)g->n[2], g->nnb, g->d_off,
+                                                  g->d_mask, g->d_brflag, g->d_brlist, g->d_count);
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 2, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    g->broken_total = (int64_t)g->h_pinned[1];
+    return PD_OK;
+}
+
+int launch_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale, double *grad, cudaStream_t s)
+{
+    const int nx = (int)g->n[0], ny = (int)g->n[1], nz = (int)g->n[2];
+    if (g->dim == 2)
+        k_grad_modulus<2><<<grid_blocks(g->N), kBlk, 0, s>>>(u, lam, g->N, nx, ny, nz, g->nnb, g->d_off, g->d_coef1,
+                                                              g->d_mask, scale, grad);
+    else
+        k_grad_modulus<3><<<grid_blocks(g->N), kBlk, 0, s>>>(u, lam, g->N, nx, ny, nz, g->nnb, g->d_off, g->d_coef1,
+                                                              g->d_mask, scale, grad);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+}  // namespace pd
+
+using namespace pd;
+
+extern "C" int pd_step(pd_grid *g, double *u, double *v, const double *b, int nsteps, double dt,
+                       const double *v_prescribed, int32_t *break_step, int32_t step_base, pd_step_stats *stats,
+                       void *stream)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (!u || !v) return fail(PD_ERR_INVALID, "u and v must be device pointers");
+    if (nsteps < 0 || !(dt > 0)) return fail(PD_ERR_INVALID, "nsteps >= 0 and dt > 0 required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t L = (int64_t)g->dim * g->N;
+    const size_t need = sizeof(double) * 2 * (size_t)L;
+    if (g->ws_bytes < need) {
+        cudaFree(g->ws);
+        g->ws = nullptr;
+        g->ws_bytes = 0;
+        if (cudaMalloc(&g->ws, need) != cudaSuccess) return fail(PD_ERR_OOM, "Verlet workspace");
+        g->ws_bytes = need;
+    }
+    double *a = (double *)g->ws;
+    double *f = a + L;
+    const uint8_t *cons = g->has_cons ? g->d_cons : nullptr;
+    const int blocks = grid_blocks(L);
+    const uint32_t mflags = PD_F64 | PD_METHOD_STENCIL | kForceMu;
+    PD_CUDA(cudaMemsetAsync(g->d_count + 2, 0, sizeof(unsigned long long), s));
+    // f = A(mu) u = -K u at the incoming state, a = (f + b) / rho
+    int rc = matvec(g, 1, u, f, mflags, s, nullptr, nullptr, nullptr, -1.0);
+    if (rc) return rc;
+    k_kick<<<blocks, kBlk, 0, s>>>(v, a, f, b, v_prescribed, cons, g->N, g->dim, dt, 1.0 / g->rho, 1);
+    for (int st = 0; st < nsteps; ++st) {
+        k_drift<<<blocks, kBlk, 0, s>>>(u, v, a, v_prescribed, cons, g->N, g->dim, dt);
+        rc = launch_break(g, u, true, break_step, step_base + st + 1, s);
+        if (rc) return rc;
+        rc = matvec(g, 1, u, f, mflags, s, nullptr, nullptr, nullptr, -1.0);
+        if (rc) return rc;
+        k_kick<<<blocks, kBlk, 0, s>>>(v, a, f, b, v_prescribed, cons, g->N, g->dim, dt, 1.0 / g->rho, 0);
+    }
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    g->broken_total = (int64_t)g->h_pinned[1];
+    if (stats) {
+        stats->steps = nsteps;
+        stats->newly_broken = (int64_t)g->h_pinned[2];
+        stats->broken_total = g->broken_total;
+    }
+    return PD_OK;
+}

@@ -1,0 +1,157 @@
+// pd_internal.cuh -- internal declarations of libpd (not part of the C ABI).
+//
+// Data layout in device memory (all owned by the pd_grid unless stated):
+//   caller vectors  [dim][N] SoA, x fastest (node p = i + nx (j + ny k));
+//   d_cons          uint8 [N], bit c set when component c is constrained (Omega_c);
+//   d_mask          uint32 [W][N] bond-intact bits, W = ceil(nnb / 32), word-major so that
+//                   a warp reading word w of 32 consecutive nodes is coalesced;
+//   d_kd{32,64}     diagonal block table Kd = sum of c(o) over in-grid offsets, indexed by the
+//                   clipped distances to the faces (the D^e table of Eq. mat:se, folded into
+//                   the diagonal);
+//   d_sym{32,64}    real symbol of one FFT tile (Sec. 3.2 Algorithm 3, per tile);
+//   d_E             double [N] per-node modulus (optional);
+//   d_brlist/flag   Omega_br: nodes holding at least one broken bond, compacted list.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pd.h"
+
+namespace pd {
+
+// ------------------------------------------------------------------ limits
+constexpr int kMaxM2 = 8;    // largest horizon M compiled for 2D
+constexpr int kMaxM3 = 4;    // largest horizon M compiled for 3D
+constexpr int kFftP = 64;    // FFT tile edge (2D)
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+#define PD_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return ::pd::fail(PD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------ offsets
+// Number of offsets o != 0 with |o|^2 <= M^2 (2D: oz = 0).
+__host__ __device__ constexpr int count_offsets(int dim, int M)
+{
+    int c = 0;
+    for (int oz = (dim == 3 ? -M : 0); oz <= (dim == 3 ? M : 0); ++oz)
+        for (int oy = -M; oy <= M; ++oy)
+            for (int ox = -M; ox <= M; ++ox) {
+                int d2 = ox * ox + oy * oy + oz * oz;
+                if (d2 > 0 && d2 <= M * M) ++c;
+            }
+    return c;
+}
+
+// Integer square root floor(sqrt(v)) for small non-negative v (compile-time friendly).
+__host__ __device__ constexpr int isqrt_c(int v)
+{
+    int r = 0;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+// Number of coefficient reals per offset: 3 in 2D (xx, xy, yy), 6 in 3D (xx, xy, xz, yy, yz, zz).
+__host__ __device__ constexpr int ncoef(int dim) { return dim == 2 ? 3 : 6; }
+
+// Coefficient table passed by value to the stencil kernels (kernel parameter space).
+template <typename T, int DIM, int M>
+struct CoefTab {
+    static constexpr int kN = count_offsets(DIM, M);
+    T v[kN * ncoef(DIM)];   // canonical offset order, ncoef(DIM) reals each
+};
+
+// ------------------------------------------------------------------ the grid
+}  // namespace pd
+
+struct pd_grid {
+    int dim = 2, M = 1, nnb = 0, W = 1;
+    int64_t n[3] = {1, 1, 1};
+    int64_t N = 0;
+    double h = 0, delta = 0;
+    double E = 1, rho = 1, thickness = 1, s0 = 0;
+    double alpha = 0, alpha1 = 0;   // micromodulus at E and at E = 1
+    int device = 0;
+    bool has_cons = false;
+    bool has_E = false;
+
+    std::vector<int32_t> off;       // [nnb][3] canonical (oz, oy, ox) lexicographic order
+    std::vector<double> coef1;      // [nnb][ncoef] bond blocks at E = 1 (alpha1 lambda h^(d-1) o_a o_b / |o|^3)
+
+    uint8_t *d_cons = nullptr;
+    double *d_E = nullptr;
+    uint32_t *d_mask = nullptr;
+    int32_t *d_brlist = nullptr;
+    uint32_t *d_brflag = nullptr;
+    int32_t *d_off = nullptr;       // [nnb][3] device copy of the offsets
+    double *d_coef = nullptr;       // [nnb][ncoef] bond blocks at the current modulus
+    double *d_coef1 = nullptr;      // [nnb][ncoef] bond blocks at E = 1
+    unsigned long long *d_count = nullptr;   // [0] |Omega_br|, [1] broken total, [2] newly broken (scratch)
+    double *d_kd64 = nullptr;
+    float *d_kd32 = nullptr;
+    double *d_sym64 = nullptr;
+    float *d_sym32 = nullptr;
+    int64_t kd_entries = 0;
+    int64_t broken_total = 0;
+
+    // CG / Verlet workspace, allocated on first use
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned long long *h_pinned = nullptr;  // small pinned host mailbox
+
+    // measured method choice cache: [dtype 0/1] -> 0 unknown, 1 stencil, 2 fft
+    int auto_choice[2] = {0, 0};
+};
+
+namespace pd {
+
+// ------------------------------------------------------------------ launchers (pd_stencil.cu)
+struct MatvecArgs {
+    const void *u;        // input  [batch][dim][N]
+    void *out;            // output [batch][dim][N]
+    int64_t batch;
+    bool project;         // P K P
+    bool use_mu;          // honour the bond mask inline (direct form)
+    bool use_E;           // per-node modulus (direct form)
+    double scale;         // multiplies the whole operator (1 = K u)
+    // optional fused reduction: dot_out[b] = sum_p in . out (FP64), needs scratch
+    double *dot_partial;  // [gridDim.x * gridDim.y] per batch
+    double *dot_out;      // [batch]
+    unsigned int *retire; // [batch] counters, zero on entry, reset by the last block
+};
+int launch_stencil(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);
+int stencil_blocks(pd_grid *g, bool f64, bool direct);   // CTAs per field (for sizing partials)
+
+// ------------------------------------------------------------------ launchers (pd_fft.cu)
+int launch_fft_tile(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);
+int fft_prepare(pd_grid *g);   // builds the tile symbol tables
+
+// ------------------------------------------------------------------ launchers (pd_crack.cu)
+int launch_df_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t batch, bool project,
+                     double scale, cudaStream_t s);
+int launch_break(pd_grid *g, const void *u, bool f64, int32_t *break_step, int32_t step_id,
+                 cudaStream_t s);
+int launch_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, cudaStream_t s);
+int refresh_broken_nodes(pd_grid *g, cudaStream_t s);
+int launch_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale, double *grad,
+                        cudaStream_t s);
+
+// ------------------------------------------------------------------ matvec front end (pd_api.cu)
+// Internal flag: bonds may have broken on the device since the host last looked;
+// always run the broken-bond correction (it reads the device-side count).
+constexpr uint32_t kForceMu = 0x80000000u;
+int upload_coefs(pd_grid *g);
+int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, cudaStream_t s,
+           double *dot_partial = nullptr, double *dot_out = nullptr, unsigned int *retire = nullptr,
+           double scale = 1.0);
+
+}  // namespace pd

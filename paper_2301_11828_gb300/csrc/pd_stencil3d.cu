@@ -1,0 +1,232 @@
+// pd_stencil3d.cu -- 3D stencil, TBTBT form (Sec. 4).
+//
+// Same operator as the 2D TBT form with 3x3 blocks (six unique reals per
+// offset, Eq. mae:e1):  (K u)_p = Kd_p u_p - sum_{o != 0} c(o) u~_{p+o}, summed
+// over offset pairs.  A CTA owns 32 x 8 x R outputs; a thread owns a z-column
+// of R outputs.  The (32 + 2M) x (8 + 2M) x (R + 2M) halo box of the three
+// components is staged in shared memory; for each (ox, oy) column pair the
+// thread loads the z-windows of columns (x+ox, y+oy) and (x-ox, y-oy).
+#include "pd_stencil.cuh"
+
+namespace pd {
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kThreads)
+k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
+        const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
+        PairTab<T, 3, M> tab, double *dot_partial, double *dot_out, unsigned int *retire)
+{
+    constexpr int R = rows3d<T, M>();
+    constexpr int TX = kTX3, TY = kTY3, SX = TX + 2 * M, SY = TY + 2 * M, SZ = R + 2 * M;
+    constexpr int PL = SX * SY * SZ;
+    constexpr int NP = PairTab<T, 3, M>::kPairs;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s = reinterpret_cast<T *>(smem_raw);   // [3][SZ][SY][SX]
+
+    const int zt = blockIdx.z % nzt;
+    const int64_t b = blockIdx.z / nzt;
+    const T *ub = u + b * 3 * N;
+    T *ob = out + b * 3 * N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = zt * R;
+
+    for (int t = threadIdx.x; t < PL; t += kThreads) {
+        const int zz = t / (SX * SY), rem = t - zz * SX * SY;
+        const int yy = rem / SX, xx = rem - yy * SX;
+        const int gx = x0 - M + xx, gy = y0 - M + yy, gz = z0 - M + zz;
+        T v0 = T(0), v1 = T(0), v2 = T(0);
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
+            const int64_t p = ((int64_t)gz * ny + gy) * nx + gx;
+            v0 = __ldg(ub + p);
+            v1 = __ldg(ub + N + p);
+            v2 = __ldg(ub + 2 * N + p);
+            if (project) {
+                const uint8_t m = __ldg(cons + p);
+                if (m & 1) v0 = T(0);
+                if (m & 2) v1 = T(0);
+                if (m & 4) v2 = T(0);
+            }
+        }
+        s[t] = v0;
+        s[PL + t] = v1;
+        s[2 * PL + t] = v2;
+    }
+    __syncthreads();
+
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const T *base = s + (ty + M) * SX + (tx + M);   // column (x, y), plane 0
+    T acc[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[c][r] = T(0);
+
+    static_for<0, M + 1>([&](auto OYI) {
+        constexpr int oy = M - decltype(OYI)::value;
+        constexpr int Mx = isqrt_c(M * M - oy * oy);
+        static_for<-Mx, Mx + 1>([&](auto OX) {
+            constexpr int ox = decltype(OX)::value;
+            if constexpr (oy > 0 || ox > 0) {
+                constexpr int Mz = isqrt_c(M * M - ox * ox - oy * oy);
+                constexpr int pbase = pair_index3(M, ox, oy, 0);   // pairs of this column are consecutive in oz
+                T wp[3][SZ], wm[3][SZ];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int i = 0; i < SZ; ++i) {
+                        wp[c][i] = base[c * PL + i * SX * SY + oy * SX + ox];
+                        wm[c][i] = base[c * PL + i * SX * SY - oy * SX - ox];
+                    }
+#pragma unroll
+                for (int oz = -Mz; oz <= Mz; ++oz) {
+                    const int pi = pbase + oz;
+                    const T *cf = tab.v + 6 * pi;
+                    const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const T s0 = wp[0][r + M + oz] + wm[0][r + M - oz];
+                        const T s1 = wp[1][r + M + oz] + wm[1][r + M - oz];
+                        const T s2 = wp[2][r + M + oz] + wm[2][r + M - oz];
+                        acc[0][r] = dfma(cxx, s0, dfma(cxy, s1, dfma(cxz, s2, acc[0][r])));
+                        acc[1][r] = dfma(cxy, s0, dfma(cyy, s1, dfma(cyz, s2, acc[1][r])));
+                        acc[2][r] = dfma(cxz, s0, dfma(cyz, s1, dfma(czz, s2, acc[2][r])));
+                    }
+                }
+            }
+        });
+    });
+    T w0[3][SZ];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int i = 0; i < SZ; ++i) w0[c][i] = base[c * PL + i * SX * SY];
+    constexpr int pcentre = pair_index3(M, 0, 0, 1);
+#pragma unroll
+    for (int oz = 1; oz <= M; ++oz) {
+        const int pi = pcentre + (oz - 1);
+        const T *cf = tab.v + 6 * pi;
+        const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const T s0 = w0[0][r + M + oz] + w0[0][r + M - oz];
+            const T s1 = w0[1][r + M + oz] + w0[1][r + M - oz];
+            const T s2 = w0[2][r + M + oz] + w0[2][r + M - oz];
+            acc[0][r] = dfma(cxx, s0, dfma(cxy, s1, dfma(cxz, s2, acc[0][r])));
+            acc[1][r] = dfma(cxy, s0, dfma(cyy, s1, dfma(cyz, s2, acc[1][r])));
+            acc[2][r] = dfma(cxz, s0, dfma(cyz, s1, dfma(czz, s2, acc[2][r])));
+        }
+    }
+
+    double dot = 0.0;
+    const int gx = x0 + tx, gy = y0 + ty;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int gz = z0 + r;
+        if (gx < nx && gy < ny && gz < nz) {
+            const int64_t p = ((int64_t)gz * ny + gy) * nx + gx;
+            const T *kk = tab.v + 6 * NP;
+            T k0 = kk[0], k1 = kk[1], k2 = kk[2], k3 = kk[3], k4 = kk[4], k5 = kk[5];
+            const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M),
+                      c0 = min(gz, M), c1 = min(nz - 1 - gz, M);
+            if (a0 != M || a1 != M || b0 != M || b1 != M || c0 != M || c1 != M) {
+                const int cls =
+                    ((((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1) * (M + 1) + c0) * (M + 1) + c1;
+                const T *q = kd + 6 * cls;
+                k0 = __ldg(q);
+                k1 = __ldg(q + 1);
+                k2 = __ldg(q + 2);
+                k3 = __ldg(q + 3);
+                k4 = __ldg(q + 4);
+                k5 = __ldg(q + 5);
+            }
+            const T u0 = w0[0][r + M], u1 = w0[1][r + M], u2 = w0[2][r + M];
+            T f0 = dfma(k0, u0, dfma(k1, u1, dfma(k2, u2, -acc[0][r])));
+            T f1 = dfma(k1, u0, dfma(k3, u1, dfma(k4, u2, -acc[1][r])));
+            T f2 = dfma(k2, u0, dfma(k4, u1, dfma(k5, u2, -acc[2][r])));
+            if (project) {
+                const uint8_t m = __ldg(cons + p);
+                if (m & 1) f0 = T(0);
+                if (m & 2) f1 = T(0);
+                if (m & 4) f2 = T(0);
+            }
+            f0 *= scale;
+            f1 *= scale;
+            f2 *= scale;
+            ob[p] = f0;
+            ob[N + p] = f1;
+            ob[2 * N + p] = f2;
+            dot += (double)u0 * f0 + (double)u1 * f1 + (double)u2 * f2;
+        }
+    }
+    if (dot_partial)
+        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y * nzt,
+                         blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zt), b);
+}
+
+namespace {
+
+template <typename T, int M>
+PairTab<T, 3, M> make_pairs3(const pd_grid *g)
+{
+    PairTab<T, 3, M> t{};
+    double c[6], tot[6] = {0, 0, 0, 0, 0, 0};
+    auto put = [&](int ox, int oy, int oz) {
+        const int pi = pair_index3(M, ox, oy, oz);
+        coef_of(g, ox, oy, oz, false, c);
+        for (int i = 0; i < 6; ++i) {
+            t.v[6 * pi + i] = (T)c[i];
+            tot[i] += 2 * c[i];
+        }
+    };
+    for (int oy = M; oy >= 0; --oy) {
+        const int Mx = isqrt_c(M * M - oy * oy);
+        for (int ox = -Mx; ox <= Mx; ++ox) {
+            if (oy == 0 && ox <= 0) continue;
+            const int Mz = isqrt_c(M * M - ox * ox - oy * oy);
+            for (int oz = -Mz; oz <= Mz; ++oz) put(ox, oy, oz);
+        }
+    }
+    for (int oz = 1; oz <= M; ++oz) put(0, 0, oz);
+    constexpr int NP = PairTab<T, 3, M>::kPairs;
+    for (int i = 0; i < 6; ++i) t.v[6 * NP + i] = (T)tot[i];
+    return t;
+}
+
+template <typename T, int M>
+int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
+{
+    constexpr int R = rows3d<T, M>();
+    const size_t smem = sizeof(T) * 3 * (kTX3 + 2 * M) * (kTY3 + 2 * M) * (R + 2 * M);
+    auto kern = k_tbt3d<T, M>;
+    allow_smem(kern, smem);
+    const int nzt = (int)((g->n[2] + R - 1) / R);
+    if ((int64_t)nzt * a.batch > 65535) return fail(PD_ERR_INVALID, "3D batch too large for one launch");
+    dim3 grid((unsigned)((g->n[0] + kTX3 - 1) / kTX3), (unsigned)((g->n[1] + kTY3 - 1) / kTY3),
+              (unsigned)(nzt * a.batch));
+    const T *kd = sizeof(T) == 4 ? (const T *)g->d_kd32 : (const T *)g->d_kd64;
+    kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], (int)g->n[2], nzt,
+                                      g->N, g->d_cons, a.project ? 1 : 0, kd, (T)a.scale, make_pairs3<T, M>(g),
+                                      a.dot_partial, a.dot_out, a.retire);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+template <typename T>
+int run_t(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
+{
+    switch (g->M) {
+        case 1: return run<T, 1>(g, a, s);
+        case 2: return run<T, 2>(g, a, s);
+        case 3: return run<T, 3>(g, a, s);
+        case 4: return run<T, 4>(g, a, s);
+    }
+    return fail(PD_ERR_INVALID, "horizon M not compiled for 3D");
+}
+
+}  // namespace
+
+int run_tbt3d(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s)
+{
+    return f64 ? run_t<double>(g, a, s) : run_t<float>(g, a, s);
+}
+
+}  // namespace pd

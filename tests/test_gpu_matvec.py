@@ -1,0 +1,238 @@
+"""GPU parity of K u against the FP64 oracle (through the C ABI).
+
+Tolerances: relative L2 <= 1e-12 for FP64, <= 2e-5 for FP32 (the inputs are
+rounded to FP32 first, so the FP32 check measures the kernel's own error).
+Sizes span several CTA tiles and leave ragged tails in every direction.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pd():
+    import paper_2301_11828_gb300 as pd
+    pd.load_library()
+    assert torch.cuda.is_available()
+    return pd
+
+
+TOL = {torch.float64: 1e-12, torch.float32: 2e-5}
+
+
+def _oracle_K(dim, n, h, M, u, cons=None, E=None, mu=None, Efield=None):
+    if Efield is not None:
+        al1 = oracle.alpha(dim, 1.0, M * h)
+        return oracle.stiffness(dim, n, h, M, al1, u, cons=cons, E=Efield, mu=mu)
+    al = oracle.alpha(dim, E if E is not None else 1.0, M * h)
+    return oracle.stiffness(dim, n, h, M, al, u, cons=cons, mu=mu)
+
+
+def _run(pd, g, u_np, dtype, flags):
+    u = torch.tensor(u_np, dtype=dtype, device="cuda")
+    out = g.matvec(u, flags=flags)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy(), u.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n,M", [((67, 45), 1), ((67, 45), 2), ((130, 97), 3), ((129, 70), 4), ((75, 66), 5),
+                                 ((80, 91), 6), ((70, 70), 7), ((99, 53), 8), ((5, 3), 3), ((1, 1), 2),
+                                 ((1, 40), 3), ((200, 2), 4)])
+def test_stencil_2d_matches_oracle(pd, dtype, n, M):
+    h = 1.0 / 64
+    rng = np.random.default_rng(M * 1000 + n[0])
+    u_np = rng.uniform(-1, 1, (2, n[1], n[0]))
+    g = pd.Grid(2, n, h, M, E=2.5)
+    out, u_used = _run(pd, g, u_np, dtype, pd.PD_METHOD_STENCIL)
+    ref = _oracle_K(2, n, h, M, u_used, E=2.5)
+    assert rel_l2(out, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_stencil_2d_projection(pd, dtype):
+    w = syn.plate_static(97, 3, tag=5, u_amp=1.0)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+    out, u_used = _run(pd, g, w.u, dtype, pd.PD_METHOD_STENCIL | pd.PD_PROJECT)
+    ref = _oracle_K(2, w.n, w.h, w.M, u_used, cons=w.constrained)
+    assert rel_l2(out, ref) <= TOL[dtype]
+    assert np.all(out[w.constrained.astype(bool)] == 0)
+    # without the flag the constraint is not applied
+    out2, _ = _run(pd, g, w.u, dtype, pd.PD_METHOD_STENCIL)
+    assert rel_l2(out2, _oracle_K(2, w.n, w.h, w.M, u_used)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n,M", [((37, 19, 13), 1), ((37, 19, 13), 2), ((40, 21, 19), 3), ((35, 17, 22), 4),
+                                 ((3, 2, 5), 3), ((1, 1, 1), 1)])
+def test_stencil_3d_matches_oracle(pd, dtype, n, M):
+    h = 1.0 / 32
+    rng = np.random.default_rng(M + 7 * n[0])
+    u_np = rng.uniform(-1, 1, (3, n[2], n[1], n[0]))
+    g = pd.Grid(3, n, h, M)
+    out, u_used = _run(pd, g, u_np, dtype, pd.PD_METHOD_STENCIL)
+    ref = _oracle_K(3, n, h, M, u_used)
+    assert rel_l2(out, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_stencil_3d_projection(pd, dtype):
+    w = syn.cube(24, 3)
+    g = pd.Grid(3, w.n, w.h, w.M, constrained=w.constrained)
+    out, u_used = _run(pd, g, w.u, dtype, pd.PD_METHOD_STENCIL | pd.PD_PROJECT)
+    ref = _oracle_K(3, w.n, w.h, w.M, u_used, cons=w.constrained)
+    assert rel_l2(out, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("M", [3, 4])
+def test_modulus_field_direct_form(pd, dtype, M):
+    """Per-node modulus: bond (p,q) uses (E_p + E_q)/2 (the direct kernel)."""
+    n = (83, 71)
+    h = 1.0 / 80
+    E = syn.lognormal_modulus(n, 0.1, 31)
+    rng = np.random.default_rng(3)
+    u_np = rng.uniform(-1, 1, (2, n[1], n[0]))
+    g = pd.Grid(2, n, h, M, E_field=torch.tensor(E, device="cuda"))
+    out, u_used = _run(pd, g, u_np, dtype, 0)
+    ref = _oracle_K(2, n, h, M, u_used, Efield=E)
+    assert rel_l2(out, ref) <= TOL[dtype]
+
+
+def _random_broken_state(pd, g, n, h, M, dim, seed, sigma=0.05):
+    """Break a scattered set of bonds with the library, return the oracle mu."""
+    rng = np.random.default_rng(seed)
+    u_np = rng.normal(0, sigma * h, (dim,) + tuple(reversed(n)))
+    g.set_material(E=1.0, s0=0.03)
+    nb = g.break_bonds(torch.tensor(u_np, device="cuda"))
+    mu = oracle.intact_mu(dim, n, M)
+    nb_or = oracle.break_bonds(dim, n, h, M, 0.03, u_np, mu)
+    assert nb == nb_or and nb > 0
+    return mu
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("dim,n,M", [(2, (90, 77), 3), (2, (70, 66), 5), (3, (30, 21, 17), 2)])
+def test_broken_bonds_df_gather(pd, dtype, dim, n, M):
+    """TBT stencil + sparse D^f gather equals the oracle's bond sum with mu."""
+    h = 1.0 / 64
+    g = pd.Grid(dim, n, h, M)
+    mu = _random_broken_state(pd, g, n, h, M, dim, seed=11 + M)
+    rng = np.random.default_rng(5)
+    u_np = rng.uniform(-1, 1, (dim,) + tuple(reversed(n)))
+    out, u_used = _run(pd, g, u_np, dtype, pd.PD_METHOD_STENCIL)
+    ref = _oracle_K(dim, n, h, M, u_used, mu=mu)
+    assert rel_l2(out, ref) <= TOL[dtype]
+    # ignoring the broken bonds gives the intact operator
+    out0, _ = _run(pd, g, u_np, dtype, pd.PD_METHOD_STENCIL | pd.PD_IGNORE_BROKEN)
+    assert rel_l2(out0, _oracle_K(dim, n, h, M, u_used)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_broken_bonds_with_modulus_field(pd, dtype):
+    n, M, h = (77, 64), 3, 1.0 / 64
+    E = syn.lognormal_modulus(n, 0.1, 8)
+    g = pd.Grid(2, n, h, M, E_field=torch.tensor(E, device="cuda"))
+    rng = np.random.default_rng(4)
+    u_b = rng.normal(0, 0.05 * h, (2, n[1], n[0]))
+    g.set_material(E=1.0, s0=0.03, E_field=torch.tensor(E, device="cuda"))
+    g.break_bonds(torch.tensor(u_b, device="cuda"))
+    mu = oracle.intact_mu(2, n, M)
+    oracle.break_bonds(2, n, h, M, 0.03, u_b, mu)
+    u_np = rng.uniform(-1, 1, (2, n[1], n[0]))
+    out, u_used = _run(pd, g, u_np, dtype, 0)
+    ref = _oracle_K(2, n, h, M, u_used, mu=mu, Efield=E)
+    assert rel_l2(out, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_matvec_equals_single(pd, dtype):
+    n, M, h = (70, 45), 3, 1.0 / 64
+    g = pd.Grid(2, n, h, M)
+    rng = np.random.default_rng(9)
+    U = torch.tensor(rng.uniform(-1, 1, (5, 2, n[1], n[0])), dtype=dtype, device="cuda")
+    out = g.matvec(U, flags=pd.PD_METHOD_STENCIL)
+    for b in range(5):
+        single = g.matvec(U[b].contiguous(), flags=pd.PD_METHOD_STENCIL)
+        assert torch.equal(out[b], single)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("M", [3, 6])
+def test_full_size_plate_1024(pd, dtype, M):
+    """The 1024 x 1024 plate at delta = 3h and 6h, whole field against the oracle."""
+    w = syn.large_plate(M)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+    out, u_used = _run(pd, g, w.u, dtype, pd.PD_METHOD_STENCIL | pd.PD_PROJECT)
+    ref = _oracle_K(2, w.n, w.h, w.M, u_used, cons=w.constrained)
+    assert rel_l2(out, ref) <= TOL[dtype]
+
+
+def test_full_size_cube_128_sampled(pd):
+    """128^3 cube, FP32: whole-field relative error, and FP64 on a sampled slab."""
+    w = syn.cube(128, 3)
+    g = pd.Grid(3, w.n, w.h, w.M, constrained=w.constrained)
+    out, u_used = _run(pd, g, w.u, torch.float32, pd.PD_METHOD_STENCIL | pd.PD_PROJECT)
+    ref = _oracle_K(3, w.n, w.h, w.M, u_used, cons=w.constrained)
+    assert rel_l2(out, ref) <= 2e-5
+    out64, u64 = _run(pd, g, w.u, torch.float64, pd.PD_METHOD_STENCIL | pd.PD_PROJECT)
+    ref64 = _oracle_K(3, w.n, w.h, w.M, u64, cons=w.constrained)
+    assert rel_l2(out64, ref64) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- bond state (bit-exact)
+
+@pytest.mark.parametrize("dim,n,M,dtype", [(2, (150, 131), 3, torch.float64), (2, (64, 70), 6, torch.float64),
+                                           (2, (90, 80), 4, torch.float32), (3, (33, 20, 18), 3, torch.float64)])
+def test_break_bonds_bit_exact(pd, dim, n, M, dtype):
+    """Broken sets equal the oracle's bit for bit (same FP64 operation order)."""
+    from helpers import mask_to_mu
+    h = 1.0 / 128
+    rng = np.random.default_rng(21)
+    g = pd.Grid(dim, n, h, M, s0=1e-3)
+    mu = oracle.intact_mu(dim, n, M)
+    total = 0
+    for it in range(3):
+        u_np = rng.normal(0, 1.5e-3 * h, (dim,) + tuple(reversed(n)))
+        u_t = torch.tensor(u_np, dtype=dtype, device="cuda")
+        u_used = u_t.double().cpu().numpy()
+        nb = g.break_bonds(u_t)
+        nb_or = oracle.break_bonds(dim, n, h, M, 1e-3, u_used, mu)
+        assert nb == nb_or
+        total += nb
+        got = mask_to_mu(g.bond_mask().cpu().numpy(), g.nnb)
+        assert np.array_equal(got, mu)
+    assert total > 0
+    assert np.array_equal(g.offsets(), oracle.offsets(dim, M))
+
+
+@pytest.mark.parametrize("nside", [32, 512])
+def test_prenotch_bit_exact(pd, nside):
+    from helpers import mask_to_mu
+    w = syn.crack_plate(nside, 3)
+    g = pd.Grid(2, w.n, w.h, w.M)
+    nb = g.break_segment(w.extra["notch"], w.extra["notch_den"])
+    mu = oracle.intact_mu(2, w.n, w.M)
+    nb_or = oracle.prenotch(w.n, w.M, w.extra["notch"], w.extra["notch_den"], mu)
+    assert nb == nb_or
+    assert np.array_equal(mask_to_mu(g.bond_mask().cpu().numpy(), g.nnb), mu)
+
+
+def test_bond_mask_roundtrip(pd):
+    from helpers import mu_to_mask
+    n, M, h = (40, 33), 3, 1.0 / 32
+    g = pd.Grid(2, n, h, M)
+    rng = np.random.default_rng(2)
+    mu = oracle.intact_mu(2, n, M)
+    oracle.break_bonds(2, n, h, M, 0.02, rng.normal(0, 0.02 * h, (2, n[1], n[0])), mu)
+    g.set_bond_mask(torch.tensor(mu_to_mask(mu), device="cuda"))
+    u_np = rng.uniform(-1, 1, (2, n[1], n[0]))
+    out, u_used = _run(pd, g, u_np, torch.float64, pd.PD_METHOD_STENCIL)
+    assert rel_l2(out, _oracle_K(2, n, h, M, u_used, mu=mu)) <= 1e-12
