@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the peridynamic stiffness product K u on one GB300.
+
+Headline (one JSON line on stdout): K u throughput in GDOF/s on the 1024 x 1024
+plate (delta = 3h, ~2.1M DOF per field), FP32, over a batch of independent
+displacement fields (load cases) so that the inputs exceed L2 -- one step is one
+batched K u launch through the C ABI.  Each rank of a multi-GPU launch works on
+its own batch (weak scaling, no collective on the data path).
+
+Also reported in the same line: the roofline of the dominant kernel, the SM
+clocks seen during the timed region, an end-to-end figure with host buffers,
+the FP32/FP64 x stencil/FFT x delta = 3h/6h variants, the static CG solve
+(mixed precision vs FP64) to a relative residual of 1e-8, the 128^3 cube and
+the dynamic crack loop, and the CPU oracle timed on this host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "K·u GDOF/s (FP32, 1024x1024 plate, delta=3h)"
+UNIT = "GDOF/s"
+NSIDE, MH = 1024, 3
+BATCH = 32          # 32 fields x 2 comps x 1M nodes x 4 B = 268 MB of inputs (> 129 MB L2)
+
+# DRAM traffic of the dominant kernel per launch (ncu, dram__bytes_read.sum + dram__bytes_write.sum),
+# recorded with the hash of the kernel sources it was taken on; reported only while they match.
+TRAFFIC = {
+    "kernel": "k_tbt2d<float,3>",
+    "sources": ["paper_2301_11828_gb300/csrc/pd_stencil2d.cu", "paper_2301_11828_gb300/csrc/pd_stencil.cuh",
+                "paper_2301_11828_gb300/csrc/pd_reduce.cuh"],
+    "sha256": None,
+    "bytes_per_field": None,
+}
+
+
+def _src_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, dev_uuid=None):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits", "-lms", "50"]
+        if dev_uuid:
+            cmd.insert(1, f"--id={dev_uuid}")
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        time.sleep(0.12)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, smax, reasons, n = [], [], set(), 0
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            n += 1
+            for name, val in zip(self.NAMES, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+# --------------------------------------------------------------------------- helpers
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _time_fn(torch, fn, reps=20, warm=3):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps / 1e3   # seconds per call
+
+
+def _cpu_baseline(budget_s=10.0):
+    """The oracle (FP64 direct bond sum, OpenMP) on one 1024^2 field, repeated for ~budget_s."""
+    import numpy as np
+    import oracle
+    import synthetic as syn
+    w = syn.large_plate(MH)
+    al = oracle.alpha(2, w.E, w.delta)
+    t0 = time.perf_counter()
+    oracle.force(2, w.n, w.h, w.M, al, w.u)
+    t1 = time.perf_counter() - t0
+    reps = max(1, int(budget_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.force(2, w.n, w.h, w.M, al, w.u)
+    dt = (time.perf_counter() - t0) / reps
+    dof = 2 * w.N
+    return {"value": dof / dt / 1e9, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{reps} x K u on one 1024x1024 field (2.1M DOF), FP64 direct bond sum, "
+                      f"{dt * 1e3:.1f} ms each"}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synthetic as syn
+    w = syn.large_plate(MH)
+    al = oracle.alpha(2, w.E, w.delta)
+    for _ in range(args.warmup):
+        oracle.force(2, w.n, w.h, w.M, al, w.u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.force(2, w.n, w.h, w.M, al, w.u)
+    dt = time.perf_counter() - t0
+    value = 2 * w.N * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "plate2d 1024x1024 delta=3h, K u, one field per step",
+                                            "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": "one 1024x1024 field (2.1M DOF) per step, FP64 direct bond sum"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2301_11828_gb300 as pd
+    import synthetic as syn
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pd.load_library()
+    dev = torch.device("cuda", local)
+
+    # ---- workload: B independent fields on the 1024^2 plate
+    w = syn.large_plate(MH)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+    B = args.batch
+    base = torch.tensor(w.u, dtype=torch.float32, device=dev)
+    U = torch.empty((B,) + base.shape, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2301_11828 + rank)
+    U.uniform_(-1.0, 1.0, generator=gen)
+    U[0].copy_(base)
+    OUT = torch.empty_like(U)
+    flags = pd.PD_F32 | pd.PD_METHOD_STENCIL
+    lib = pd.load_library()
+    stream = torch.cuda.current_stream()
+    sptr = pd._stream(stream)
+    hdl = g.handle
+
+    def step():
+        rc = lib.pd_matvec_batch(hdl, B, pd._dptr(U), pd._dptr(OUT), flags, sptr)
+        if rc:
+            raise pd.PDError(rc, pd.pd_last_error())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.15)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_s, t_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_s.record()
+    for k in range(args.steps):
+        evs[k][0].record()
+        step()
+        evs[k][1].record()
+    t_e.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed = t_s.elapsed_time(t_e) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    dof_step = B * 2 * w.N
+    value = dof_step * args.steps * ws / elapsed / 1e9
+
+    # ---- roofline of the dominant kernel (the stencil launch is the whole step)
+    peak, peak_kind = _peaks()
+    alg_bytes = B * w.N * 2 * 2 * 4          # read u, write K u, FP32, 2 components
+    achieved = alg_bytes / (launch_ms / 1e3) / 1e9
+    traffic = None
+    if TRAFFIC["sha256"] and TRAFFIC["sha256"] == _src_hash(TRAFFIC["sources"]) and TRAFFIC["bytes_per_field"]:
+        traffic = TRAFFIC["bytes_per_field"] * B
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": TRAFFIC["kernel"], "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    Uh = U.cpu().pin_memory()
+    OUTh = torch.empty_like(Uh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step():
+        U.copy_(Uh, non_blocking=True)
+        step()
+        OUTh.copy_(OUT, non_blocking=True)
+
+    e2e_s = _time_fn(torch, e2e_step, reps=e2e_steps, warm=2)
+    e2e = {"value": dof_step / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Uh.numel() * 4,
+           "d2h_bytes_per_step": OUTh.numel() * 4}
+    del Uh, OUTh
+
+    extras = {}
+    if rank == 0 and not args.quick:
+        extras = _extras(torch, pd, syn, dev)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = _cpu_baseline(args.cpu_budget)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"plate2d {NSIDE}x{NSIDE} delta=3h, K u on a batch of {B} fields "
+                                       f"(load cases), one batched launch per step",
+                           "global_batch": B * ws, "dof_per_field": 2 * w.N, "method": "stencil",
+                           "l2": f"no flush: inputs {B * 2 * w.N * 4 / 1e6:.0f} MB > 129 MB L2",
+                           "parallelism": f"replicas x{ws} (independent batches)"},
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+                "cpu_baseline": cpu}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _extras(torch, pd, syn, dev):
+    """Secondary measurements (rank 0): variants, CG, cube, crack loop."""
+    import numpy as np
+    out = {}
+    variants = {}
+    for M in (3, 6):
+        w = syn.large_plate(M)
+        g = pd.Grid(2, w.n, w.h, w.M)
+        for dt, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+            B = 8 if dt == torch.float32 else 4
+            U = torch.rand((B, 2, NSIDE, NSIDE), dtype=dt, device=dev) * 2 - 1
+            O = torch.empty_like(U)
+            for meth, mname in ((pd.PD_METHOD_STENCIL, "stencil"), (pd.PD_METHOD_FFT, "fft")):
+                try:
+                    s = _time_fn(torch, lambda: g.matvec(U, O, flags=meth), reps=10)
+                    variants[f"M{M}_{name}_{mname}"] = round(B * 2 * w.N / s / 1e9, 2)
+                except pd.PDError as e:
+                    variants[f"M{M}_{name}_{mname}"] = None
+            del U, O
+        g.close()
+    out["variants_gdofs"] = variants
+    # autotuned method choice per horizon / precision on the 1024^2 plate
+    tune = {}
+    for M in (3, 6):
+        w = syn.large_plate(M)
+        g = pd.Grid(2, w.n, w.h, w.M)
+        t = g.autotune()
+        tune[f"M{M}"] = {k: round(v, 4) for k, v in t.items()}
+        g.close()
+    out["autotune_ms_per_field"] = tune
+    # static solve on the 1024^2 plate (clamp left, traction right), rtol 1e-8
+    w = syn.large_plate(3)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+    g.autotune()
+    b = torch.tensor(w.b, device=dev)
+    cg = {}
+    for mode, name in ((pd.PD_CG_MIXED, "mixed"), (pd.PD_CG_F64, "f64")):
+        u = torch.zeros_like(b)
+        pd.pd_cg_solve(g.handle, b, u, 1e-8, 64, mode, allow_not_converged=True)   # warm: workspace, graphs
+        u.zero_()
+        torch.cuda.synchronize()
+        st = pd.pd_cg_solve(g.handle, b, u, 1e-8, 400000, mode, allow_not_converged=True)
+        cg[name] = {"seconds": round(st.seconds, 4), "iterations": st.iterations, "outer": st.outer,
+                    "f64_matvecs": st.f64_matvecs, "rel_residual": st.rel_residual}
+    if cg["mixed"]["seconds"] > 0:
+        cg["speedup_mixed_vs_f64"] = round(cg["f64"]["seconds"] / cg["mixed"]["seconds"], 3)
+    out["cg_1024_rtol1e-8"] = cg
+    g.close()
+    # 3D cube 128^3, FP32
+    w = syn.cube(128, 3)
+    g = pd.Grid(3, w.n, w.h, w.M, constrained=w.constrained)
+    U = torch.tensor(w.u, dtype=torch.float32, device=dev)
+    O = torch.empty_like(U)
+    s = _time_fn(torch, lambda: g.matvec(U, O, flags=pd.PD_METHOD_STENCIL), reps=10)
+    out["cube128_f32_gdofs"] = round(3 * w.N / s / 1e9, 2)
+    g.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH)
+    ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

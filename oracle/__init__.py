@@ -82,11 +82,18 @@ def lib():
             L.or_grad_modulus.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           dp, dp, dp, dp]
             L.or_grad_modulus.restype = ctypes.c_int
+            L.or_threads.argtypes = []
+            L.or_threads.restype = ctypes.c_int
             _lib = L
     return _lib
 
 
 # --------------------------------------------------------------------------- helpers
+
+def threads() -> int:
+    """OpenMP threads the oracle's node loops use."""
+    return int(lib().or_threads())
+
 
 def _n64(n):
     arr = (ctypes.c_int64 * 3)(*(list(int(v) for v in n) + [1] * (3 - len(n))))

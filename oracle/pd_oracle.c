@@ -407,3 +407,16 @@ int or_grad_modulus(int dim, const int64_t *n, double h, int M, double alpha1,
     free(blk);
     return 0;
 }
+
+/* Number of threads the OpenMP loops above use (1 without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -67,6 +67,8 @@ SIGNATURES = {
     "pd_step": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats), _VP]),
     "pd_break_bonds": (_I, [_VP, _VP, _U32, ctypes.POINTER(_I64), _VP]),
     "pd_break_segment": (_I, [_VP, ctypes.POINTER(_I64), _I64, ctypes.POINTER(_I64), _VP]),
+    "pd_set_method": (_I, [_VP, _U32]),
+    "pd_autotune": (_I, [_VP, _U32, _VP, _VP]),
     "pd_get_info": (_I, [_VP, ctypes.POINTER(pd_grid_info)]),
     "pd_get_offsets": (_I, [_VP, _VP, _I]),
     "pd_get_bond_mask": (_I, [_VP, _VP, _VP]),
@@ -187,6 +189,16 @@ def pd_break_segment(g, seg, den: int, stream=None) -> int:
     return int(n.value)
 
 
+def pd_set_method(g, method: int):
+    _check(load_library().pd_set_method(g, int(method)))
+
+
+def pd_autotune(g, flags: int = PD_F32 | PD_F64, stream=None):
+    t = (ctypes.c_double * 4)()
+    _check(load_library().pd_autotune(g, int(flags), t, _stream(stream)))
+    return {"stencil_f32_ms": t[0], "fft_f32_ms": t[1], "stencil_f64_ms": t[2], "fft_f64_ms": t[3]}
+
+
 def pd_get_info(g) -> pd_grid_info:
     info = pd_grid_info()
     _check(load_library().pd_get_info(g, ctypes.byref(info)))
@@ -276,6 +288,12 @@ class Grid:
 
     def break_segment(self, seg, den, stream=None) -> int:
         return pd_break_segment(self.handle, seg, den, stream)
+
+    def prefer_method(self, method: int):
+        pd_set_method(self.handle, method)
+
+    def autotune(self, flags: int = PD_F32 | PD_F64, stream=None):
+        return pd_autotune(self.handle, flags, stream)
 
     def offsets(self) -> np.ndarray:
         return pd_get_offsets(self.handle)

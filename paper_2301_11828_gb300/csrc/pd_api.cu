@@ -125,6 +125,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_coef);
     cudaFree(g->d_coef1);
     cudaFree(g->ws);
+    cg_release(g);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     delete g;
 }
@@ -328,6 +329,7 @@ int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s
     rc = upload_coefs(g);
     if (rc) return rc;
     g->auto_choice[0] = g->auto_choice[1] = 0;
+    ++g->op_stamp;
     if (g->d_sym32) return fft_prepare(g);
     return PD_OK;
 }
@@ -345,6 +347,71 @@ int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_
     if (rc) return rc;
     if (batch < 1) return fail(PD_ERR_INVALID, "batch must be >= 1");
     return matvec(g, batch, u, out, flags, (cudaStream_t)stream);
+}
+
+int pd_set_method(pd_grid *g, uint32_t method)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (method == PD_METHOD_AUTO) {
+        g->auto_choice[0] = g->auto_choice[1] = 0;
+    } else if (method == PD_METHOD_STENCIL) {
+        g->auto_choice[0] = g->auto_choice[1] = 1;
+    } else if (method == PD_METHOD_FFT) {
+        if (g->dim != 2 || g->has_E) return fail(PD_ERR_INVALID, "the FFT method needs a 2D grid without a modulus field");
+        g->auto_choice[0] = g->auto_choice[1] = 2;
+    } else {
+        return fail(PD_ERR_INVALID, "method must be PD_METHOD_AUTO, PD_METHOD_STENCIL or PD_METHOD_FFT");
+    }
+    ++g->op_stamp;
+    return PD_OK;
+}
+
+int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!(flags & (PD_F32 | PD_F64))) return fail(PD_ERR_INVALID, "flags must name PD_F32 and/or PD_F64");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (times_ms)
+        for (int i = 0; i < 4; ++i) times_ms[i] = 0.0;
+    const size_t bytes = sizeof(double) * (size_t)g->dim * g->N;
+    void *u = nullptr, *o = nullptr;
+    if (cudaMalloc(&u, bytes) != cudaSuccess || cudaMalloc(&o, bytes) != cudaSuccess) {
+        cudaFree(u);
+        return fail(PD_ERR_OOM, "autotune scratch");
+    }
+    cudaMemsetAsync(u, 0, bytes, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool fft_ok = (g->dim == 2) && !g->has_E;
+    for (int prec = 0; prec < 2 && rc == PD_OK; ++prec) {
+        const uint32_t dt = prec ? PD_F64 : PD_F32;
+        if (!(flags & dt)) continue;
+        float best[2] = {1e30f, 1e30f};
+        for (int m = 0; m < (fft_ok ? 2 : 1) && rc == PD_OK; ++m) {
+            const uint32_t fl = dt | (m ? PD_METHOD_FFT : PD_METHOD_STENCIL) | PD_IGNORE_BROKEN;
+            for (int w = 0; w < 3 && rc == PD_OK; ++w) rc = matvec(g, 1, u, o, fl, s);
+            const int reps = 10;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && rc == PD_OK; ++r) rc = matvec(g, 1, u, o, fl, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best[m] = ms / reps;
+            if (times_ms) times_ms[2 * prec + m] = best[m];
+        }
+        g->auto_choice[prec] = (fft_ok && best[1] < best[0]) ? 2 : 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(u);
+    cudaFree(o);
+    ++g->op_stamp;
+    if (rc) return rc;
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
 }
 
 int pd_get_info(pd_grid *g, pd_grid_info *info)
@@ -409,6 +476,7 @@ int pd_break_bonds(pd_grid *g, const void *u, uint32_t flags, int64_t *n_newly_b
     PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     g->broken_total = (int64_t)g->h_pinned[1];
+    if (g->h_pinned[2]) ++g->op_stamp;
     if (n_newly_broken) *n_newly_broken = (int64_t)g->h_pinned[2];
     return PD_OK;
 }
@@ -431,6 +499,7 @@ int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_b
     PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     g->broken_total = (int64_t)g->h_pinned[1];
+    if (g->h_pinned[2]) ++g->op_stamp;
     if (n_broken) *n_broken = (int64_t)g->h_pinned[2];
     return PD_OK;
 }

@@ -1,7 +1,458 @@
-// pd_cg.cu -- conjugate gradients (placeholder).
-#include "pd_internal.cuh"
+// pd_cg.cu -- conjugate gradients on the projected stiffness P K P u = P b.
+//
+// The paper drives its static problem (Eq. mat:e2) with adaptive dynamic
+// relaxation; this library pairs the same operator with CG, in two modes:
+//
+//  * PD_CG_F64: textbook CG with FP64 vectors and the FP64 operator.
+//  * PD_CG_MIXED: iterative refinement.  The outer loop keeps u in FP64 and
+//    forms the true residual r = P(b - K u) with the FP64 operator; the inner
+//    loop solves K d = r / |r| approximately by CG with FP32 vectors and the
+//    FP32 operator (dot products are reduced in FP64); then u += |r| d.
+//
+// One inner iteration is three launches: (1) q = K p with p.q fused into the
+// stencil epilogue, (2) alpha = rr / pq, x += alpha p, r -= alpha q, r.r
+// reduced in the same kernel, whose last block also forms beta and the
+// convergence flag, (3) p = r + beta p.  All scalars stay on the device; the
+// host only looks at the flag between chunks of iterations, which are captured
+// once into a CUDA graph and replayed.  Every kernel returns early once the
+// flag is set, so iterations after convergence inside a chunk change nothing.
+#include <cuda_runtime.h>
 
-extern "C" int pd_cg_solve(pd_grid *, const double *, double *, double, int, uint32_t, pd_cg_stats *, void *)
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "pd_internal.cuh"
+#include "pd_reduce.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr int kBlk = 256;
+constexpr int kRedBlocks = 152 * 4;   // grid of the streaming kernels (grid-stride)
+constexpr int kChunk = 32;            // inner iterations per graph launch
+
+struct CgScal {
+    double rr;       // r.r of the current iterate
+    double pq;       // p.q, written by the fused matvec dot
+    double rr_new;   // r.r after the update (last block)
+    double tol2;     // inner loop stops when rr <= tol2
+    double beta;
+    double aux;      // scratch for the host-driven reductions
+    int done;
+    int iters;
+    unsigned int retire[4];
+};
+
+// Deterministic grid reduction whose last block returns true in thread 0.
+__device__ __forceinline__ bool grid_last(double block_value, double *partial, double *out, unsigned int *retire,
+                                          double *red)
 {
-    return pd::fail(PD_ERR_INVALID, "CG not built");
+    __shared__ bool s_last;
+    const int nb = gridDim.x, bid = blockIdx.x;
+    if (threadIdx.x == 0) {
+        partial[bid] = block_value;
+        __threadfence();
+        const unsigned int t = atomicAdd(retire, 1u);
+        s_last = (t == (unsigned int)(nb - 1));
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += __ldcg(&partial[i]);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        *out = s;
+        *retire = 0u;
+        return true;
+    }
+    return false;
+}
+
+// x += alpha p ; r -= alpha q ; rr_new = r.r ; last block: beta, rr, done, iters.
+template <typename T>
+__global__ void __launch_bounds__(kBlk)
+k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_t L, CgScal *sc, double *partial)
+{
+    __shared__ double red[kBlk / 32];
+    __shared__ int s_done;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_alpha = (sc->pq != 0.0) ? sc->rr / sc->pq : 0.0;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const T a = (T)s_alpha;
+    T acc = T(0);
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+        const T xi = x[i] + a * p[i];
+        const T ri = r[i] - a * q[i];
+        x[i] = xi;
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    const double bs = block_sum((double)acc, red);
+    if (grid_last(bs, partial, &sc->rr_new, &sc->retire[0], red)) {
+        const double rn = sc->rr_new;
+        sc->beta = (sc->rr > 0.0) ? rn / sc->rr : 0.0;
+        sc->rr = rn;
+        sc->iters += 1;
+        if (!(rn > sc->tol2)) sc->done = 1;   // also stops on NaN
+    }
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void __launch_bounds__(kBlk) k_cg_p(T *p, const T *__restrict__ r, int64_t L, const CgScal *sc)
+{
+    if (sc->done) return;
+    const T beta = (T)sc->beta;
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk)
+        p[i] = r[i] + beta * p[i];
+}
+
+// out = a . b (FP64 accumulation in the kernel's precision per thread)
+template <typename T>
+__global__ void __launch_bounds__(kBlk)
+k_dot(const T *__restrict__ a, const T *__restrict__ b, int64_t L, double *out, double *partial, unsigned int *retire)
+{
+    __shared__ double red[kBlk / 32];
+    T acc = T(0);
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk)
+        acc += a[i] * b[i];
+    const double bs = block_sum((double)acc, red);
+    grid_last(bs, partial, out, retire, red);
+}
+
+// r = P(b - Ku) in FP64, and r.r  (Ku already projected by the matvec)
+__global__ void __launch_bounds__(kBlk)
+k_resid(double *r, const double *__restrict__ b, const double *__restrict__ Ku, const uint8_t *__restrict__ cons,
+        int64_t N, int dim, double *out, double *partial, unsigned int *retire)
+{
+    __shared__ double red[kBlk / 32];
+    double acc = 0.0;
+    const int64_t L = (int64_t)dim * N;
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+        const int c = (int)(i / N);
+        const int64_t p = i - c * N;
+        const bool fixed = cons && ((cons[p] >> c) & 1);
+        const double v = fixed ? 0.0 : b[i] - Ku[i];
+        r[i] = v;
+        acc += v * v;
+    }
+    const double bs = block_sum(acc, red);
+    grid_last(bs, partial, out, retire, red);
+}
+
+// Inner start (mixed): r32 = r64 * inv, p32 = r32, x32 = 0, sc->rr = r32.r32, done flag.
+__global__ void __launch_bounds__(kBlk)
+k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64, int64_t L, double inv, double tau2,
+              CgScal *sc, double *partial)
+{
+    __shared__ double red[kBlk / 32];
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+        const float v = (float)(r64[i] * inv);
+        r32[i] = v;
+        p32[i] = v;
+        x32[i] = 0.f;
+        acc += v * v;
+    }
+    const double bs = block_sum((double)acc, red);
+    if (grid_last(bs, partial, &sc->rr, &sc->retire[1], red)) {
+        sc->tol2 = tau2 * sc->rr;
+        sc->done = (sc->rr > sc->tol2) ? 0 : 1;
+        sc->iters = 0;
+    }
+}
+
+// Plain start (FP64): p = r, sc->rr = rr (given on device in sc->aux), tol2, done.
+__global__ void __launch_bounds__(kBlk)
+k_plain_start(double *p, const double *__restrict__ r, int64_t L, double tol2, CgScal *sc)
+{
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) p[i] = r[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->rr = sc->aux;
+        sc->tol2 = tol2;
+        sc->done = (sc->rr > tol2) ? 0 : 1;
+        sc->iters = 0;
+    }
+}
+
+// u += s * x32 on free components (constrained components stay 0).
+__global__ void __launch_bounds__(kBlk)
+k_correct(double *u, const float *__restrict__ x32, double s, int64_t L)
+{
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk)
+        u[i] += s * (double)x32[i];
+}
+
+__global__ void __launch_bounds__(kBlk)
+k_zero_constrained(double *u, const uint8_t *__restrict__ cons, int64_t N, int dim)
+{
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < (int64_t)dim * N; i += (int64_t)gridDim.x * kBlk) {
+        const int c = (int)(i / N);
+        if ((cons[i - c * N] >> c) & 1) u[i] = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ workspace
+struct CgWs {
+    size_t bytes = 0;
+    void *base = nullptr;
+    double *r64, *q64, *p64;    // FP64 residual, operator output, direction
+    float *r32, *p32, *q32, *x32;
+    CgScal *sc;
+    double *partial;            // >= max(kRedBlocks, stencil CTAs) doubles
+    double *partial2;
+    cudaStream_t cap = nullptr; // capture stream
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [0] FP32 inner, [1] FP64 plain
+    const void *graph_key[2] = {nullptr, nullptr};
+    int64_t graph_stamp[2] = {-1, -1};
+};
+
+int ensure_ws(pd_grid *g, CgWs *&w)
+{
+    const int64_t L = (int64_t)g->dim * g->N;
+    const int nblk = std::max(stencil_blocks(g, true, g->has_E || g->broken_total > 0),
+                              stencil_blocks(g, false, g->has_E || g->broken_total > 0));
+    const size_t nparts = (size_t)std::max(nblk, kRedBlocks) + 64;
+    const size_t need = sizeof(double) * 3 * L + sizeof(float) * 4 * L + sizeof(CgScal) + 2 * sizeof(double) * nparts + 1024;
+    w = (CgWs *)g->cg;
+    if (w && w->bytes >= need) return PD_OK;
+    if (!w) {
+        w = new CgWs();
+        g->cg = w;
+        PD_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+    }
+    if (w->base) cudaFree(w->base);
+    for (int i = 0; i < 2; ++i)
+        if (w->graph[i]) {
+            cudaGraphExecDestroy(w->graph[i]);
+            w->graph[i] = nullptr;
+        }
+    w->base = nullptr;
+    w->bytes = 0;
+    if (cudaMalloc(&w->base, need) != cudaSuccess) return fail(PD_ERR_OOM, "CG workspace");
+    w->bytes = need;
+    char *c = (char *)w->base;
+    auto take = [&](size_t n) { char *q = c; c += (n + 255) & ~(size_t)255; return q; };
+    w->r64 = (double *)take(sizeof(double) * L);
+    w->q64 = (double *)take(sizeof(double) * L);
+    w->p64 = (double *)take(sizeof(double) * L);
+    w->r32 = (float *)take(sizeof(float) * L);
+    w->p32 = (float *)take(sizeof(float) * L);
+    w->q32 = (float *)take(sizeof(float) * L);
+    w->x32 = (float *)take(sizeof(float) * L);
+    w->sc = (CgScal *)take(sizeof(CgScal));
+    w->partial = (double *)take(sizeof(double) * nparts);
+    w->partial2 = (double *)take(sizeof(double) * nparts);
+    PD_CUDA(cudaMemset(w->sc, 0, sizeof(CgScal)));
+    return PD_OK;
+}
+
+// One inner iteration on FP32 (mixed) or FP64 (plain) vectors.
+int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s)
+{
+    const int64_t L = (int64_t)g->dim * g->N;
+    const bool fuse = !(g->broken_total > 0 && !g->has_E);
+    const uint32_t fl = (f64 ? PD_F64 : PD_F32) | PD_PROJECT;
+    void *p = f64 ? (void *)w->p64 : (void *)w->p32;
+    void *q = f64 ? (void *)w->q64 : (void *)w->q32;
+    int rc;
+    if (fuse) {
+        rc = matvec(g, 1, p, q, fl, s, w->partial, &w->sc->pq, &w->sc->retire[2]);
+    } else {
+        rc = matvec(g, 1, p, q, fl, s);
+        if (rc == PD_OK) {
+            if (f64) k_dot<double><<<kRedBlocks, kBlk, 0, s>>>(w->p64, w->q64, L, &w->sc->pq, w->partial2, &w->sc->retire[3]);
+            else k_dot<float><<<kRedBlocks, kBlk, 0, s>>>(w->p32, w->q32, L, &w->sc->pq, w->partial2, &w->sc->retire[3]);
+        }
+    }
+    if (rc) return rc;
+    if (f64) {
+        k_cg_update<double><<<kRedBlocks, kBlk, 0, s>>>(x64, w->r64, w->p64, w->q64, L, w->sc, w->partial2);
+        k_cg_p<double><<<kRedBlocks, kBlk, 0, s>>>(w->p64, w->r64, L, w->sc);
+    } else {
+        k_cg_update<float><<<kRedBlocks, kBlk, 0, s>>>(w->x32, w->r32, w->p32, w->q32, L, w->sc, w->partial2);
+        k_cg_p<float><<<kRedBlocks, kBlk, 0, s>>>(w->p32, w->r32, L, w->sc);
+    }
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+// Runs inner iterations until the device flag is set or `budget` iterations
+// were issued.  Chunks of kChunk iterations run as one captured graph.
+int inner_loop(pd_grid *g, CgWs *w, bool f64, double *x64, int budget, cudaStream_t s, int *done_iters)
+{
+    const int gi = f64 ? 1 : 0;
+    // one plain iteration first: sets kernel attributes outside any capture
+    int issued = 0;
+    int rc = iteration(g, w, f64, x64, s);
+    if (rc) return rc;
+    ++issued;
+    const void *key = x64;
+    if (!w->graph[gi] || w->graph_key[gi] != key || w->graph_stamp[gi] != g->op_stamp) {
+        if (w->graph[gi]) {
+            cudaGraphExecDestroy(w->graph[gi]);
+            w->graph[gi] = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            for (int i = 0; i < kChunk && ok; ++i) ok = (iteration(g, w, f64, x64, w->cap) == PD_OK);
+            ok = (cudaStreamEndCapture(w->cap, &graph) == cudaSuccess) && ok;
+        }
+        if (ok && cudaGraphInstantiate(&w->graph[gi], graph, 0) != cudaSuccess) {
+            w->graph[gi] = nullptr;
+            ok = false;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        w->graph_key[gi] = key;
+        w->graph_stamp[gi] = g->op_stamp;
+    }
+    volatile CgScal *hs = (volatile CgScal *)g->h_pinned;
+    while (issued < budget) {
+        const int n = std::min(kChunk, budget - issued);
+        if (w->graph[gi] && n == kChunk) {
+            PD_CUDA(cudaGraphLaunch(w->graph[gi], s));
+        } else {
+            for (int i = 0; i < n; ++i) {
+                rc = iteration(g, w, f64, x64, s);
+                if (rc) return rc;
+            }
+        }
+        issued += n;
+        PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, s));
+        PD_CUDA(cudaStreamSynchronize(s));
+        if (hs->done) break;
+    }
+    PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    *done_iters = hs->iters;
+    return hs->done ? PD_OK : PD_ERR_NOT_CONVERGED;
+}
+
+// r64 = P(b - K u) with the FP64 operator; returns |r|^2 on the host.
+int true_residual(pd_grid *g, CgWs *w, const double *b, const double *u, cudaStream_t s, double *rr)
+{
+    const int64_t L = (int64_t)g->dim * g->N;
+    int rc = matvec(g, 1, u, w->q64, PD_F64 | PD_PROJECT, s);
+    if (rc) return rc;
+    k_resid<<<kRedBlocks, kBlk, 0, s>>>(w->r64, b, w->q64, g->has_cons ? g->d_cons : nullptr, g->N, g->dim,
+                                        &w->sc->aux, w->partial2, &w->sc->retire[3]);
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaMemcpyAsync(g->h_pinned, &w->sc->aux, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    *rr = *(volatile double *)g->h_pinned;
+    (void)L;
+    return PD_OK;
+}
+
+}  // namespace
+
+void cg_release(pd_grid *g)
+{
+    CgWs *w = (CgWs *)g->cg;
+    if (!w) return;
+    for (int i = 0; i < 2; ++i)
+        if (w->graph[i]) cudaGraphExecDestroy(w->graph[i]);
+    if (w->base) cudaFree(w->base);
+    if (w->cap) cudaStreamDestroy(w->cap);
+    delete w;
+    g->cg = nullptr;
+}
+
+}  // namespace pd
+
+using namespace pd;
+
+extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter, uint32_t mode,
+                           pd_cg_stats *stats, void *stream)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (!b || !u) return fail(PD_ERR_INVALID, "b and u must be device pointers");
+    if (!(rtol > 0) || max_iter < 1) return fail(PD_ERR_INVALID, "rtol > 0 and max_iter >= 1 required");
+    if (mode != PD_CG_F64 && mode != PD_CG_MIXED) return fail(PD_ERR_INVALID, "mode must be PD_CG_F64 or PD_CG_MIXED");
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    CgWs *w = nullptr;
+    int rc = ensure_ws(g, w);
+    if (rc) return rc;
+    const int64_t L = (int64_t)g->dim * g->N;
+    const int blocks = kRedBlocks;
+    if (g->has_cons) k_zero_constrained<<<blocks, kBlk, 0, s>>>(u, g->d_cons, g->N, g->dim);
+
+    // |P b|^2
+    double bb = 0.0;
+    {
+        PD_CUDA(cudaMemsetAsync(w->q64, 0, sizeof(double) * L, s));
+        k_resid<<<blocks, kBlk, 0, s>>>(w->r64, b, w->q64, g->has_cons ? g->d_cons : nullptr, g->N, g->dim,
+                                        &w->sc->aux, w->partial2, &w->sc->retire[3]);
+        PD_CUDA(cudaMemcpyAsync(g->h_pinned, &w->sc->aux, sizeof(double), cudaMemcpyDeviceToHost, s));
+        PD_CUDA(cudaStreamSynchronize(s));
+        bb = *(volatile double *)g->h_pinned;
+    }
+    const double bnorm = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
+    int total_iters = 0, outer = 0, f64mv = 0;
+    double rel = 0.0;
+    int status = PD_ERR_NOT_CONVERGED;
+
+    if (mode == PD_CG_F64) {
+        for (int restart = 0; restart < 4; ++restart) {
+            double rr;
+            rc = true_residual(g, w, b, u, s, &rr);
+            if (rc) return rc;
+            ++f64mv;
+            rel = std::sqrt(rr) / bnorm;
+            if (rel <= rtol) { status = PD_OK; break; }
+            if (total_iters >= max_iter) break;
+            ++outer;
+            *(volatile double *)g->h_pinned = rr;
+            PD_CUDA(cudaMemcpyAsync(&w->sc->aux, g->h_pinned, sizeof(double), cudaMemcpyHostToDevice, s));
+            k_plain_start<<<blocks, kBlk, 0, s>>>(w->p64, w->r64, L, rtol * rtol * bb * 0.25, w->sc);
+            int it = 0;
+            rc = inner_loop(g, w, true, u, max_iter - total_iters, s, &it);
+            total_iters += it;
+            f64mv += it;
+            if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
+        }
+    } else {
+        for (int o = 0; o < 60; ++o) {
+            double rr;
+            rc = true_residual(g, w, b, u, s, &rr);
+            if (rc) return rc;
+            ++f64mv;
+            rel = std::sqrt(rr) / bnorm;
+            if (rel <= rtol) { status = PD_OK; break; }
+            if (total_iters >= max_iter || !std::isfinite(rel)) break;
+            ++outer;
+            const double rn = std::sqrt(rr);
+            // inner target: the reduction still needed (with margin), but not below FP32 reach
+            const double need = 0.3 * rtol * bnorm / rn;
+            const double tau = std::min(0.5, std::max(need, 2e-5));
+            k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->r64, L, 1.0 / rn, tau * tau, w->sc,
+                                                  w->partial2);
+            int it = 0;
+            rc = inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it);
+            total_iters += it;
+            if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
+            k_correct<<<blocks, kBlk, 0, s>>>(u, w->x32, rn, L);
+            PD_CUDA(cudaGetLastError());
+        }
+    }
+    PD_CUDA(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->iterations = total_iters;
+        stats->outer = outer;
+        stats->f64_matvecs = f64mv;
+        stats->rel_residual = rel;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status != PD_OK) return fail(PD_ERR_NOT_CONVERGED, "CG reached its iteration cap");
+    return PD_OK;
 }

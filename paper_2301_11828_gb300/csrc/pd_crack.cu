@@ -370,6 +370,7 @@ int refresh_broken_nodes(pd_grid *g, cudaStream_t s)
     PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 2, cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     g->broken_total = (int64_t)g->h_pinned[1];
+    ++g->op_stamp;
     return PD_OK;
 }
 
@@ -429,6 +430,7 @@ extern "C" int pd_step(pd_grid *g, double *u, double *v, const double *b, int ns
     PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     g->broken_total = (int64_t)g->h_pinned[1];
+    if (g->h_pinned[2]) ++g->op_stamp;
     if (stats) {
         stats->steps = nsteps;
         stats->newly_broken = (int64_t)g->h_pinned[2];

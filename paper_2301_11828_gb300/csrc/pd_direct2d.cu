@@ -101,7 +101,7 @@ k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
             }
         });
     });
-    double dot = 0.0;
+    T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int gy = y0 + ty * R + r;
@@ -117,11 +117,11 @@ k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
             fy *= scale;
             ob[p] = fx;
             ob[N + p] = fy;
-            dot += (double)upx[r] * (double)fx + (double)upy[r] * (double)fy;
+            dot = dfma(upx[r], fx, dfma(upy[r], fy, dot));
         }
     }
     if (dot_partial)
-        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
+        finish_block_dot((double)dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
                          blockIdx.x + gridDim.x * blockIdx.y, b);
 }
 

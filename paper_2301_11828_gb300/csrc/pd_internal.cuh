@@ -110,6 +110,9 @@ struct pd_grid {
 
     // measured method choice cache: [dtype 0/1] -> 0 unknown, 1 stencil, 2 fft
     int auto_choice[2] = {0, 0};
+
+    void *cg = nullptr;        // CG workspace and captured graphs (pd_cg.cu)
+    int64_t op_stamp = 0;      // bumped whenever the operator changes (material, bond state)
 };
 
 namespace pd {
@@ -150,6 +153,7 @@ int launch_grad_modulus(pd_grid *g, const double *u, const double *lam, double s
 // always run the broken-bond correction (it reads the device-side count).
 constexpr uint32_t kForceMu = 0x80000000u;
 int upload_coefs(pd_grid *g);
+void cg_release(pd_grid *g);
 int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, cudaStream_t s,
            double *dot_partial = nullptr, double *dot_out = nullptr, unsigned int *retire = nullptr,
            double scale = 1.0);

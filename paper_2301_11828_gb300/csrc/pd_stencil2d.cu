@@ -104,7 +104,7 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
         }
     });
 
-    double dot = 0.0;
+    T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
     const int gx = x0 + tx;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -131,11 +131,11 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
             fy *= scale;
             ob[p] = fx;
             ob[N + p] = fy;
-            dot += (double)upx * (double)fx + (double)upy * (double)fy;
+            dot = dfma(upx, fx, dfma(upy, fy, dot));
         }
     }
     if (dot_partial)
-        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
+        finish_block_dot((double)dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
                          blockIdx.x + gridDim.x * blockIdx.y, b);
 }
 

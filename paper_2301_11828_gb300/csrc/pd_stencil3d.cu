@@ -116,7 +116,7 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
         }
     }
 
-    double dot = 0.0;
+    T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
     const int gx = x0 + tx, gy = y0 + ty;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -154,11 +154,11 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
             ob[p] = f0;
             ob[N + p] = f1;
             ob[2 * N + p] = f2;
-            dot += (double)u0 * f0 + (double)u1 * f1 + (double)u2 * f2;
+            dot = dfma(u0, f0, dfma(u1, f1, dfma(u2, f2, dot)));
         }
     }
     if (dot_partial)
-        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y * nzt,
+        finish_block_dot((double)dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y * nzt,
                          blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zt), b);
 }
 
