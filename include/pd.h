@@ -141,6 +141,26 @@ int pd_step(pd_grid *g, double *u, double *v, const double *b, int nsteps, doubl
             const double *v_prescribed, int32_t *break_step, int32_t step_base,
             pd_step_stats *stats, void *stream);
 
+/* pd_step without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library call cudaMalloc --
+ * code running while a CUDA graph is being captured (an allocation there is
+ * not recorded and may fail), services whose device memory is owned by their
+ * own pool or caching allocator (a foreign cudaMalloc can fail or fragment
+ * it), and real-time loops where the implicit synchronisation of cudaMalloc
+ * would stall the stream.  Same arguments and results as pd_step.
+ * Its two work vectors live in one fixed array of 2^20 doubles (8 MiB) that
+ * the library defines in device memory; every GPU that loads the library holds
+ * it until the process exits.  Limit: dim * N <= 524288 (a 512 x 512 plate in
+ * 2D); larger grids get PD_ERR_INVALID with a message naming the limit.  The
+ * first call on each device looks the array's address up; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other threads, other grids) race on it
+ * and must be serialised by the caller.  The grid itself must have been
+ * created beforehand (pd_create_grid allocates). */
+int pd_step_noalloc(pd_grid *g, double *u, double *v, const double *b, int nsteps, double dt,
+                    const double *v_prescribed, int32_t *break_step, int32_t step_base,
+                    pd_step_stats *stats, void *stream);
+
 /* One breaking pass: every intact bond with stretch s >= s0 (Eq. fra:s1,
  * evaluated in FP64 as X = xi + (u_q - u_p), s = (|X| - |xi|)/|xi|, xi = h o,
  * no contraction) is broken in both directions.  u: DEVICE [dim][N] of the

@@ -65,6 +65,8 @@ SIGNATURES = {
     "pd_matvec_batch": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
     "pd_cg_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
     "pd_step": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats), _VP]),
+    "pd_step_noalloc": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats),
+                             _VP]),
     "pd_break_bonds": (_I, [_VP, _VP, _U32, ctypes.POINTER(_I64), _VP]),
     "pd_break_segment": (_I, [_VP, ctypes.POINTER(_I64), _I64, ctypes.POINTER(_I64), _VP]),
     "pd_set_method": (_I, [_VP, _U32]),
@@ -173,6 +175,18 @@ def pd_step(g, u, v, b, nsteps: int, dt: float, v_prescribed=None, break_step=No
                                   int(nsteps), float(dt), _dptr(v_prescribed, torch.float64),
                                   _dptr(break_step, torch.int32), int(step_base), ctypes.byref(st),
                                   _stream(stream)))
+    return st
+
+
+def pd_step_noalloc(g, u, v, b, nsteps: int, dt: float, v_prescribed=None, break_step=None, step_base: int = 0,
+                    stream=None):
+    """pd_step without device allocation (fixed internal scratch; dim * N <= 524288)."""
+    import torch
+    st = pd_step_stats()
+    _check(load_library().pd_step_noalloc(g, _dptr(u, torch.float64), _dptr(v, torch.float64),
+                                          _dptr(b, torch.float64), int(nsteps), float(dt),
+                                          _dptr(v_prescribed, torch.float64), _dptr(break_step, torch.int32),
+                                          int(step_base), ctypes.byref(st), _stream(stream)))
     return st
 
 

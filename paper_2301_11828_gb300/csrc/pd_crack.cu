@@ -16,6 +16,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
+#include <string>
 
 #include "pd_internal.cuh"
 
@@ -416,6 +418,90 @@ extern "C" int pd_step(pd_grid *g, double *u, double *v, const double *b, int ns
     PD_CUDA(cudaMemsetAsync(g->d_count + 2, 0, sizeof(unsigned long long), s));
     // f = A(mu) u = -K u at the incoming state, a = (f + b) / rho
     int rc = matvec(g, 1, u, f, mflags, s, nullptr, nullptr, nullptr, -1.0);
+    if (rc) return rc;
+    k_kick<<<blocks, kBlk, 0, s>>>(v, a, f, b, v_prescribed, cons, g->N, g->dim, dt, 1.0 / g->rho, 1);
+    for (int st = 0; st < nsteps; ++st) {
+        k_drift<<<blocks, kBlk, 0, s>>>(u, v, a, v_prescribed, cons, g->N, g->dim, dt);
+        rc = launch_break(g, u, true, break_step, step_base + st + 1, s);
+        if (rc) return rc;
+        rc = matvec(g, 1, u, f, mflags, s, nullptr, nullptr, nullptr, -1.0);
+        if (rc) return rc;
+        k_kick<<<blocks, kBlk, 0, s>>>(v, a, f, b, v_prescribed, cons, g->N, g->dim, dt, 1.0 / g->rho, 0);
+    }
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaMemcpyAsync(g->h_pinned, g->d_count, sizeof(unsigned long long) * 3, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    g->broken_total = (int64_t)g->h_pinned[1];
+    if (g->h_pinned[2]) ++g->op_stamp;
+    if (stats) {
+        stats->steps = nsteps;
+        stats->newly_broken = (int64_t)g->h_pinned[2];
+        stats->broken_total = g->broken_total;
+    }
+    return PD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pd_step_noalloc: the velocity-Verlet loop of pd_step without any device
+// allocation.  pd_step keeps its two work vectors (acceleration and force) in
+// a buffer it cudaMallocs on first use; some callers cannot let a library do
+// that (see pd.h).  This variant keeps the two vectors in the file-scope array
+// below instead: 2^20 doubles (8 MiB), which every GPU that loads the library
+// holds until the process exits, so dim * N may be at most 2^19
+// (a 512 x 512 plate in 2D).
+namespace pd {
+namespace {
+
+constexpr size_t kNoAllocDoubles = (size_t)1 << 20;
+static __device__ __align__(256) double g_step_scratch[kNoAllocDoubles];
+
+// The array's name is only a host-side stand-in in host code; its device
+// address is looked up once per device with that device current.
+std::mutex g_scratch_mu;
+double *g_scratch_addr[64] = {};
+
+int step_scratch(double **out)
+{
+    int dev = -1;
+    PD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(PD_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_step_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PD_ERR_CUDA, std::string("cudaGetSymbolAddress(step scratch): ") + cudaGetErrorString(e));
+        g_scratch_addr[dev] = (double *)p;
+    }
+    *out = g_scratch_addr[dev];
+    return PD_OK;
+}
+
+}  // namespace
+}  // namespace pd
+
+extern "C" int pd_step_noalloc(pd_grid *g, double *u, double *v, const double *b, int nsteps, double dt,
+                               const double *v_prescribed, int32_t *break_step, int32_t step_base,
+                               pd_step_stats *stats, void *stream)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (!u || !v) return fail(PD_ERR_INVALID, "u and v must be device pointers");
+    if (nsteps < 0 || !(dt > 0)) return fail(PD_ERR_INVALID, "nsteps >= 0 and dt > 0 required");
+    const int64_t L = (int64_t)g->dim * g->N;
+    if ((size_t)(2 * L) > kNoAllocDoubles)
+        return fail(PD_ERR_INVALID, "pd_step_noalloc: dim * N = " + std::to_string(L) +
+                                        " exceeds its fixed scratch (dim * N <= 524288); use pd_step");
+    double *scratch = nullptr;
+    int rc = step_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *a = scratch;       // both vectors are written in full before they are read
+    double *f = scratch + L;
+    const uint8_t *cons = g->has_cons ? g->d_cons : nullptr;
+    const int blocks = grid_blocks(L);
+    const uint32_t mflags = PD_F64 | PD_METHOD_STENCIL | kForceMu;
+    PD_CUDA(cudaMemsetAsync(g->d_count + 2, 0, sizeof(unsigned long long), s));
+    rc = matvec(g, 1, u, f, mflags, s, nullptr, nullptr, nullptr, -1.0);
     if (rc) return rc;
     k_kick<<<blocks, kBlk, 0, s>>>(v, a, f, b, v_prescribed, cons, g->N, g->dim, dt, 1.0 / g->rho, 1);
     for (int st = 0; st < nsteps; ++st) {
