@@ -38,8 +38,8 @@ BATCH = 32          # 32 fields x 2 comps x 1M nodes x 4 B = 268 MB of inputs (>
 # DRAM traffic of the dominant kernel per launch (ncu, dram__bytes_read.sum + dram__bytes_write.sum),
 # recorded with the hash of the kernel sources it was taken on; reported only while they match.
 TRAFFIC = {
-    "kernel": "k_tbt2d<float,3>",
-    "sources": ["paper_2301_11828_gb300/csrc/pd_stencil2d.cu", "paper_2301_11828_gb300/csrc/pd_stencil.cuh",
+    "kernel": "k_tbt2d_tma<3>",
+    "sources": ["paper_2301_11828_gb300/csrc/pd_stencil2d_tma.cu", "paper_2301_11828_gb300/csrc/pd_stencil.cuh",
                 "paper_2301_11828_gb300/csrc/pd_reduce.cuh"],
     "sha256": None,
     "bytes_per_field": None,
@@ -316,7 +316,10 @@ def _extras(torch, pd, syn, dev):
             B = 8 if dt == torch.float32 else 4
             U = torch.rand((B, 2, NSIDE, NSIDE), dtype=dt, device=dev) * 2 - 1
             O = torch.empty_like(U)
-            for meth, mname in ((pd.PD_METHOD_STENCIL, "stencil"), (pd.PD_METHOD_FFT, "fft")):
+            for meth, mname in ((pd.PD_METHOD_STENCIL, "stencil"), (pd.PD_METHOD_STENCIL | pd.PD_NO_TMA, "stencil_plain"),
+                                (pd.PD_METHOD_FFT, "fft")):
+                if name == "f64" and mname == "stencil_plain":
+                    continue
                 try:
                     s = _time_fn(torch, lambda: g.matvec(U, O, flags=meth), reps=10)
                     variants[f"M{M}_{name}_{mname}"] = round(B * 2 * w.N / s / 1e9, 2)

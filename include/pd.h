@@ -59,6 +59,7 @@ typedef enum {
 #define PD_METHOD_FFT     0x20u  /* TBT part by FFT with the symbol product fused (Algorithms 3/4) */
 #define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
+#define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
 
 /* ---- modes for pd_cg_solve ---- */
 #define PD_CG_F64   0x1u  /* plain CG, FP64 vectors and FP64 matvec */
@@ -73,6 +74,7 @@ typedef struct {
     int64_t N;        /* number of nodes */
     double h, delta, alpha;  /* spacing, horizon, micromodulus constant at the set modulus */
     int64_t n_broken_nodes;  /* nodes with at least one broken bond (Omega_br) */
+    int32_t device_error;    /* nonzero once a bounded device-side wait ran out (PD_ERR_TIMEOUT cause) */
 } pd_grid_info;
 
 typedef struct {

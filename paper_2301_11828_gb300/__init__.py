@@ -28,6 +28,7 @@ PD_METHOD_STENCIL = 0x10
 PD_METHOD_FFT = 0x20
 PD_PROJECT = 0x100
 PD_IGNORE_BROKEN = 0x200
+PD_NO_TMA = 0x400
 PD_CG_F64 = 0x1
 PD_CG_MIXED = 0x2
 
@@ -44,7 +45,8 @@ class PDError(RuntimeError):
 class pd_grid_info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("M", ctypes.c_int), ("nnb", ctypes.c_int), ("mask_words", ctypes.c_int),
                 ("n", ctypes.c_int64 * 3), ("N", ctypes.c_int64), ("h", ctypes.c_double),
-                ("delta", ctypes.c_double), ("alpha", ctypes.c_double), ("n_broken_nodes", ctypes.c_int64)]
+                ("delta", ctypes.c_double), ("alpha", ctypes.c_double), ("n_broken_nodes", ctypes.c_int64),
+                ("device_error", ctypes.c_int32)]
 
 
 class pd_cg_stats(ctypes.Structure):

@@ -117,6 +117,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_brlist);
     cudaFree(g->d_brflag);
     cudaFree(g->d_count);
+    cudaFree(g->d_err);
     cudaFree(g->d_kd64);
     cudaFree(g->d_kd32);
     cudaFree(g->d_sym64);
@@ -176,6 +177,8 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
     a.out = out;
     a.batch = batch;
     a.project = (flags & PD_PROJECT) && g->has_cons;
+    a.input_projected = (flags & kInputProjected) != 0;
+    a.no_tma = (flags & PD_NO_TMA) != 0;
     a.scale = scale;
 
     if (g->has_E) {
@@ -272,6 +275,8 @@ int pd_create_grid(int dim, const int64_t n[3], double h, double delta, const ui
     if (cudaMemset(g->d_count, 0, sizeof(unsigned long long) * 8) != cudaSuccess)
         return bail(PD_ERR_CUDA, "counters");
     if (cudaMallocHost(&g->h_pinned, 4096) != cudaSuccess) return bail(PD_ERR_OOM, "pinned mailbox");
+    if (cudaMalloc(&g->d_err, sizeof(int)) != cudaSuccess) return bail(PD_ERR_OOM, "error word");
+    if (cudaMemset(g->d_err, 0, sizeof(int)) != cudaSuccess) return bail(PD_ERR_CUDA, "error word");
     if (constrained) {
         std::vector<uint8_t> bits((size_t)N, 0);
         bool any = false;
@@ -431,6 +436,9 @@ int pd_get_info(pd_grid *g, pd_grid_info *info)
     unsigned long long cnt = 0;
     PD_CUDA(cudaMemcpy(&cnt, g->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
     info->n_broken_nodes = (int64_t)cnt;
+    int derr = 0;
+    PD_CUDA(cudaMemcpy(&derr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    info->device_error = derr;
     return PD_OK;
 }
 

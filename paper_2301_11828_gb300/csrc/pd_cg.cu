@@ -259,7 +259,7 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s)
 {
     const int64_t L = (int64_t)g->dim * g->N;
     const bool fuse = !(g->broken_total > 0 && !g->has_E);
-    const uint32_t fl = (f64 ? PD_F64 : PD_F32) | PD_PROJECT;
+    const uint32_t fl = (f64 ? PD_F64 : PD_F32) | PD_PROJECT | kInputProjected;
     void *p = f64 ? (void *)w->p64 : (void *)w->p32;
     void *q = f64 ? (void *)w->q64 : (void *)w->q32;
     int rc;

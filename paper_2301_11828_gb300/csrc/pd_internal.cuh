@@ -96,6 +96,7 @@ struct pd_grid {
     double *d_coef = nullptr;       // [nnb][ncoef] bond blocks at the current modulus
     double *d_coef1 = nullptr;      // [nnb][ncoef] bond blocks at E = 1
     unsigned long long *d_count = nullptr;   // [0] |Omega_br|, [1] broken total, [2] newly broken (scratch)
+    int *d_err = nullptr;                     // device-side error word (bounded waits that ran out)
     double *d_kd64 = nullptr;
     float *d_kd32 = nullptr;
     double *d_sym64 = nullptr;
@@ -112,6 +113,7 @@ struct pd_grid {
     int auto_choice[2] = {0, 0};
 
     void *cg = nullptr;        // CG workspace and captured graphs (pd_cg.cu)
+    bool no_tma = false;       // use the plain FP32 stencil instead of the TMA-fed one
     int64_t op_stamp = 0;      // bumped whenever the operator changes (material, bond state)
 };
 
@@ -125,6 +127,8 @@ struct MatvecArgs {
     bool project;         // P K P
     bool use_mu;          // honour the bond mask inline (direct form)
     bool use_E;           // per-node modulus (direct form)
+    bool input_projected; // the caller guarantees P u = u (skip the input projection)
+    bool no_tma;          // force the plain FP32 2D stencil
     double scale;         // multiplies the whole operator (1 = K u)
     // optional fused reduction: dot_out[b] = sum_p in . out (FP64), needs scratch
     double *dot_partial;  // [gridDim.x * gridDim.y] per batch
@@ -133,6 +137,8 @@ struct MatvecArgs {
 };
 int launch_stencil(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);
 int stencil_blocks(pd_grid *g, bool f64, bool direct);   // CTAs per field (for sizing partials)
+bool tma_stencil_eligible(const pd_grid *g, const MatvecArgs &a, bool f64);
+int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers (pd_fft.cu)
 int launch_fft_tile(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);
@@ -152,6 +158,8 @@ int launch_grad_modulus(pd_grid *g, const double *u, const double *lam, double s
 // Internal flag: bonds may have broken on the device since the host last looked;
 // always run the broken-bond correction (it reads the device-side count).
 constexpr uint32_t kForceMu = 0x80000000u;
+// Internal flag: the input already satisfies P u = u (the CG keeps its vectors projected).
+constexpr uint32_t kInputProjected = 0x40000000u;
 int upload_coefs(pd_grid *g);
 void cg_release(pd_grid *g);
 int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, cudaStream_t s,

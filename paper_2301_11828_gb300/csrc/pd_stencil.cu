@@ -23,7 +23,11 @@ void coef_of(const pd_grid *g, int ox, int oy, int oz, bool unit, double *c)
 int launch_stencil(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s)
 {
     if (a.batch < 1 || a.batch > 65535) return fail(PD_ERR_INVALID, "batch must be in [1, 65535]");
-    if (g->dim == 2) return (a.use_E || a.use_mu) ? run_direct2d(g, f64, a, s) : run_tbt2d(g, f64, a, s);
+    if (g->dim == 2) {
+        if (a.use_E || a.use_mu) return run_direct2d(g, f64, a, s);
+        if (!g->no_tma && !a.no_tma && tma_stencil_eligible(g, a, f64)) return run_tbt2d_tma(g, a, s);
+        return run_tbt2d(g, f64, a, s);
+    }
     return run_tbt3d(g, f64, a, s);
 }
 

@@ -1,0 +1,392 @@
+// pd_stencil2d_tma.cu -- FP32 2D stencil (TBT form, Sec. 3.2-3.4) for sm_103a:
+// persistent CTAs, TMA-fed double-buffered halo tiles, packed FP32x2 math.
+//
+// Same operator as pd_stencil2d.cu:
+//     (K u)_p = Kd_p u_p - sum_{o in half} c(o) (u~_{p+o} + u~_{p-o}),
+// with u~ zero outside the grid.  Differences in how it is computed:
+//   * The halo box of a tile (both components) is fetched by one
+//     cp.async.bulk.tensor (TMA) per tile into shared memory.  The tensor
+//     map's out-of-bounds fill supplies the zero padding outside the grid, so
+//     no thread tests bounds on the way in.  While a CTA computes one tile the
+//     TMA engine already loads the next one into the other buffer; an mbarrier
+//     with an expected byte count signals arrival.  Every wait has an
+//     iteration limit; on expiry the kernel records an error code and returns.
+//   * The x start of the box is rounded down to a 16-byte boundary (TMA rule)
+//     and the box is widened to cover the halo.
+//   * For each offset pair the two components are handled as one packed
+//     FP32x2 value s = (s_x, s_y): the accumulators a1 += (cxx, cyy) * s and
+//     a2 += (cxy, cxy) * s give (K u) after the final swap
+//     a_x = a1.x + a2.y, a_y = a1.y + a2.x -- one packed add and two packed
+//     fused multiply-adds per pair instead of six scalar instructions.
+// Used for FP32 grids whose row length is a multiple of 4 floats (TMA stride
+// rule); other grids use the plain kernel.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "pd_stencil.cuh"
+
+namespace pd {
+
+namespace {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk(float a, float b)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk(u64 r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b)
+{
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((const void *)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr int kTXt = 64;                 // outputs per tile along x
+constexpr int kRt = 8;                   // outputs per thread along y
+constexpr int kTYt = kGY2 * kRt;         // outputs per tile along y (32)
+
+template <int M>
+__host__ __device__ constexpr int x_lead() { return M <= 4 ? 4 : 8; }   // 16-byte aligned halo on the left
+template <int M>
+__host__ __device__ constexpr int box_x() { return kTXt + 2 * x_lead<M>(); }
+template <int M>
+__host__ __device__ constexpr int box_y() { return kTYt + 2 * M; }
+
+// Pair coefficients packed for the FP32x2 form: (cxx, cyy) and (cxy, cxy) per pair,
+// then the interior Kd (xx, xy, yy, pad).
+template <int M>
+struct __align__(16) PackTab {
+    static constexpr int kPairs = count_offsets(2, M) / 2;
+    float v[4 * kPairs + 4];
+};
+
+template <int M>
+__global__ void __launch_bounds__(kThreads)
+k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u, float *__restrict__ out, int nx,
+            int ny, int64_t N, int tiles_x, int tiles_y, int ntiles, const uint8_t *__restrict__ cons,
+            int project_in, int project_out, const float *__restrict__ kd, float scale, PackTab<M> tab,
+            double *dot_partial, double *dot_out, unsigned int *retire, int *err)
+{
+    constexpr int XL = x_lead<M>(), BX = box_x<M>(), BY = box_y<M>(), WL = kRt + 2 * M;
+    constexpr int PLANE = BX * BY;
+    constexpr uint32_t kBytes = 2u * PLANE * sizeof(float);
+    constexpr int NP = PackTab<M>::kPairs;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *const sbase = reinterpret_cast<float *>(smem_raw);   // buffer k at sbase + 2 * PLANE * k
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_abort;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    const int tx = threadIdx.x % kTXt, ty = threadIdx.x / kTXt;
+    auto tile_coords = [&](int t, int &x0, int &y0, int &b) {
+        x0 = (t % tiles_x) * kTXt;
+        const int r = t / tiles_x;
+        y0 = (r % tiles_y) * kTYt;
+        b = r / tiles_y;
+    };
+    auto issue = [&](int t, int which) {
+        int x0, y0, b;
+        tile_coords(t, x0, y0, b);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bars[which], kBytes);
+        tma_load_3d(sbase + 2 * PLANE * which, &map, x0 - XL, y0 - M, 2 * b, &bars[which]);
+    };
+
+    int it = 0, t_abort = 0;
+    if (threadIdx.x == 0 && blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    double dot_blk_total = 0.0;   // per-thread, summed over this CTA's tiles (dot needs one batch)
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int cur = it & 1;
+        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x, cur ^ 1);
+        if (!mbar_wait(&bars[cur], (it >> 1) & 1)) {
+            atomicExch(err, 1);
+            s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) {
+            t_abort = t;
+            break;
+        }
+        int x0, y0, b;
+        tile_coords(t, x0, y0, b);
+        float *sx = sbase + 2 * PLANE * cur, *sy = sx + PLANE;
+        if (project_in) {
+            for (int e = threadIdx.x; e < PLANE; e += kThreads) {
+                const int gx = x0 - XL + e % BX, gy = y0 - M + e / BX;
+                if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+                    const uint8_t m = __ldg(cons + (int64_t)gy * nx + gx);
+                    if (m & 1) sx[e] = 0.f;
+                    if (m & 2) sy[e] = 0.f;
+                }
+            }
+            __syncthreads();
+        }
+
+        const float *colx = sx + (ty * kRt) * BX + tx + XL;
+        const float *coly = sy + (ty * kRt) * BX + tx + XL;
+        u64 a1[kRt], a2[kRt];
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) { a1[r] = 0ull; a2[r] = 0ull; }
+        static_for<1, M + 1>([&](auto OX) {
+            constexpr int ox = decltype(OX)::value;
+            constexpr int My = isqrt_c(M * M - ox * ox);
+            u64 wp[WL], wm[WL];
+#pragma unroll
+            for (int i = 0; i < WL; ++i) {
+                wp[i] = pk(colx[i * BX + ox], coly[i * BX + ox]);
+                wm[i] = pk(colx[i * BX - ox], coly[i * BX - ox]);
+            }
+            static_for<-My, My + 1>([&](auto OY) {
+                constexpr int oy = decltype(OY)::value;
+                constexpr int pi = pair_index2(M, ox, oy);
+                const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
+                const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
+#pragma unroll
+                for (int r = 0; r < kRt; ++r) {
+                    const u64 s = fadd2(wp[r + M + oy], wm[r + M - oy]);
+                    a1[r] = ffma2(c1, s, a1[r]);
+                    a2[r] = ffma2(c2, s, a2[r]);
+                }
+            });
+        });
+        u64 w0[WL];
+#pragma unroll
+        for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
+        static_for<1, M + 1>([&](auto OY) {
+            constexpr int oy = decltype(OY)::value;
+            constexpr int pi = pair_index2(M, 0, oy);
+            const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
+            const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const u64 s = fadd2(w0[r + M + oy], w0[r + M - oy]);
+                a1[r] = ffma2(c1, s, a1[r]);
+                a2[r] = ffma2(c2, s, a2[r]);
+            }
+        });
+
+        float *ob = out + (int64_t)b * 2 * N;
+        const int gx = x0 + tx;
+        float dot = 0.f;
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) {
+            const int gy = y0 + ty * kRt + r;
+            if (gx < nx && gy < ny) {
+                const int64_t p = (int64_t)gy * nx + gx;
+                const float2 up = upk(w0[r + M]);
+                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                const float ax = x1.x + x2.y, ay = x1.y + x2.x;
+                float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
+                const int c0 = min(gx, M), c1 = min(nx - 1 - gx, M), d0 = min(gy, M), d1 = min(ny - 1 - gy, M);
+                if (c0 != M || c1 != M || d0 != M || d1 != M) {
+                    const int cls = ((c0 * (M + 1) + c1) * (M + 1) + d0) * (M + 1) + d1;
+                    kxx = __ldg(kd + 3 * cls);
+                    kxy = __ldg(kd + 3 * cls + 1);
+                    kyy = __ldg(kd + 3 * cls + 2);
+                }
+                float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
+                float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
+                if (project_out) {
+                    const uint8_t m = __ldg(cons + p);
+                    if (m & 1) fx = 0.f;
+                    if (m & 2) fy = 0.f;
+                }
+                fx *= scale;
+                fy *= scale;
+                ob[p] = fx;
+                ob[N + p] = fy;
+                dot = __fmaf_rn(up.x, fx, __fmaf_rn(up.y, fy, dot));
+            }
+        }
+        dot_blk_total += (double)dot;
+        __syncthreads();   // all reads of buf[cur] done before it is refilled
+    }
+    if (s_abort) {
+        // let a copy still in flight land (bounded) before the CTA exits
+        if (threadIdx.x == 0 && t_abort + (int)gridDim.x < ntiles) mbar_wait(&bars[(it & 1) ^ 1], ((it + 1) >> 1) & 1);
+        return;
+    }
+    if (dot_partial) {
+        // single-field launches only (batch == 1): one partial per CTA
+        __shared__ double red[kThreads / 32];
+        const double s = block_sum(dot_blk_total, red);
+        grid_finish(s, gridDim.x, blockIdx.x, dot_partial, dot_out, retire, red);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+template <int M>
+PackTab<M> make_pack(const pd_grid *g)
+{
+    PackTab<M> t{};
+    double c[6], tot[3] = {0, 0, 0};
+    auto put = [&](int ox, int oy) {
+        const int pi = pair_index2(M, ox, oy);
+        coef_of(g, ox, oy, 0, false, c);
+        t.v[4 * pi + 0] = (float)c[0];
+        t.v[4 * pi + 1] = (float)c[2];
+        t.v[4 * pi + 2] = (float)c[1];
+        t.v[4 * pi + 3] = (float)c[1];
+        for (int i = 0; i < 3; ++i) tot[i] += 2 * c[i];
+    };
+    for (int ox = 1; ox <= M; ++ox) {
+        const int My = isqrt_c(M * M - ox * ox);
+        for (int oy = -My; oy <= My; ++oy) put(ox, oy);
+    }
+    for (int oy = 1; oy <= M; ++oy) put(0, oy);
+    constexpr int NP = PackTab<M>::kPairs;
+    for (int i = 0; i < 3; ++i) t.v[4 * NP + i] = (float)tot[i];
+    return t;
+}
+
+template <int M>
+int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
+{
+    constexpr int BX = box_x<M>(), BY = box_y<M>();
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(PD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const int nx = (int)g->n[0], ny = (int)g->n[1];
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(2 * a.batch)};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)BX, (cuuint32_t)BY, 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(a.u), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PD_ERR_CUDA, "tensor map encode failed");
+    const size_t smem = 2ull * 2 * BX * BY * sizeof(float);
+    auto kern = k_tbt2d_tma<M>;
+    static int attr_done[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_done[dev] = 1;
+    }
+    const int tiles_x = (nx + kTXt - 1) / kTXt, tiles_y = (ny + kTYt - 1) / kTYt;
+    const int64_t nt = (int64_t)tiles_x * tiles_y * a.batch;
+    if (nt > (1ll << 30)) return fail(PD_ERR_INVALID, "too many tiles");
+    int occ = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (occ < 1) occ = 1;
+    int blocks = (int)std::min<int64_t>(nt, (int64_t)occ * sms);
+    if (a.dot_partial && a.batch != 1) return fail(PD_ERR_INVALID, "fused dot needs a single field");
+    kern<<<blocks, kThreads, smem, s>>>(map, (const float *)a.u, (float *)a.out, nx, ny, g->N, tiles_x, tiles_y,
+                                        (int)nt, g->d_cons, (a.project && !a.input_projected) ? 1 : 0,
+                                        a.project ? 1 : 0, g->d_kd32, (float)a.scale, make_pack<M>(g),
+                                        a.dot_partial, a.dot_out, a.retire, g->d_err);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
+}  // namespace
+
+bool tma_stencil_eligible(const pd_grid *g, const MatvecArgs &a, bool f64)
+{
+    if (f64 || g->dim != 2 || a.use_E || a.use_mu) return false;
+    if (g->n[0] % 4 != 0) return false;                       // row stride must be a multiple of 16 bytes
+    if (((uintptr_t)a.u & 15) != 0) return false;             // 16-byte aligned base
+    return encode_fn() != nullptr;
+}
+
+int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
+{
+    switch (g->M) {
+        case 1: return run<1>(g, a, s);
+        case 2: return run<2>(g, a, s);
+        case 3: return run<3>(g, a, s);
+        case 4: return run<4>(g, a, s);
+        case 5: return run<5>(g, a, s);
+        case 6: return run<6>(g, a, s);
+        case 7: return run<7>(g, a, s);
+        case 8: return run<8>(g, a, s);
+    }
+    return fail(PD_ERR_INVALID, "horizon M not compiled for 2D");
+}
+
+}  // namespace pd
