@@ -233,6 +233,24 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         float *ob = out + (int64_t)b * 2 * N;
         const int gx = x0 + tx;
         float dot = 0.f;
+        // Tiles whose every output keeps a full horizon inside the grid need no
+        // edge table, no bounds test and (unless asked) no projection.
+        const bool interior = (x0 >= M) && (x0 + kTXt <= nx - M) && (y0 >= M) && (y0 + kTYt <= ny - M);
+        if (interior && !project_out && !dot_partial) {
+            const float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
+            float *o0 = ob + (int64_t)(y0 + ty * kRt) * nx + gx;
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const float2 up = upk(w0[r + M]);
+                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                const float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
+                const float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
+                o0[(int64_t)r * nx] = fx * scale;
+                o0[(int64_t)r * nx + N] = fy * scale;
+            }
+            __syncthreads();   // all reads of this buffer done before it is refilled
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < kRt; ++r) {
             const int gy = y0 + ty * kRt + r;
@@ -345,6 +363,7 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_done[dev]) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         attr_done[dev] = 1;
     }
     const int tiles_x = (nx + kTXt - 1) / kTXt, tiles_y = (ny + kTYt - 1) / kTYt;
