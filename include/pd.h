@@ -163,6 +163,24 @@ int pd_step_noalloc(pd_grid *g, double *u, double *v, const double *b, int nstep
                     const double *v_prescribed, int32_t *break_step, int32_t step_base,
                     pd_step_stats *stats, void *stream);
 
+/* Reverse-mode sweep through one segment of the Verlet loop (Algorithm 2 with
+ * a = (f + b)/rho), for gradients of a loss of the final state.  The segment is
+ * the `nsteps` steps that pd_step took from the state (u_start, v_start) at
+ * step index step_base; the sweep replays them (storing u at every step) with
+ * the bond state of each step rebuilt from mask0 (the mask when the run began,
+ * DEVICE uint32 [mask_words][N]) and break_step (as recorded by pd_step: bond
+ * (p, k) intact at step s unless 0 < break_step[p * nnb + k] <= s), then runs
+ * backward.  ubar, vbar, abar (DEVICE double [dim][N]): on entry the adjoints
+ * of u, v, a at the segment's end; on exit at its start.  When step_base == 0
+ * the dependence of the first acceleration on u_0 is included and abar is
+ * cleared.  grad_E (DEVICE double [N] or NULL) accumulates dL/dE for the
+ * per-node modulus field (bond modulus (E_p + E_q)/2).  Breaking is not
+ * differentiated: the recorded bond history is held fixed.  Allocates a
+ * workspace of (nsteps + 6) vectors for the call. */
+int pd_step_adjoint(pd_grid *g, const double *u_start, const double *v_start, const double *b, int nsteps,
+                    double dt, const double *v_prescribed, const uint32_t *mask0, const int32_t *break_step,
+                    int32_t step_base, double *ubar, double *vbar, double *abar, double *grad_E, void *stream);
+
 /* One breaking pass: every intact bond with stretch s >= s0 (Eq. fra:s1,
  * evaluated in FP64 as X = xi + (u_q - u_p), s = (|X| - |xi|)/|xi|, xi = h o,
  * no contraction) is broken in both directions.  u: DEVICE [dim][N] of the

@@ -337,3 +337,52 @@ def symbol(dim: int, L, h: float, M: int, alpha_: float) -> np.ndarray:
         for b in range(dim):
             G[a, b][idx] = T[a, b]
     return np.fft.fftn(G, axes=tuple(range(2, 2 + dim)))
+
+
+def vv_history(dim, n, h, M, alpha_, u0, v0, nsteps, dt, rho=1.0, b=None, E=None, mu0=None, s0=0.0, cons=None,
+               vpres=None):
+    """Algorithm 2 step by step, keeping u and the bond state after every step.
+    Returns (us, vs, mus): lists of length nsteps + 1 (index = step)."""
+    u, v = np.array(u0, dtype=np.float64), np.array(v0, dtype=np.float64)
+    mu = intact_mu(dim, n, M) if mu0 is None else mu0.copy()
+    us, vs, mus = [u.copy()], [v.copy()], [mu.copy()]
+    for _ in range(nsteps):
+        vv(dim, n, h, M, alpha_, u, v, 1, dt, rho=rho, b=b, E=E, mu=mu, s0=s0, cons=cons, vpres=vpres)
+        us.append(u.copy())
+        vs.append(v.copy())
+        mus.append(mu.copy())
+    return us, vs, mus
+
+
+def vv_grad_modulus(dim, n, h, M, alpha1, E, u0, v0, nsteps, dt, rho=1.0, b=None, mu0=None, s0=0.0, cons=None,
+                    vpres=None):
+    """Gradient of L = 1/2 |u_N|^2 after nsteps steps of Algorithm 2 (a = (f + b)/rho,
+    bond modulus (E_p + E_q)/2, alpha1 = alpha at E = 1) with respect to E, the
+    bond history held at the one the forward run produced.
+
+    Discrete adjoint of one step n -> n+1 (free components; constrained
+    components move with the prescribed velocity and do not depend on v, a):
+      u_{n+1} = u_n + dt v_n + dt^2/2 a_n ;  a_{n+1} = (A_{n+1} u_{n+1} + b)/rho ;
+      v_{n+1} = v_n + dt/2 (a_n + a_{n+1}).
+    Returns (u_N, dL/dE)."""
+    us, vs, mus = vv_history(dim, n, h, M, alpha1, u0, v0, nsteps, dt, rho, b, E, mu0, s0, cons, vpres)
+    free = np.ones_like(us[0]) if cons is None else (1.0 - np.asarray(cons, dtype=np.float64))
+    ub = us[-1].copy()                      # dL/du_N
+    vb = np.zeros_like(ub)
+    ab = np.zeros_like(ub)
+    gE = np.zeros(tuple(reversed([int(v) for v in n])))
+    for s in reversed(range(nsteps)):
+        # velocity update
+        ab = (ab + 0.5 * dt * vb) * free
+        ab_prev = 0.5 * dt * vb * free
+        vb = vb * free
+        # acceleration from the displacement at step s+1 (bond state of step s+1)
+        ub = ub + force(dim, n, h, M, alpha1, ab, E=E, mu=mus[s + 1]) / rho
+        gE = gE + grad_modulus(dim, n, h, M, alpha1, us[s + 1], ab, mu=mus[s + 1]) / rho
+        # displacement update
+        vb = vb + dt * ub * free
+        ab = ab_prev + 0.5 * dt * dt * ub * free
+    ab = ab * free
+    ub = ub + force(dim, n, h, M, alpha1, ab, E=E, mu=mus[0]) / rho
+    gE = gE + grad_modulus(dim, n, h, M, alpha1, us[0], ab, mu=mus[0]) / rho
+    return us[-1], gE

@@ -69,6 +69,7 @@ SIGNATURES = {
     "pd_step": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats), _VP]),
     "pd_step_noalloc": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats),
                              _VP]),
+    "pd_step_adjoint": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "pd_break_bonds": (_I, [_VP, _VP, _U32, ctypes.POINTER(_I64), _VP]),
     "pd_break_segment": (_I, [_VP, ctypes.POINTER(_I64), _I64, ctypes.POINTER(_I64), _VP]),
     "pd_set_method": (_I, [_VP, _U32]),
@@ -192,6 +193,16 @@ def pd_step_noalloc(g, u, v, b, nsteps: int, dt: float, v_prescribed=None, break
     return st
 
 
+def pd_step_adjoint(g, u_start, v_start, b, nsteps: int, dt: float, v_prescribed, mask0, break_step,
+                    step_base: int, ubar, vbar, abar, grad_E=None, stream=None):
+    import torch
+    f64 = torch.float64
+    _check(load_library().pd_step_adjoint(g, _dptr(u_start, f64), _dptr(v_start, f64), _dptr(b, f64), int(nsteps),
+                                          float(dt), _dptr(v_prescribed, f64), _dptr(mask0, torch.int32),
+                                          _dptr(break_step, torch.int32), int(step_base), _dptr(ubar, f64),
+                                          _dptr(vbar, f64), _dptr(abar, f64), _dptr(grad_E, f64), _stream(stream)))
+
+
 def pd_break_bonds(g, u, stream=None) -> int:
     n = ctypes.c_int64(0)
     _check(load_library().pd_break_bonds(g, _dptr(u), _dtype_flag(u), ctypes.byref(n), _stream(stream)))
@@ -262,7 +273,7 @@ class Grid:
                  thickness=1.0, s0=0.0, E_field=None):
         self.dim, self.n, self.h, self.M = dim, tuple(int(v) for v in n), float(h), int(M)
         self.handle = pd_create_grid(dim, self.n, h, M * h, constrained)
-        pd_set_material(self.handle, E, rho, thickness, s0, E_field)
+        self.set_material(E, rho, thickness, s0, E_field)
         info = pd_get_info(self.handle)
         self.nnb, self.mask_words, self.alpha = info.nnb, info.mask_words, info.alpha
 
@@ -276,6 +287,7 @@ class Grid:
 
     def set_material(self, E=1.0, rho=1.0, thickness=1.0, s0=0.0, E_field=None):
         pd_set_material(self.handle, E, rho, thickness, s0, E_field)
+        self.E, self.rho, self.thickness, self.s0 = float(E), float(rho), float(thickness), float(s0)
         self.alpha = pd_get_info(self.handle).alpha
 
     def matvec(self, u, out=None, flags: int = 0, stream=None):

@@ -429,3 +429,40 @@ def test_verlet_prescribed_velocity_layers():
     np.testing.assert_allclose(u[1][lay != 0], 50 * dt * vpres[1][lay != 0], rtol=1e-12)
     assert np.array_equal(v[1][lay != 0], vpres[1][lay != 0])
     assert np.abs(u[0]).max() > 0   # free x components respond
+
+
+def test_dynamic_modulus_gradient_matches_finite_differences():
+    """P12 (dynamic): the oracle's discrete adjoint of Algorithm 2 equals central
+    differences of L = 1/2 |u_N|^2 in E, on a pre-notched plate whose bonds break
+    during the run (the +/- runs are checked to break the same bonds)."""
+    w = syn.crack_plate(20, 3)
+    n, M, h = w.n, w.M, w.h
+    lay = w.extra["vel_layers"]
+    cons = np.zeros((2,) + lay.shape, dtype=np.uint8)
+    cons[1] = lay != 0
+    vp = np.zeros((2,) + lay.shape)
+    vp[1] = lay * 0.02
+    E = w.extra["E_field"]
+    al1 = oracle.alpha(2, 1.0, M * h)
+    mu0 = oracle.intact_mu(2, n, M)
+    oracle.prenotch(n, M, w.extra["notch"], w.extra["notch_den"], mu0)
+    dt, steps, s0 = 2e-3, 30, 2e-3
+    u0 = np.zeros((2,) + lay.shape)
+    uN, g = oracle.vv_grad_modulus(2, n, h, M, al1, E, u0, vp.copy(), steps, dt, mu0=mu0, s0=s0, cons=cons, vpres=vp)
+    us, _, mus = oracle.vv_history(2, n, h, M, al1, u0, vp.copy(), steps, dt, E=E, mu0=mu0, s0=s0, cons=cons, vpres=vp)
+    assert (mus[-1] == 0).sum() > (mu0 == 0).sum()   # bonds broke during the run
+    rng = np.random.default_rng(12)
+    picks = list(np.argsort(-np.abs(g).ravel())[:3]) + list(rng.choice(E.size, 2, replace=False))
+    for flat in picks:
+        idx = np.unravel_index(flat, E.shape)
+        eps = 1e-4 * E[idx]
+        res = []
+        for sgn in (1, -1):
+            Ep = E.copy()
+            Ep[idx] += sgn * eps
+            usp, _, musp = oracle.vv_history(2, n, h, M, al1, u0, vp.copy(), steps, dt, E=Ep, mu0=mu0, s0=s0,
+                                            cons=cons, vpres=vp)
+            assert all(np.array_equal(a, b) for a, b in zip(musp, mus))
+            res.append(0.5 * (usp[-1] ** 2).sum())
+        fd = (res[0] - res[1]) / (2 * eps)
+        assert g[idx] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(g).max())
