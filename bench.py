@@ -355,6 +355,37 @@ def _extras(torch, pd, syn, dev):
         cg["speedup_mixed_vs_f64"] = round(cg["f64"]["seconds"] / cg["mixed"]["seconds"], 3)
     out["cg_1024_rtol1e-8"] = cg
     g.close()
+    # 64 uneven plates (sides 128..512, M in {3,4}): one batched solve vs one solve per plate
+    plates = syn.batched_plates(64)
+    grids = [pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained) for w in plates]
+    bs = [torch.tensor(w.b, device=dev) for w in plates]
+    dof = sum(2 * w.N for w in plates)
+    bt = pd.pd_batch_create(grids)
+    us = [torch.zeros_like(x) for x in bs]
+    pd.pd_batch_cg_solve(bt, bs, us, 1e-8, 64, allow_not_converged=True)   # warm: graph capture
+    for u in us:
+        u.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = pd.pd_batch_cg_solve(bt, bs, us, 1e-8, 1_000_000)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    pd.pd_batch_destroy(bt)
+    for g_, b_ in zip(grids, bs):   # warm each plate's own workspace and graphs
+        pd.pd_cg_solve(g_.handle, b_, torch.zeros_like(b_), 1e-8, 64, pd.PD_CG_MIXED, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for g_, b_ in zip(grids, bs):
+        pd.pd_cg_solve(g_.handle, b_, torch.zeros_like(b_), 1e-8, 1_000_000, pd.PD_CG_MIXED)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    out["batch_64_plates_rtol1e-8"] = {
+        "dof_total": dof, "batched_s": round(t_batch, 4), "sequential_s": round(t_seq, 4),
+        "batched_dof_per_s": dof / t_batch, "sequential_dof_per_s": dof / t_seq,
+        "speedup": round(t_seq / t_batch, 3), "max_rel_residual": max(s.rel_residual for s in st),
+        "max_inner_iterations": max(s.iterations for s in st)}
+    for g_ in grids:
+        g_.close()
     # 3D cube 128^3, FP32
     w = syn.cube(128, 3)
     g = pd.Grid(3, w.n, w.h, w.M, constrained=w.constrained)

@@ -209,6 +209,27 @@ int pd_set_method(pd_grid *g, uint32_t method);
  * not measured). */
 int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream);
 
+/* ---- batches of independent static solves ----
+ * A pd_batch groups `count` existing 2D grids (each with its own size,
+ * horizon M <= 4, constraints and modulus; no modulus field) so that their
+ * solves advance together: each CG stage is one launch over the tiles or
+ * chunks of every plate, and the inner iterations replay as a captured CUDA
+ * graph.  The grids must outlive the batch; the batch keeps concatenated
+ * copies of the vectors (allocated here).  Errors: PD_ERR_INVALID, PD_ERR_OOM. */
+typedef struct pd_batch pd_batch;
+int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out);
+
+/* Solves P K P u_i = P b_i for every plate of the batch by FP32 inner CG under
+ * FP64 iterative refinement (the PD_CG_MIXED scheme) until every plate reaches
+ * ||P(b_i - K u_i)|| <= rtol ||P b_i||.  b, u: HOST arrays of `count` DEVICE
+ * pointers to double [2][N_i]; u_i is the initial guess on entry and the
+ * solution on exit.  stats: HOST array of `count` entries or NULL (seconds is
+ * the wall time of the whole batch).  max_iter caps the inner iterations of the
+ * slowest plate summed over refinement passes. */
+int pd_batch_cg_solve(pd_batch *bt, const double *const *b, double *const *u, double rtol, int max_iter,
+                      pd_cg_stats *stats, void *stream);
+int pd_batch_destroy(pd_batch *bt);
+
 /* Reads grid facts (host struct). */
 int pd_get_info(pd_grid *g, pd_grid_info *info);
 

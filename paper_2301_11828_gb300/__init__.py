@@ -70,6 +70,9 @@ SIGNATURES = {
     "pd_step_noalloc": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats),
                              _VP]),
     "pd_step_adjoint": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
+    "pd_batch_create": (_I, [_VP, _I, ctypes.POINTER(_VP)]),
+    "pd_batch_cg_solve": (_I, [_VP, _VP, _VP, _D, _I, ctypes.POINTER(pd_cg_stats), _VP]),
+    "pd_batch_destroy": (_I, [_VP]),
     "pd_break_bonds": (_I, [_VP, _VP, _U32, ctypes.POINTER(_I64), _VP]),
     "pd_break_segment": (_I, [_VP, ctypes.POINTER(_I64), _I64, ctypes.POINTER(_I64), _VP]),
     "pd_set_method": (_I, [_VP, _U32]),
@@ -201,6 +204,31 @@ def pd_step_adjoint(g, u_start, v_start, b, nsteps: int, dt: float, v_prescribed
                                           float(dt), _dptr(v_prescribed, f64), _dptr(mask0, torch.int32),
                                           _dptr(break_step, torch.int32), int(step_base), _dptr(ubar, f64),
                                           _dptr(vbar, f64), _dptr(abar, f64), _dptr(grad_E, f64), _stream(stream)))
+
+
+def pd_batch_create(grids) -> ctypes.c_void_p:
+    arr = (ctypes.c_void_p * len(grids))(*[getattr(g, "handle", g) for g in grids])
+    out = ctypes.c_void_p()
+    _check(load_library().pd_batch_create(arr, len(grids), ctypes.byref(out)))
+    return out
+
+
+def pd_batch_cg_solve(bt, bs, us, rtol: float, max_iter: int, stream=None, allow_not_converged=False):
+    """bs, us: lists of float64 CUDA tensors [2, ny_i, nx_i]; returns per-plate pd_cg_stats."""
+    import torch
+    n = len(bs)
+    bp = (ctypes.c_void_p * n)(*[_dptr(b, torch.float64).value for b in bs])
+    up = (ctypes.c_void_p * n)(*[_dptr(u, torch.float64).value for u in us])
+    st = (pd_cg_stats * n)()
+    rc = load_library().pd_batch_cg_solve(bt, bp, up, float(rtol), int(max_iter), st, _stream(stream))
+    if not (allow_not_converged and rc == PD_ERR_NOT_CONVERGED):
+        _check(rc)
+    return list(st)
+
+
+def pd_batch_destroy(bt):
+    if bt is not None and bt.value:
+        _check(load_library().pd_batch_destroy(bt))
 
 
 def pd_break_bonds(g, u, stream=None) -> int:
