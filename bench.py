@@ -389,10 +389,61 @@ def _extras(torch, pd, syn, dev):
     # 3D cube 128^3, FP32
     w = syn.cube(128, 3)
     g = pd.Grid(3, w.n, w.h, w.M, constrained=w.constrained)
+    cube = {}
+    for dt_, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+        U = torch.tensor(w.u, dtype=dt_, device=dev)
+        O = torch.empty_like(U)
+        for meth, mname in ((pd.PD_METHOD_STENCIL, "stencil"), (pd.PD_METHOD_FFT, "fft")):
+            s = _time_fn(torch, lambda: g.matvec(U, O, flags=meth | pd.PD_PROJECT), reps=10)
+            cube[f"{name}_{mname}_gdofs"] = round(3 * w.N / s / 1e9, 2)
+    # FP32 FFT product against the FP64 oracle on the same (rounded) input
+    import oracle
     U = torch.tensor(w.u, dtype=torch.float32, device=dev)
-    O = torch.empty_like(U)
-    s = _time_fn(torch, lambda: g.matvec(U, O, flags=pd.PD_METHOD_STENCIL), reps=10)
-    out["cube128_f32_gdofs"] = round(3 * w.N / s / 1e9, 2)
+    o32 = g.matvec(U, flags=pd.PD_METHOD_FFT | pd.PD_PROJECT).double().cpu().numpy()
+    ref = oracle.stiffness(3, w.n, w.h, w.M, oracle.alpha(3, 1.0, w.delta), U.double().cpu().numpy(),
+                           cons=w.constrained)
+    cube["f32_fft_rel_err_vs_oracle"] = float(np.linalg.norm(o32 - ref) / np.linalg.norm(ref))
+    g.autotune()
+    b = torch.tensor(w.b, device=dev)
+    for mode, name in ((pd.PD_CG_MIXED, "cg_mixed"), (pd.PD_CG_F64, "cg_f64")):
+        u = torch.zeros_like(b)
+        pd.pd_cg_solve(g.handle, b, u, 1e-8, 32, mode, allow_not_converged=True)
+        u.zero_()
+        st = pd.pd_cg_solve(g.handle, b, u, 1e-8, 200000, mode, allow_not_converged=True)
+        cube[name] = {"seconds": round(st.seconds, 4), "iterations": st.iterations, "rel_residual": st.rel_residual}
+    out["cube128"] = cube
+    g.close()
+    # dynamic crack loop on the 512^2 pre-notched plate (lognormal modulus, edge velocity layers)
+    w = syn.crack_plate(512, 3)
+    lay = w.extra["vel_layers"]
+    cons = np.zeros((2,) + lay.shape, dtype=np.uint8)
+    cons[1] = lay != 0
+    vp = np.zeros((2,) + lay.shape)
+    vp[1] = lay * w.extra["v0"]
+    Et = torch.tensor(w.extra["E_field"], device=dev)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=cons, E_field=Et, s0=w.s0)
+    g.break_segment(w.extra["notch"], w.extra["notch_den"])
+    vpt = torch.tensor(vp, device=dev)
+    u = torch.zeros((2,) + lay.shape, dtype=torch.float64, device=dev)
+    v = vpt.clone()
+    dtc = 2.99e-3
+    g.step(u, v, None, nsteps=5, dt=dtc, v_prescribed=vpt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = g.step(u, v, None, nsteps=200, dt=dtc, v_prescribed=vpt)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    from paper_2301_11828_gb300.autograd import verlet_run
+    E = Et.clone().requires_grad_(True)
+    u0 = torch.zeros_like(u)
+    t0 = time.perf_counter()
+    uN = verlet_run(g, E, u0, vpt.clone(), 200, dtc, v_prescribed=vpt, checkpoint_every=45)
+    (0.5 * (uN * uN).sum()).backward()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    out["crack512"] = {"steps_per_s": round(200 / t_fwd, 1), "dof_steps_per_s": 2 * w.N * 200 / t_fwd,
+                       "bonds_broken_in_200_steps": st.newly_broken,
+                       "forward_plus_adjoint_200_steps_s": round(t_grad, 4)}
     g.close()
     return out
 

@@ -122,6 +122,10 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_kd32);
     cudaFree(g->d_sym64);
     cudaFree(g->d_sym32);
+    cudaFree(g->d_sym3_64);
+    cudaFree(g->d_sym3_32);
+    cudaFree(g->d_ctot64);
+    cudaFree(g->d_ctot32);
     cudaFree(g->d_off);
     cudaFree(g->d_coef);
     cudaFree(g->d_coef1);
@@ -194,7 +198,6 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
     }
     bool use_fft = (method == PD_METHOD_FFT);
     if (method == 0) use_fft = (g->auto_choice[f64 ? 1 : 0] == 2);
-    if (use_fft && g->dim != 2) return fail(PD_ERR_INVALID, "the FFT method is built for 2D grids");
     if (dot_partial && need_mu) return fail(PD_ERR_INVALID, "internal: fused dot with broken bonds");
     a.dot_partial = dot_partial;
     a.dot_out = dot_out;
@@ -335,6 +338,10 @@ int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s
     if (rc) return rc;
     g->auto_choice[0] = g->auto_choice[1] = 0;
     ++g->op_stamp;
+    if (g->d_sym3_32) {
+        rc = fft3_prepare(g);
+        if (rc) return rc;
+    }
     if (g->d_sym32) return fft_prepare(g);
     return PD_OK;
 }
@@ -362,7 +369,7 @@ int pd_set_method(pd_grid *g, uint32_t method)
     } else if (method == PD_METHOD_STENCIL) {
         g->auto_choice[0] = g->auto_choice[1] = 1;
     } else if (method == PD_METHOD_FFT) {
-        if (g->dim != 2 || g->has_E) return fail(PD_ERR_INVALID, "the FFT method needs a 2D grid without a modulus field");
+        if (g->has_E) return fail(PD_ERR_INVALID, "the FFT method needs a grid without a modulus field");
         g->auto_choice[0] = g->auto_choice[1] = 2;
     } else {
         return fail(PD_ERR_INVALID, "method must be PD_METHOD_AUTO, PD_METHOD_STENCIL or PD_METHOD_FFT");
@@ -389,7 +396,7 @@ int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const bool fft_ok = (g->dim == 2) && !g->has_E;
+    const bool fft_ok = !g->has_E;
     for (int prec = 0; prec < 2 && rc == PD_OK; ++prec) {
         const uint32_t dt = prec ? PD_F64 : PD_F32;
         if (!(flags & dt)) continue;

@@ -341,7 +341,7 @@ int fft_prepare(pd_grid *g)
 
 int launch_fft_tile(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s)
 {
-    if (g->dim != 2) return fail(PD_ERR_INVALID, "the FFT method is built for 2D grids");
+    if (g->dim == 3) return launch_fft3_tile(g, f64, a, s);
     if (a.batch < 1 || a.batch > 65535) return fail(PD_ERR_INVALID, "batch must be in [1, 65535]");
     if (!g->d_sym32) {
         int rc = fft_prepare(g);

@@ -101,6 +101,10 @@ struct pd_grid {
     float *d_kd32 = nullptr;
     double *d_sym64 = nullptr;
     float *d_sym32 = nullptr;
+    double *d_sym3_64 = nullptr;    // 3D tile symbol (6 x 16^3)
+    float *d_sym3_32 = nullptr;
+    double *d_ctot64 = nullptr;     // interior diagonal block (3D FFT epilogue)
+    float *d_ctot32 = nullptr;
     int64_t kd_entries = 0;
     int64_t broken_total = 0;
 
@@ -143,6 +147,8 @@ int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s);
 // ------------------------------------------------------------------ launchers (pd_fft.cu)
 int launch_fft_tile(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);
 int fft_prepare(pd_grid *g);   // builds the tile symbol tables
+int fft3_prepare(pd_grid *g);  // 3D (pd_fft3d.cu)
+int launch_fft3_tile(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers (pd_crack.cu)
 int launch_df_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t batch, bool project,
