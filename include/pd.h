@@ -63,7 +63,7 @@ typedef enum {
 
 /* ---- modes for pd_cg_solve ---- */
 #define PD_CG_F64   0x1u  /* plain CG, FP64 vectors and FP64 matvec */
-#define PD_CG_MIXED 0x2u  /* FP32-matvec CG inside FP64 iterative refinement */
+#define PD_CG_MIXED 0x2u  /* FP32-matvec CG, FP64 solution, FP64 residual replacement every 10x drop */
 
 typedef struct {
     int dim;          /* 2 or 3 */
@@ -79,7 +79,7 @@ typedef struct {
 
 typedef struct {
     int iterations;        /* total inner (matvec) iterations */
-    int outer;             /* refinement passes (1 for PD_CG_F64) */
+    int outer;             /* FP64 residual replacements (mixed) or restarts (FP64) */
     int f64_matvecs;       /* FP64 operator applications */
     double rel_residual;   /* ||P(b - K u)|| / ||P b||, FP64, recomputed at the end */
     double seconds;        /* wall time of the solve, device-synchronised */

@@ -4,10 +4,13 @@
 // relaxation; this library pairs the same operator with CG, in two modes:
 //
 //  * PD_CG_F64: textbook CG with FP64 vectors and the FP64 operator.
-//  * PD_CG_MIXED: iterative refinement.  The outer loop keeps u in FP64 and
-//    forms the true residual r = P(b - K u) with the FP64 operator; the inner
-//    loop solves K d = r / |r| approximately by CG with FP32 vectors and the
-//    FP32 operator (dot products are reduced in FP64); then u += |r| d.
+//  * PD_CG_MIXED: CG with FP32 vectors and the FP32 operator (dot products
+//    reduced in FP64), u kept in FP64, with reliable updates: each time the
+//    FP32 residual has fallen tenfold, the FP32 increment is folded into u, the
+//    true residual r = P(b - K u) is formed with the FP64 operator and replaces
+//    the FP32 one while the search direction is kept.  This is FP64 iterative
+//    refinement without the restarts, so the iteration count stays close to
+//    that of FP64 CG.
 //
 // One inner iteration is three launches: (1) q = K p with p.q fused into the
 // stencil epilogue, (2) alpha = rr / pq, x += alpha p, r -= alpha q, r.r
@@ -182,12 +185,40 @@ k_plain_start(double *p, const double *__restrict__ r, int64_t L, double tol2, C
     }
 }
 
-// u += s * x32 on free components (constrained components stay 0).
+// u += s * x32, then x32 = 0 (a reliable update folds the FP32 increment into u).
 __global__ void __launch_bounds__(kBlk)
-k_correct(double *u, const float *__restrict__ x32, double s, int64_t L)
+k_correct_zero(double *u, float *x32, double s, int64_t L)
 {
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk)
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
         u[i] += s * (double)x32[i];
+        x32[i] = 0.f;
+    }
+}
+
+// r32 = r64 * inv: the true residual replaces the recursive one.  The inner loop
+// stopped in the update of iteration k, so p still holds p_{k-1} and sc->beta
+// holds beta_k; the new direction is p_k = r_true + beta_k p_{k-1}, i.e. the
+// direction CG would have formed had its recursive residual been exact.
+// sc->rr = r32.r32, sc->tol2 = tol2 (absolute), the inner loop is re-armed.
+__global__ void __launch_bounds__(kBlk)
+k_replace(float *r32, float *p32, const double *__restrict__ r64, int64_t L, double inv, double tol2, CgScal *sc,
+          double *partial)
+{
+    __shared__ double red[kBlk / 32];
+    const float beta = (float)sc->beta;
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+        const float v = (float)(r64[i] * inv);
+        p32[i] = v + beta * p32[i];
+        r32[i] = v;
+        acc += v * v;
+    }
+    const double bs = block_sum((double)acc, red);
+    if (grid_last(bs, partial, &sc->rr, &sc->retire[1], red)) {
+        sc->tol2 = tol2;
+        sc->done = (sc->rr > tol2) ? 0 : 1;
+        sc->iters = 0;
+    }
 }
 
 __global__ void __launch_bounds__(kBlk)
@@ -422,27 +453,45 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
             if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
         }
     } else {
-        for (int o = 0; o < 60; ++o) {
-            double rr;
-            rc = true_residual(g, w, b, u, s, &rr);
-            if (rc) return rc;
-            ++f64mv;
-            rel = std::sqrt(rr) / bnorm;
-            if (rel <= rtol) { status = PD_OK; break; }
-            if (total_iters >= max_iter || !std::isfinite(rel)) break;
-            ++outer;
-            const double rn = std::sqrt(rr);
-            // inner target: the reduction still needed (with margin), but not below FP32 reach
-            const double need = 0.3 * rtol * bnorm / rn;
-            const double tau = std::min(0.5, std::max(need, 2e-5));
-            k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->r64, L, 1.0 / rn, tau * tau, w->sc,
-                                                  w->partial2);
-            int it = 0;
-            rc = inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it);
-            total_iters += it;
-            if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
-            k_correct<<<blocks, kBlk, 0, s>>>(u, w->x32, rn, L);
-            PD_CUDA(cudaGetLastError());
+        // FP32 CG with reliable updates: whenever the FP32 recursive residual has
+        // dropped by kRU since the last update, the FP32 increment is added to u
+        // in FP64, the true residual b - K u is formed with the FP64 operator and
+        // replaces the FP32 residual; the search direction is kept, so the Krylov
+        // history is not lost as it is by a restart.  FP32 vectors are scaled by
+        // the initial residual norm s0 so they stay O(1).
+        constexpr double kRU = 0.1;
+        double rr;
+        rc = true_residual(g, w, b, u, s, &rr);
+        if (rc) return rc;
+        ++f64mv;
+        rel = std::sqrt(rr) / bnorm;
+        const double s0 = std::sqrt(rr) > 0 ? std::sqrt(rr) : 1.0;
+        const double tgt2 = (0.5 * rtol * bnorm / s0) * (0.5 * rtol * bnorm / s0);
+        if (rel <= rtol) {
+            status = PD_OK;
+        } else {
+            double rr_ref = rr / (s0 * s0);
+            k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->r64, L, 1.0 / s0,
+                                                  std::max(kRU * kRU, tgt2 / rr_ref), w->sc, w->partial2);
+            for (int phase = 0; phase < 1000; ++phase) {
+                ++outer;
+                int it = 0;
+                rc = inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it);
+                total_iters += it;
+                if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
+                k_correct_zero<<<blocks, kBlk, 0, s>>>(u, w->x32, s0, L);
+                PD_CUDA(cudaGetLastError());
+                rc = true_residual(g, w, b, u, s, &rr);
+                if (rc) return rc;
+                ++f64mv;
+                rel = std::sqrt(rr) / bnorm;
+                if (rel <= rtol) { status = PD_OK; break; }
+                if (total_iters >= max_iter || !std::isfinite(rel)) break;
+                rr_ref = rr / (s0 * s0);
+                k_replace<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->r64, L, 1.0 / s0, std::max(kRU * kRU * rr_ref, tgt2),
+                                                  w->sc, w->partial2);
+                PD_CUDA(cudaGetLastError());
+            }
         }
     }
     PD_CUDA(cudaStreamSynchronize(s));
