@@ -35,6 +35,7 @@ constexpr int kChunk = 4096;
 constexpr int kBT = 256;
 constexpr int kTX = 64, kR = 8, kTY = 32;   // FP32 tile
 constexpr int kR64 = 4, kTY64 = 16;         // FP64 tile
+constexpr int64_t kGroupNodes = 2 << 20;    // nodes per group: 4 FP32 vectors of 2 components = 64 MB
 
 struct PlateDesc {
     int nx, ny, M, tiles_x, tiles_y, tile_base, chunk_base, nchunks;
@@ -44,6 +45,12 @@ struct PlateDesc {
     const double *kd64;
     float c32[3 * (kMaxPairs + 1)];     // pairs in kernel order, then the interior Kd
     double c64[3 * (kMaxPairs + 1)];
+};
+
+// Contiguous tile and chunk ranges of the group being solved (device memory, so
+// that one captured graph serves every group).
+struct BatchRange {
+    int tile_begin32, tile_end32, tile_begin64, tile_end64, chunk_begin, chunk_end;
 };
 
 struct BatchScal {
@@ -172,14 +179,19 @@ __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const 
 template <typename T>
 __global__ void __launch_bounds__(kBT)
 k_batch_matvec(const PlateDesc *__restrict__ desc, int np, int ntiles, const T *__restrict__ in, T *__restrict__ out,
-               double *partial, const BatchScal *__restrict__ scal)
+               double *partial, const BatchScal *__restrict__ scal, const BatchRange *__restrict__ range)
 {
     constexpr int R = sizeof(T) == 4 ? kR : kR64;
     constexpr int SXmax = kTX + 2 * kMaxBM, SYmax = kGY2 * R + 2 * kMaxBM;
     __shared__ T s_x[SXmax * SYmax], s_y[SXmax * SYmax];
     __shared__ T coef[3 * (kMaxPairs + 1)];
     __shared__ double red[kBT / 32];
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int t0 = 0, t1 = ntiles;
+    if (range) {
+        t0 = (sizeof(T) == 4) ? range->tile_begin32 : range->tile_begin64;
+        t1 = (sizeof(T) == 4) ? range->tile_end32 : range->tile_end64;
+    }
+    for (int t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
         const int pl = plate_of_tile(desc, np, t);
         const PlateDesc &d = desc[pl];
         if (scal && scal[pl].done) continue;   // uniform over the CTA
@@ -201,23 +213,35 @@ k_batch_matvec(const PlateDesc *__restrict__ desc, int np, int ntiles, const T *
     }
 }
 
+// Sum of a[0..n) by one warp: lane-strided partial sums, then a butterfly
+// (fixed order, so every caller gets the same bits); the total is in all lanes.
+__device__ __forceinline__ double warp_sum(const double *__restrict__ a, int n)
+{
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += a[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // x += alpha p, r -= alpha q over the chunk; alpha = rr / pq re-summed per plate.
 __global__ void __launch_bounds__(kBT)
-k_batch_update(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, float *x, float *r,
+k_batch_update(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, float *x, float *r,
                const float *__restrict__ p, const float *__restrict__ q, const double *__restrict__ tile_part,
                const double *__restrict__ rr_prev, double *rr_cur, const BatchScal *__restrict__ scal)
 {
     __shared__ double red[kBT / 32];
     __shared__ double s_alpha;
-    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const int pl = cplate[c];
         const PlateDesc &d = desc[pl];
         if (scal[pl].done) continue;
-        if (threadIdx.x == 0) {
-            double pq = 0.0, rr = 0.0;
-            for (int t = 0; t < d.tiles_x * d.tiles_y; ++t) pq += tile_part[d.tile_base + t];
-            for (int k = 0; k < d.nchunks; ++k) rr += rr_prev[d.chunk_base + k];
-            s_alpha = (pq != 0.0) ? rr / pq : 0.0;
+        if (threadIdx.x < 32) {
+            const double pq = warp_sum(tile_part + d.tile_base, d.tiles_x * d.tiles_y);
+            const double rr = warp_sum(rr_prev + d.chunk_base, d.nchunks);
+            if (threadIdx.x == 0) s_alpha = (pq != 0.0) ? rr / pq : 0.0;
         }
         __syncthreads();
         const float a = (float)s_alpha;
@@ -239,26 +263,24 @@ k_batch_update(const PlateDesc *__restrict__ desc, const int *__restrict__ cplat
 
 // p = r + beta p; beta = rr_cur / rr_prev; plates below their tolerance are marked done.
 __global__ void __launch_bounds__(kBT)
-k_batch_pupdate(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, float *p,
+k_batch_pupdate(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, float *p,
                 const float *__restrict__ r, const double *__restrict__ rr_prev, const double *__restrict__ rr_cur,
                 BatchScal *scal)
 {
     __shared__ double s_beta;
     __shared__ int s_stop;
-    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const int pl = cplate[c];
         const PlateDesc &d = desc[pl];
         if (scal[pl].done) continue;
-        if (threadIdx.x == 0) {
-            double rn = 0.0, ro = 0.0;
-            for (int k = 0; k < d.nchunks; ++k) {
-                rn += rr_cur[d.chunk_base + k];
-                ro += rr_prev[d.chunk_base + k];
-            }
-            s_beta = (ro > 0.0) ? rn / ro : 0.0;
-            s_stop = !(rn > scal[pl].tol2);
-            if (c == d.chunk_base) {
-                scal[pl].iters += 1;
+        if (threadIdx.x < 32) {
+            const double rn = warp_sum(rr_cur + d.chunk_base, d.nchunks);
+            const double ro = warp_sum(rr_prev + d.chunk_base, d.nchunks);
+            if (threadIdx.x == 0) {
+                s_beta = (ro > 0.0) ? rn / ro : 0.0;
+                s_stop = !(rn > scal[pl].tol2);
+                if (c == d.chunk_base) scal[pl].iters += 1;
             }
         }
         __syncthreads();
@@ -278,11 +300,14 @@ k_batch_pupdate(const PlateDesc *__restrict__ desc, const int *__restrict__ cpla
 
 // r64 = P(b - Ku), chunk partials of r64.r64
 __global__ void __launch_bounds__(kBT)
-k_batch_resid(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, double *r64,
-              const double *__restrict__ b, const double *__restrict__ Ku, double *part)
+k_batch_resid(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, double *r64,
+              const double *__restrict__ b, const double *__restrict__ Ku, double *part,
+              const BatchScal *__restrict__ scal)
 {
     __shared__ double red[kBT / 32];
-    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
+        if (scal && scal[cplate[c]].done) continue;
         const PlateDesc &d = desc[cplate[c]];
         const int64_t lo = d.off + (int64_t)(c - d.chunk_base) * kChunk;
         const int64_t hi = min(lo + (int64_t)kChunk, d.off + 2 * d.N);
@@ -305,12 +330,14 @@ k_batch_resid(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate
 // inner start: r32 = r64 / |r64|, p = r32, x = 0; chunk partials of r32.r32 into rr (the
 // "previous" buffer of the first iteration)
 __global__ void __launch_bounds__(kBT)
-k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, float *r32, float *p32,
+k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, float *r32, float *p32,
               float *x32, const double *__restrict__ r64, double *rr, const BatchScal *__restrict__ scal)
 {
     __shared__ double red[kBT / 32];
-    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const int pl = cplate[c];
+        if (scal[pl].done) continue;
         const PlateDesc &d = desc[pl];
         const double inv = scal[pl].inv_rn;
         const int64_t lo = d.off + (int64_t)(c - d.chunk_base) * kChunk;
@@ -331,9 +358,11 @@ k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate
 
 // zero the constrained components of u (the solution satisfies u = 0 on Omega_c)
 __global__ void __launch_bounds__(kBT)
-k_batch_project(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, double *u)
+k_batch_project(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch,
+                const BatchRange *__restrict__ range, double *u)
 {
-    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const PlateDesc &d = desc[cplate[c]];
         if (!d.cons) continue;
         const int64_t lo = d.off + (int64_t)(c - d.chunk_base) * kChunk;
@@ -348,10 +377,11 @@ k_batch_project(const PlateDesc *__restrict__ desc, const int *__restrict__ cpla
 
 // u += |r| x on plates that ran an inner solve this pass
 __global__ void __launch_bounds__(kBT)
-k_batch_correct(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, double *u,
+k_batch_correct(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, double *u,
                 const float *__restrict__ x32, const BatchScal *__restrict__ scal, const int *__restrict__ active)
 {
-    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const int pl = cplate[c];
         if (!active[pl]) continue;
         const PlateDesc &d = desc[pl];
@@ -368,13 +398,17 @@ k_batch_correct(const PlateDesc *__restrict__ desc, const int *__restrict__ cpla
 using namespace pd;
 
 struct pd_batch {
-    std::vector<pd_grid *> grids;
+    std::vector<pd_grid *> grids;       // in solve order (ascending size)
+    std::vector<int> order;             // solve position -> caller's index
+    std::vector<std::pair<int, int>> groups;   // [begin, end) solve positions sharing one pass
     int np = 0, ntiles32 = 0, ntiles64 = 0, nch = 0;
     int64_t total = 0;                  // concatenated vector length
     std::vector<int64_t> offs;
     PlateDesc *d_desc32 = nullptr, *d_desc64 = nullptr;
     int *d_cplate = nullptr, *d_active = nullptr;
     BatchScal *d_scal = nullptr;
+    BatchRange *d_range = nullptr;
+    std::vector<BatchRange> ranges;     // per group
     void *ws = nullptr;
     double *u64, *b64, *r64, *q64, *part_t, *rrA, *rrB, *part_c;
     float *r32, *p32, *q32, *x32;
@@ -391,12 +425,18 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
     *out = nullptr;
     pd_batch *bt = new pd_batch();
     bt->np = count;
+    bt->order.resize(count);
+    for (int i = 0; i < count; ++i) bt->order[i] = i;
+    for (int i = 0; i < count; ++i)
+        if (!grids[i]) return fail(PD_ERR_INVALID, "NULL grid in batch");
+    std::stable_sort(bt->order.begin(), bt->order.end(),
+                     [&](int a, int b) { return grids[a]->N < grids[b]->N; });
     std::vector<PlateDesc> d32(count), d64(count);
     std::vector<int> cplate;
     int tb32 = 0, tb64 = 0;
     int64_t off = 0;
     for (int i = 0; i < count; ++i) {
-        pd_grid *g = grids[i];
+        pd_grid *g = grids[bt->order[i]];
         if (!g || g->dim != 2 || g->M > kMaxBM || g->has_E) {
             delete bt;
             return fail(PD_ERR_INVALID, "batch plates must be 2D, horizon M <= 4, without a modulus field");
@@ -449,6 +489,33 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
         off += 2 * d.N;
     }
     bt->total = off;
+    // groups of consecutive (similar-size) plates whose FP32 working set stays in L2
+    {
+        int64_t acc = 0;
+        int begin = 0;
+        for (int i = 0; i < count; ++i) {
+            const int64_t n = bt->grids[i]->N;
+            if (i > begin && acc + n > kGroupNodes) {
+                bt->groups.push_back({begin, i});
+                begin = i;
+                acc = 0;
+            }
+            acc += n;
+        }
+        bt->groups.push_back({begin, count});
+        for (const auto &gr : bt->groups) {
+            const PlateDesc &f32 = d32[gr.first], &l32 = d32[gr.second - 1];
+            const PlateDesc &f64 = d64[gr.first], &l64 = d64[gr.second - 1];
+            BatchRange r;
+            r.tile_begin32 = f32.tile_base;
+            r.tile_end32 = l32.tile_base + l32.tiles_x * l32.tiles_y;
+            r.tile_begin64 = f64.tile_base;
+            r.tile_end64 = l64.tile_base + l64.tiles_x * l64.tiles_y;
+            r.chunk_begin = f32.chunk_base;
+            r.chunk_end = l32.chunk_base + l32.nchunks;
+            bt->ranges.push_back(r);
+        }
+    }
     bt->ntiles32 = tb32;
     bt->ntiles64 = tb64;
     bt->nch = (int)cplate.size();
@@ -460,7 +527,8 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
         cudaMalloc(&bt->d_desc64, sizeof(PlateDesc) * count) != cudaSuccess ||
         cudaMalloc(&bt->d_cplate, sizeof(int) * bt->nch) != cudaSuccess ||
         cudaMalloc(&bt->d_active, sizeof(int) * count) != cudaSuccess ||
-        cudaMalloc(&bt->d_scal, sizeof(BatchScal) * count) != cudaSuccess)
+        cudaMalloc(&bt->d_scal, sizeof(BatchScal) * count) != cudaSuccess ||
+        cudaMalloc(&bt->d_range, sizeof(BatchRange)) != cudaSuccess)
         return bail(PD_ERR_OOM, "batch descriptors");
     cudaMemcpy(bt->d_desc32, d32.data(), sizeof(PlateDesc) * count, cudaMemcpyHostToDevice);
     cudaMemcpy(bt->d_desc64, d64.data(), sizeof(PlateDesc) * count, cudaMemcpyHostToDevice);
@@ -504,6 +572,7 @@ int pd_batch_destroy(pd_batch *bt)
     cudaFree(bt->d_cplate);
     cudaFree(bt->d_active);
     cudaFree(bt->d_scal);
+    cudaFree(bt->d_range);
     cudaFree(bt->ws);
     delete bt;
     return PD_OK;
@@ -520,10 +589,10 @@ int batch_two_iterations(pd_batch *bt, cudaStream_t s)
         double *prev = (k == 0) ? bt->rrB : bt->rrA;
         double *cur = (k == 0) ? bt->rrA : bt->rrB;
         k_batch_matvec<float><<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->np, bt->ntiles32, bt->p32, bt->q32,
-                                                         bt->part_t, bt->d_scal);
-        k_batch_update<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->x32, bt->r32, bt->p32,
+                                                         bt->part_t, bt->d_scal, bt->d_range);
+        k_batch_update<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->x32, bt->r32, bt->p32,
                                                   bt->q32, bt->part_t, prev, cur, bt->d_scal);
-        k_batch_pupdate<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->p32, bt->r32, prev, cur,
+        k_batch_pupdate<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->p32, bt->r32, prev, cur,
                                                    bt->d_scal);
     }
     PD_CUDA(cudaGetLastError());
@@ -541,22 +610,16 @@ extern "C" int pd_batch_cg_solve(pd_batch *bt, const double *const *b, double *c
     const auto t0 = std::chrono::steady_clock::now();
     const int np = bt->np;
     for (int i = 0; i < np; ++i) {
-        if (!b[i] || !u[i]) return fail(PD_ERR_INVALID, "NULL plate vector");
+        const int ci = bt->order[i];
+        if (!b[ci] || !u[ci]) return fail(PD_ERR_INVALID, "NULL plate vector");
         const size_t bytes = sizeof(double) * 2 * (size_t)bt->grids[i]->N;
-        PD_CUDA(cudaMemcpyAsync(bt->b64 + bt->offs[i], b[i], bytes, cudaMemcpyDeviceToDevice, s));
-        PD_CUDA(cudaMemcpyAsync(bt->u64 + bt->offs[i], u[i], bytes, cudaMemcpyDeviceToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(bt->b64 + bt->offs[i], b[ci], bytes, cudaMemcpyDeviceToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(bt->u64 + bt->offs[i], u[ci], bytes, cudaMemcpyDeviceToDevice, s));
     }
-    k_batch_project<<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, bt->d_cplate, bt->nch, bt->u64);
+    k_batch_project<<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, bt->d_cplate, bt->nch, nullptr, bt->u64);
     std::vector<double> part(bt->nch), bb(np, 0.0), rr(np, 0.0);
     std::vector<BatchScal> sc(np);
-    std::vector<int> active(np, 0), finished(np, 0), outer(np, 0), iters(np, 0);
-    // |P b|^2 per plate (residual of u = 0)
-    PD_CUDA(cudaMemsetAsync(bt->q64, 0, sizeof(double) * bt->total, s));
-    k_batch_resid<<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, bt->d_cplate, bt->nch, bt->r64, bt->b64, bt->q64,
-                                            bt->part_c);
-    PD_CUDA(cudaMemcpyAsync(part.data(), bt->part_c, sizeof(double) * bt->nch, cudaMemcpyDeviceToHost, s));
-    PD_CUDA(cudaStreamSynchronize(s));
-    std::vector<int> cpl(bt->nch);
+    std::vector<int> active(np, 0), outer(np, 0), iters(np, 0), fmv(np, 0), cpl(bt->nch);
     {
         int k = 0;
         for (int i = 0; i < np; ++i) {
@@ -564,102 +627,118 @@ extern "C" int pd_batch_cg_solve(pd_batch *bt, const double *const *b, double *c
             for (int j = 0; j < nc; ++j) cpl[k++] = i;
         }
     }
+    // |P b|^2 per plate (residual of u = 0)
+    PD_CUDA(cudaMemsetAsync(bt->q64, 0, sizeof(double) * bt->total, s));
+    k_batch_resid<<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, bt->d_cplate, bt->nch, nullptr, bt->r64, bt->b64,
+                                            bt->q64, bt->part_c, nullptr);
+    PD_CUDA(cudaMemcpyAsync(part.data(), bt->part_c, sizeof(double) * bt->nch, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < bt->nch; ++c) bb[cpl[c]] += part[c];
-    int total_iters = 0, passes = 0, status = PD_ERR_NOT_CONVERGED;
-    double worst = 0.0;
-    for (passes = 0; passes < 60; ++passes) {
-        // FP64 residual of every plate
-        k_batch_matvec<double><<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, np, bt->ntiles64, bt->u64, bt->q64, nullptr,
-                                                          nullptr);
-        k_batch_resid<<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, bt->d_cplate, bt->nch, bt->r64, bt->b64, bt->q64,
-                                                bt->part_c);
-        PD_CUDA(cudaMemcpyAsync(part.data(), bt->part_c, sizeof(double) * bt->nch, cudaMemcpyDeviceToHost, s));
-        PD_CUDA(cudaStreamSynchronize(s));
-        std::fill(rr.begin(), rr.end(), 0.0);
-        for (int c = 0; c < bt->nch; ++c) rr[cpl[c]] += part[c];
-        int n_active = 0;
-        worst = 0.0;
-        for (int i = 0; i < np; ++i) {
-            const double bn = bb[i] > 0 ? std::sqrt(bb[i]) : 1.0;
-            const double rel = std::sqrt(rr[i]) / bn;
-            worst = std::max(worst, rel);
-            finished[i] = (rel <= rtol) ? 1 : 0;
-            active[i] = !finished[i];
-            const double rn = std::sqrt(rr[i]);
-            const double need = 0.3 * rtol * bn / (rn > 0 ? rn : 1.0);
-            const double tau = std::min(0.5, std::max(need, 2e-5));
-            sc[i].tol2 = tau * tau;
-            sc[i].rn = rn;
-            sc[i].inv_rn = rn > 0 ? 1.0 / rn : 0.0;
-            sc[i].done = finished[i];
-            sc[i].iters = 0;
-            if (active[i]) {
-                ++n_active;
-                ++outer[i];
+    // the inner-loop graph (fixed pointers, reused by every group and pass)
+    constexpr int kPairsPerGraph = 16;   // 32 iterations per replay
+    if (!bt->graph) {
+        cudaGraph_t gr = nullptr;
+        bool ok = cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        for (int k = 0; k < kPairsPerGraph && ok; ++k) ok = batch_two_iterations(bt, bt->cap) == PD_OK;
+        ok = (cudaStreamEndCapture(bt->cap, &gr) == cudaSuccess) && ok;
+        if (!ok || cudaGraphInstantiate(&bt->graph, gr, 0) != cudaSuccess) bt->graph = nullptr;
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+    }
+    int status = PD_OK;
+    for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+        const auto &grp = bt->groups[gi];
+        PD_CUDA(cudaMemcpyAsync(bt->d_range, &bt->ranges[gi], sizeof(BatchRange), cudaMemcpyHostToDevice, s));
+        int group_iters = 0, group_status = PD_ERR_NOT_CONVERGED;
+        for (int pass = 0; pass < 60; ++pass) {
+            // FP64 residual of the group's plates (other plates skip)
+            for (int i = 0; i < np; ++i) {
+                sc[i] = BatchScal{};
+                sc[i].done = (i >= grp.first && i < grp.second) ? 0 : 1;
             }
-        }
-        if (n_active == 0) {
-            status = PD_OK;
-            break;
-        }
-        if (total_iters >= max_iter) break;
-        PD_CUDA(cudaMemcpyAsync(bt->d_scal, sc.data(), sizeof(BatchScal) * np, cudaMemcpyHostToDevice, s));
-        PD_CUDA(cudaMemcpyAsync(bt->d_active, active.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
-        k_batch_start<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->r32, bt->p32, bt->x32,
-                                                bt->r64, bt->rrB, bt->d_scal);
-        PD_CUDA(cudaGetLastError());
-        // inner loop: chunks of iterations as one graph
-        constexpr int kPairsPerGraph = 16;   // 32 iterations per replay
-        if (!bt->graph) {
-            cudaGraph_t gr = nullptr;
-            bool ok = cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-            for (int k = 0; k < kPairsPerGraph && ok; ++k) ok = batch_two_iterations(bt, bt->cap) == PD_OK;
-            ok = (cudaStreamEndCapture(bt->cap, &gr) == cudaSuccess) && ok;
-            if (!ok || cudaGraphInstantiate(&bt->graph, gr, 0) != cudaSuccess) bt->graph = nullptr;
-            if (gr) cudaGraphDestroy(gr);
-            cudaGetLastError();
-        }
-        int issued = 0;
-        while (total_iters + issued < max_iter) {
-            if (bt->graph) {
-                PD_CUDA(cudaGraphLaunch(bt->graph, s));
-            } else {
-                for (int k = 0; k < kPairsPerGraph; ++k) {
-                    int rc = batch_two_iterations(bt, s);
-                    if (rc) return rc;
-                }
-            }
-            issued += 2 * kPairsPerGraph;
-            PD_CUDA(cudaMemcpyAsync(sc.data(), bt->d_scal, sizeof(BatchScal) * np, cudaMemcpyDeviceToHost, s));
+            PD_CUDA(cudaMemcpyAsync(bt->d_scal, sc.data(), sizeof(BatchScal) * np, cudaMemcpyHostToDevice, s));
+            k_batch_matvec<double><<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, np, bt->ntiles64, bt->u64, bt->q64,
+                                                              nullptr, bt->d_scal, bt->d_range);
+            k_batch_resid<<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, bt->d_cplate, bt->nch, bt->d_range, bt->r64,
+                                                    bt->b64, bt->q64, bt->part_c, bt->d_scal);
+            PD_CUDA(cudaMemcpyAsync(part.data(), bt->part_c, sizeof(double) * bt->nch, cudaMemcpyDeviceToHost, s));
             PD_CUDA(cudaStreamSynchronize(s));
-            bool all = true;
-            for (int i = 0; i < np; ++i) all = all && sc[i].done;
-            if (all) break;
+            int n_active = 0;
+            for (int i = grp.first; i < grp.second; ++i) rr[i] = 0.0;
+            for (int c = 0; c < bt->nch; ++c)
+                if (cpl[c] >= grp.first && cpl[c] < grp.second) rr[cpl[c]] += part[c];
+            for (int i = 0; i < np; ++i) {
+                active[i] = 0;
+                sc[i].done = 1;
+                if (i < grp.first || i >= grp.second) continue;
+                ++fmv[i];
+                const double bn = bb[i] > 0 ? std::sqrt(bb[i]) : 1.0;
+                const double rn = std::sqrt(rr[i]);
+                if (rn / bn <= rtol) continue;
+                active[i] = 1;
+                ++outer[i];
+                ++n_active;
+                const double need = 0.3 * rtol * bn / (rn > 0 ? rn : 1.0);
+                const double tau = std::min(0.5, std::max(need, 2e-5));
+                sc[i].tol2 = tau * tau;
+                sc[i].rn = rn;
+                sc[i].inv_rn = rn > 0 ? 1.0 / rn : 0.0;
+                sc[i].done = 0;
+            }
+            if (n_active == 0) {
+                group_status = PD_OK;
+                break;
+            }
+            if (group_iters >= max_iter) break;
+            PD_CUDA(cudaMemcpyAsync(bt->d_scal, sc.data(), sizeof(BatchScal) * np, cudaMemcpyHostToDevice, s));
+            PD_CUDA(cudaMemcpyAsync(bt->d_active, active.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+            k_batch_start<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->r32, bt->p32, bt->x32,
+                                                    bt->r64, bt->rrB, bt->d_scal);
+            PD_CUDA(cudaGetLastError());
+            int issued = 0;
+            while (group_iters + issued < max_iter) {
+                if (bt->graph) {
+                    PD_CUDA(cudaGraphLaunch(bt->graph, s));
+                } else {
+                    for (int k = 0; k < kPairsPerGraph; ++k) {
+                        int rc = batch_two_iterations(bt, s);
+                        if (rc) return rc;
+                    }
+                }
+                issued += 2 * kPairsPerGraph;
+                PD_CUDA(cudaMemcpyAsync(sc.data(), bt->d_scal, sizeof(BatchScal) * np, cudaMemcpyDeviceToHost, s));
+                PD_CUDA(cudaStreamSynchronize(s));
+                bool all = true;
+                for (int i = grp.first; i < grp.second; ++i) all = all && sc[i].done;
+                if (all) break;
+            }
+            int mx = 0;
+            for (int i = grp.first; i < grp.second; ++i) {
+                iters[i] += sc[i].iters;
+                mx = std::max(mx, sc[i].iters);
+            }
+            group_iters += mx;
+            k_batch_correct<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->u64, bt->x32,
+                                                      bt->d_scal, bt->d_active);
+            PD_CUDA(cudaGetLastError());
         }
-        int mx = 0;
-        for (int i = 0; i < np; ++i) {
-            iters[i] += sc[i].iters;
-            mx = std::max(mx, sc[i].iters);
-        }
-        total_iters += mx;
-        k_batch_correct<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->u64, bt->x32, bt->d_scal,
-                                                  bt->d_active);
-        PD_CUDA(cudaGetLastError());
+        if (group_status != PD_OK) status = PD_ERR_NOT_CONVERGED;
     }
     for (int i = 0; i < np; ++i) {
         const size_t bytes = sizeof(double) * 2 * (size_t)bt->grids[i]->N;
-        PD_CUDA(cudaMemcpyAsync(u[i], bt->u64 + bt->offs[i], bytes, cudaMemcpyDeviceToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(u[bt->order[i]], bt->u64 + bt->offs[i], bytes, cudaMemcpyDeviceToDevice, s));
     }
     PD_CUDA(cudaStreamSynchronize(s));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) {
         for (int i = 0; i < np; ++i) {
             const double bn = bb[i] > 0 ? std::sqrt(bb[i]) : 1.0;
-            stats[i].iterations = iters[i];
-            stats[i].outer = outer[i];
-            stats[i].f64_matvecs = passes + 1;
-            stats[i].rel_residual = std::sqrt(rr[i]) / bn;
-            stats[i].seconds = secs;
+            pd_cg_stats &st = stats[bt->order[i]];
+            st.iterations = iters[i];
+            st.outer = outer[i];
+            st.f64_matvecs = fmv[i];
+            st.rel_residual = std::sqrt(rr[i]) / bn;
+            st.seconds = secs;
         }
     }
     if (status != PD_OK) return fail(PD_ERR_NOT_CONVERGED, "batched CG reached its iteration cap");
