@@ -197,14 +197,15 @@ int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_b
 /* Chooses the method PD_METHOD_AUTO resolves to for each precision:
  * method = PD_METHOD_STENCIL or PD_METHOD_FFT pins it (both precisions);
  * PD_METHOD_AUTO clears the choice (AUTO then means the stencil until
- * pd_autotune has run).  The FFT method exists for 2D grids without a
- * modulus field.  Host-only; no device work. */
+ * pd_autotune has run).  The FFT method exists for 2D and 3D grids
+ * without a modulus field.  Host-only; no device work. */
 int pd_set_method(pd_grid *g, uint32_t method);
 
 /* Measures both methods of K u for the precision(s) in flags (PD_F32 and/or
  * PD_F64) on scratch vectors of this grid (allocated and freed inside the
- * call, CUDA events on `stream`, a few warm-up and timed launches each) and
- * records the faster one for PD_METHOD_AUTO.  times_ms: host double [4] or
+ * call, CUDA events on `stream`; three warm-up launches each, then five
+ * alternating trials of ten launches per method, each method keeping its
+ * fastest trial) and records the faster one for PD_METHOD_AUTO.  times_ms: host double [4] or
  * NULL, receives {stencil f32, fft f32, stencil f64, fft f64} in ms (0 where
  * not measured). */
 int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream);

@@ -33,7 +33,7 @@ namespace pd {
 namespace {
 
 constexpr int kBlk = 256;
-constexpr int kRedBlocks = 152 * 4;   // grid of the streaming kernels (grid-stride)
+constexpr int kRedMax = 152 * 8;      // upper bound of the streaming kernels' grid (grid-stride)
 constexpr int kChunk = 32;            // inner iterations per graph launch
 
 struct CgScal {
@@ -47,6 +47,30 @@ struct CgScal {
     int iters;
     unsigned int retire[4];
 };
+
+// 16 bytes of T: the streaming kernels move whole packs with one vector load
+// or store.  A kernel gets the number of packs `nv` it may treat that way (0
+// when a pointer is not 16-byte aligned) and handles elements [nv * n, L) one
+// by one.
+template <typename T>
+struct alignas(16) Pk {
+    static constexpr int n = 16 / (int)sizeof(T);
+    T v[n];
+};
+
+template <typename T>
+__device__ __forceinline__ Pk<T> ldp(const T *a, int64_t j)
+{
+    return reinterpret_cast<const Pk<T> *>(a)[j];
+}
+
+template <typename T>
+__device__ __forceinline__ void stp(T *a, int64_t j, const Pk<T> &v)
+{
+    reinterpret_cast<Pk<T> *>(a)[j] = v;
+}
+
+__host__ __device__ inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Deterministic grid reduction whose last block returns true in thread 0.
 __device__ __forceinline__ bool grid_last(double block_value, double *partial, double *out, unsigned int *retire,
@@ -76,8 +100,9 @@ __device__ __forceinline__ bool grid_last(double block_value, double *partial, d
 
 // x += alpha p ; r -= alpha q ; rr_new = r.r ; last block: beta, rr, done, iters.
 template <typename T>
-__global__ void __launch_bounds__(kBlk)
-k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_t L, CgScal *sc, double *partial)
+__global__ void __launch_bounds__(kBlk, 4)
+k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_t L, int64_t nv, CgScal *sc,
+            double *partial)
 {
     __shared__ double red[kBlk / 32];
     __shared__ int s_done;
@@ -90,7 +115,20 @@ k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_
     if (s_done) return;
     const T a = (T)s_alpha;
     T acc = T(0);
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    for (int64_t j = t0; j < nv; j += st) {
+        Pk<T> xv = ldp(x, j), rv = ldp(r, j);
+        const Pk<T> pv = ldp(p, j), qv = ldp(q, j);
+#pragma unroll
+        for (int e = 0; e < Pk<T>::n; ++e) {
+            xv.v[e] += a * pv.v[e];
+            rv.v[e] -= a * qv.v[e];
+            acc += rv.v[e] * rv.v[e];
+        }
+        stp(x, j, xv);
+        stp(r, j, rv);
+    }
+    for (int64_t i = nv * Pk<T>::n + t0; i < L; i += st) {
         const T xi = x[i] + a * p[i];
         const T ri = r[i] - a * q[i];
         x[i] = xi;
@@ -109,23 +147,37 @@ k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_
 
 // p = r + beta p
 template <typename T>
-__global__ void __launch_bounds__(kBlk) k_cg_p(T *p, const T *__restrict__ r, int64_t L, const CgScal *sc)
+__global__ void __launch_bounds__(kBlk)
+k_cg_p(T *p, const T *__restrict__ r, int64_t L, int64_t nv, const CgScal *sc)
 {
     if (sc->done) return;
     const T beta = (T)sc->beta;
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk)
-        p[i] = r[i] + beta * p[i];
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    for (int64_t j = t0; j < nv; j += st) {
+        Pk<T> pv = ldp(p, j);
+        const Pk<T> rv = ldp(r, j);
+#pragma unroll
+        for (int e = 0; e < Pk<T>::n; ++e) pv.v[e] = rv.v[e] + beta * pv.v[e];
+        stp(p, j, pv);
+    }
+    for (int64_t i = nv * Pk<T>::n + t0; i < L; i += st) p[i] = r[i] + beta * p[i];
 }
 
-// out = a . b (FP64 accumulation in the kernel's precision per thread)
+// out = a . b (accumulated per thread in the kernel's precision, FP64 across threads)
 template <typename T>
 __global__ void __launch_bounds__(kBlk)
-k_dot(const T *__restrict__ a, const T *__restrict__ b, int64_t L, double *out, double *partial, unsigned int *retire)
+k_dot(const T *__restrict__ a, const T *__restrict__ b, int64_t L, int64_t nv, double *out, double *partial,
+      unsigned int *retire)
 {
     __shared__ double red[kBlk / 32];
     T acc = T(0);
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk)
-        acc += a[i] * b[i];
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    for (int64_t j = t0; j < nv; j += st) {
+        const Pk<T> av = ldp(a, j), bv = ldp(b, j);
+#pragma unroll
+        for (int e = 0; e < Pk<T>::n; ++e) acc += av.v[e] * bv.v[e];
+    }
+    for (int64_t i = nv * Pk<T>::n + t0; i < L; i += st) acc += a[i] * b[i];
     const double bs = block_sum((double)acc, red);
     grid_last(bs, partial, out, retire, red);
 }
@@ -151,13 +203,28 @@ k_resid(double *r, const double *__restrict__ b, const double *__restrict__ Ku, 
 }
 
 // Inner start (mixed): r32 = r64 * inv, p32 = r32, x32 = 0, sc->rr = r32.r32, done flag.
+// nv counts packs of four floats (two packs of doubles each).
 __global__ void __launch_bounds__(kBlk)
-k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64, int64_t L, double inv, double tau2,
-              CgScal *sc, double *partial)
+k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64, int64_t L, int64_t nv, double inv,
+              double tau2, CgScal *sc, double *partial)
 {
     __shared__ double red[kBlk / 32];
     float acc = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    for (int64_t j = t0; j < nv; j += st) {
+        const Pk<double> a = ldp(r64, 2 * j), b = ldp(r64, 2 * j + 1);
+        Pk<float> v;
+        v.v[0] = (float)(a.v[0] * inv);
+        v.v[1] = (float)(a.v[1] * inv);
+        v.v[2] = (float)(b.v[0] * inv);
+        v.v[3] = (float)(b.v[1] * inv);
+        stp(r32, j, v);
+        stp(p32, j, v);
+        stp(x32, j, Pk<float>{});
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc += v.v[e] * v.v[e];
+    }
+    for (int64_t i = nv * 4 + t0; i < L; i += st) {
         const float v = (float)(r64[i] * inv);
         r32[i] = v;
         p32[i] = v;
@@ -187,9 +254,21 @@ k_plain_start(double *p, const double *__restrict__ r, int64_t L, double tol2, C
 
 // u += s * x32, then x32 = 0 (a reliable update folds the FP32 increment into u).
 __global__ void __launch_bounds__(kBlk)
-k_correct_zero(double *u, float *x32, double s, int64_t L)
+k_correct_zero(double *u, float *x32, double s, int64_t L, int64_t nv)
 {
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    for (int64_t j = t0; j < nv; j += st) {
+        const Pk<float> x = ldp(x32, j);
+        Pk<double> a = ldp(u, 2 * j), b = ldp(u, 2 * j + 1);
+        a.v[0] += s * (double)x.v[0];
+        a.v[1] += s * (double)x.v[1];
+        b.v[0] += s * (double)x.v[2];
+        b.v[1] += s * (double)x.v[3];
+        stp(u, 2 * j, a);
+        stp(u, 2 * j + 1, b);
+        stp(x32, j, Pk<float>{});
+    }
+    for (int64_t i = nv * 4 + t0; i < L; i += st) {
         u[i] += s * (double)x32[i];
         x32[i] = 0.f;
     }
@@ -201,13 +280,29 @@ k_correct_zero(double *u, float *x32, double s, int64_t L)
 // direction CG would have formed had its recursive residual been exact.
 // sc->rr = r32.r32, sc->tol2 = tol2 (absolute), the inner loop is re-armed.
 __global__ void __launch_bounds__(kBlk)
-k_replace(float *r32, float *p32, const double *__restrict__ r64, int64_t L, double inv, double tol2, CgScal *sc,
-          double *partial)
+k_replace(float *r32, float *p32, const double *__restrict__ r64, int64_t L, int64_t nv, double inv, double tol2,
+          CgScal *sc, double *partial)
 {
     __shared__ double red[kBlk / 32];
     const float beta = (float)sc->beta;
     float acc = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    for (int64_t j = t0; j < nv; j += st) {
+        const Pk<double> a = ldp(r64, 2 * j), b = ldp(r64, 2 * j + 1);
+        Pk<float> v, pv = ldp(p32, j);
+        v.v[0] = (float)(a.v[0] * inv);
+        v.v[1] = (float)(a.v[1] * inv);
+        v.v[2] = (float)(b.v[0] * inv);
+        v.v[3] = (float)(b.v[1] * inv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            pv.v[e] = v.v[e] + beta * pv.v[e];
+            acc += v.v[e] * v.v[e];
+        }
+        stp(p32, j, pv);
+        stp(r32, j, v);
+    }
+    for (int64_t i = nv * 4 + t0; i < L; i += st) {
         const float v = (float)(r64[i] * inv);
         p32[i] = v + beta * p32[i];
         r32[i] = v;
@@ -237,8 +332,10 @@ struct CgWs {
     double *r64, *q64, *p64;    // FP64 residual, operator output, direction
     float *r32, *p32, *q32, *x32;
     CgScal *sc;
-    double *partial;            // >= max(kRedBlocks, stencil CTAs) doubles
+    double *partial;            // >= max(red, stencil CTAs) doubles
     double *partial2;
+    int red = 0;                // grid of the streaming kernels: resident CTAs on all SMs, <= kRedMax
+    int red64 = 0;              // the same for the FP64 update
     cudaStream_t cap = nullptr; // capture stream
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [0] FP32 inner, [1] FP64 plain
     const void *graph_key[2] = {nullptr, nullptr};
@@ -250,7 +347,7 @@ int ensure_ws(pd_grid *g, CgWs *&w)
     const int64_t L = (int64_t)g->dim * g->N;
     const int nblk = std::max(stencil_blocks(g, true, g->has_E || g->broken_total > 0),
                               stencil_blocks(g, false, g->has_E || g->broken_total > 0));
-    const size_t nparts = (size_t)std::max(nblk, kRedBlocks) + 64;
+    const size_t nparts = (size_t)std::max(nblk, kRedMax) + 64;
     const size_t need = sizeof(double) * 3 * L + sizeof(float) * 4 * L + sizeof(CgScal) + 2 * sizeof(double) * nparts + 1024;
     w = (CgWs *)g->cg;
     if (w && w->bytes >= need) return PD_OK;
@@ -258,6 +355,13 @@ int ensure_ws(pd_grid *g, CgWs *&w)
         w = new CgWs();
         g->cg = w;
         PD_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+        int dev = 0, sms = 0, occ = 0;
+        PD_CUDA(cudaGetDevice(&dev));
+        PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_update<float>, kBlk, 0));
+        w->red = std::max(1, std::min(kRedMax, sms * std::max(occ, 1)));
+        PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_update<double>, kBlk, 0));
+        w->red64 = std::max(1, std::min(kRedMax, sms * std::max(occ, 1)));
     }
     if (w->base) cudaFree(w->base);
     for (int i = 0; i < 2; ++i)
@@ -299,17 +403,22 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s)
     } else {
         rc = matvec(g, 1, p, q, fl, s);
         if (rc == PD_OK) {
-            if (f64) k_dot<double><<<kRedBlocks, kBlk, 0, s>>>(w->p64, w->q64, L, &w->sc->pq, w->partial2, &w->sc->retire[3]);
-            else k_dot<float><<<kRedBlocks, kBlk, 0, s>>>(w->p32, w->q32, L, &w->sc->pq, w->partial2, &w->sc->retire[3]);
+            if (f64)
+                k_dot<double><<<w->red, kBlk, 0, s>>>(w->p64, w->q64, L, L / 2, &w->sc->pq, w->partial2,
+                                                     &w->sc->retire[3]);
+            else
+                k_dot<float><<<w->red, kBlk, 0, s>>>(w->p32, w->q32, L, L / 4, &w->sc->pq, w->partial2,
+                                                    &w->sc->retire[3]);
         }
     }
     if (rc) return rc;
     if (f64) {
-        k_cg_update<double><<<kRedBlocks, kBlk, 0, s>>>(x64, w->r64, w->p64, w->q64, L, w->sc, w->partial2);
-        k_cg_p<double><<<kRedBlocks, kBlk, 0, s>>>(w->p64, w->r64, L, w->sc);
+        const int64_t nv = aligned16(x64) ? L / 2 : 0;
+        k_cg_update<double><<<w->red64, kBlk, 0, s>>>(x64, w->r64, w->p64, w->q64, L, nv, w->sc, w->partial2);
+        k_cg_p<double><<<w->red64, kBlk, 0, s>>>(w->p64, w->r64, L, L / 2, w->sc);
     } else {
-        k_cg_update<float><<<kRedBlocks, kBlk, 0, s>>>(w->x32, w->r32, w->p32, w->q32, L, w->sc, w->partial2);
-        k_cg_p<float><<<kRedBlocks, kBlk, 0, s>>>(w->p32, w->r32, L, w->sc);
+        k_cg_update<float><<<w->red, kBlk, 0, s>>>(w->x32, w->r32, w->p32, w->q32, L, L / 4, w->sc, w->partial2);
+        k_cg_p<float><<<w->red, kBlk, 0, s>>>(w->p32, w->r32, L, L / 4, w->sc);
     }
     PD_CUDA(cudaGetLastError());
     return PD_OK;
@@ -374,7 +483,7 @@ int true_residual(pd_grid *g, CgWs *w, const double *b, const double *u, cudaStr
     const int64_t L = (int64_t)g->dim * g->N;
     int rc = matvec(g, 1, u, w->q64, PD_F64 | PD_PROJECT, s);
     if (rc) return rc;
-    k_resid<<<kRedBlocks, kBlk, 0, s>>>(w->r64, b, w->q64, g->has_cons ? g->d_cons : nullptr, g->N, g->dim,
+    k_resid<<<w->red, kBlk, 0, s>>>(w->r64, b, w->q64, g->has_cons ? g->d_cons : nullptr, g->N, g->dim,
                                         &w->sc->aux, w->partial2, &w->sc->retire[3]);
     PD_CUDA(cudaGetLastError());
     PD_CUDA(cudaMemcpyAsync(g->h_pinned, &w->sc->aux, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -415,7 +524,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
     int rc = ensure_ws(g, w);
     if (rc) return rc;
     const int64_t L = (int64_t)g->dim * g->N;
-    const int blocks = kRedBlocks;
+    const int blocks = w->red;
     if (g->has_cons) k_zero_constrained<<<blocks, kBlk, 0, s>>>(u, g->d_cons, g->N, g->dim);
 
     // |P b|^2
@@ -471,7 +580,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
             status = PD_OK;
         } else {
             double rr_ref = rr / (s0 * s0);
-            k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->r64, L, 1.0 / s0,
+            k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->r64, L, L / 4, 1.0 / s0,
                                                   std::max(kRU * kRU, tgt2 / rr_ref), w->sc, w->partial2);
             for (int phase = 0; phase < 1000; ++phase) {
                 ++outer;
@@ -479,7 +588,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
                 rc = inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it);
                 total_iters += it;
                 if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
-                k_correct_zero<<<blocks, kBlk, 0, s>>>(u, w->x32, s0, L);
+                k_correct_zero<<<blocks, kBlk, 0, s>>>(u, w->x32, s0, L, aligned16(u) ? L / 4 : 0);
                 PD_CUDA(cudaGetLastError());
                 rc = true_residual(g, w, b, u, s, &rr);
                 if (rc) return rc;
@@ -488,7 +597,8 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
                 if (rel <= rtol) { status = PD_OK; break; }
                 if (total_iters >= max_iter || !std::isfinite(rel)) break;
                 rr_ref = rr / (s0 * s0);
-                k_replace<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->r64, L, 1.0 / s0, std::max(kRU * kRU * rr_ref, tgt2),
+                k_replace<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->r64, L, L / 4, 1.0 / s0,
+                                                  std::max(kRU * kRU * rr_ref, tgt2),
                                                   w->sc, w->partial2);
                 PD_CUDA(cudaGetLastError());
             }

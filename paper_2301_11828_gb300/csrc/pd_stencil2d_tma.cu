@@ -1,5 +1,5 @@
 // pd_stencil2d_tma.cu -- FP32 2D stencil (TBT form, Sec. 3.2-3.4) for sm_103a:
-// persistent CTAs, TMA-fed double-buffered halo tiles, packed FP32x2 math.
+// persistent CTAs, TMA-fed multi-buffered halo tiles, packed FP32x2 math.
 //
 // Same operator as pd_stencil2d.cu:
 //     (K u)_p = Kd_p u_p - sum_{o in half} c(o) (u~_{p+o} + u~_{p-o}),
@@ -8,8 +8,9 @@
 //     cp.async.bulk.tensor (TMA) per tile into shared memory.  The tensor
 //     map's out-of-bounds fill supplies the zero padding outside the grid, so
 //     no thread tests bounds on the way in.  While a CTA computes one tile the
-//     TMA engine already loads the next one into the other buffer; an mbarrier
-//     with an expected byte count signals arrival.  Every wait has an
+//     TMA engine already loads its next kStages - 1 tiles into the other
+//     buffers (enough bytes in flight per SM to cover HBM latency); an mbarrier
+//     per buffer with an expected byte count signals arrival.  Every wait has an
 //     iteration limit; on expiry the kernel records an error code and returns.
 //   * The x start of the box is rounded down to a 16-byte boundary (TMA rule)
 //     and the box is widened to cover the halo.
@@ -99,6 +100,7 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+constexpr int kStages = 3;               // halo tiles in flight or in use per CTA
 constexpr int kTXt = 64;                 // outputs per tile along x
 constexpr int kRt = 8;                   // outputs per thread along y
 constexpr int kTYt = kGY2 * kRt;         // outputs per tile along y (32)
@@ -118,8 +120,10 @@ struct __align__(16) PackTab {
     float v[4 * kPairs + 4];
 };
 
+// Three CTAs per SM (three halo tiles in flight each) up to M = 4; register
+// growth beyond that leaves two.
 template <int M>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (M <= 4 ? 3 : 2))
 k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u, float *__restrict__ out, int nx,
             int ny, int64_t N, int tiles_x, int tiles_y, int ntiles, const uint8_t *__restrict__ cons,
             int project_in, int project_out, const float *__restrict__ kd, float scale, PackTab<M> tab,
@@ -131,21 +135,29 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
     constexpr int NP = PackTab<M>::kPairs;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *const sbase = reinterpret_cast<float *>(smem_raw);   // buffer k at sbase + 2 * PLANE * k
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[kStages];
     __shared__ int s_abort;
+    // Edge-class diagonal table (Kd by clipped face distances), kept in shared
+    // memory when small so that edge outputs do not wait on global loads.
+    constexpr int KDS = (M <= 3) ? 3 * (M + 1) * (M + 1) * (M + 1) * (M + 1) : 1;
+    __shared__ float s_kd[KDS];
+    if (M <= 3)
+        for (int i = threadIdx.x; i < KDS; i += kThreads) s_kd[i] = __ldg(kd + i);
 
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
     __syncthreads();
 
     const int tx = threadIdx.x % kTXt, ty = threadIdx.x / kTXt;
+    // Tile t lies in tile row r = t / tiles_x; the columns of each row are
+    // rotated by r so that a persistent CTA, which takes every gridDim.x-th
+    // tile, meets left/right edge tiles (slower epilogue) as often as the others.
     auto tile_coords = [&](int t, int &x0, int &y0, int &b) {
-        x0 = (t % tiles_x) * kTXt;
         const int r = t / tiles_x;
+        x0 = ((t - r * tiles_x + r) % tiles_x) * kTXt;
         y0 = (r % tiles_y) * kTYt;
         b = r / tiles_y;
     };
@@ -157,21 +169,34 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         tma_load_3d(sbase + 2 * PLANE * which, &map, x0 - XL, y0 - M, 2 * b, &bars[which]);
     };
 
-    int it = 0, t_abort = 0;
-    if (threadIdx.x == 0 && blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    // The CTA's k-th tile is blockIdx.x + k * gridDim.x; it lands in buffer k % kStages,
+    // whose barrier completes its (k / kStages)-th phase.  kStages - 1 loads run ahead.
+    int it = 0, n_issued = 0;   // n_issued: loads issued so far (thread 0 only)
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kStages - 1; ++k) {
+            const int64_t tk = blockIdx.x + (int64_t)k * gridDim.x;
+            if (tk < ntiles) {
+                issue((int)tk, k);
+                ++n_issued;
+            }
+        }
     double dot_blk_total = 0.0;   // per-thread, summed over this CTA's tiles (dot needs one batch)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-        const int cur = it & 1;
-        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x, cur ^ 1);
-        if (!mbar_wait(&bars[cur], (it >> 1) & 1)) {
+        const int cur = it % kStages;
+        if (threadIdx.x == 0) {
+            // buffer (it - 1) % kStages was released by the barrier that ended the last iteration
+            const int64_t tn = t + (int64_t)(kStages - 1) * gridDim.x;
+            if (tn < ntiles) {
+                issue((int)tn, (it + kStages - 1) % kStages);
+                ++n_issued;
+            }
+        }
+        if (!mbar_wait(&bars[cur], (it / kStages) & 1)) {
             atomicExch(err, 1);
             s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) {
-            t_abort = t;
-            break;
-        }
+        if (s_abort) break;
         int x0, y0, b;
         tile_coords(t, x0, y0, b);
         float *sx = sbase + 2 * PLANE * cur, *sy = sx + PLANE;
@@ -187,106 +212,138 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
             __syncthreads();
         }
 
-        const float *colx = sx + (ty * kRt) * BX + tx + XL;
-        const float *coly = sy + (ty * kRt) * BX + tx + XL;
-        u64 a1[kRt], a2[kRt];
+        // The tile body is instantiated twice: tiles whose every output keeps a
+        // full horizon inside the grid (and need no projection or dot) take a
+        // copy without the edge table, bounds tests and projection, so the
+        // compiler schedules the common case without the rare paths.
+        auto tile_body = [&](auto EDGE) {
+            constexpr bool edge = decltype(EDGE)::value;
+            const float *colx = sx + (ty * kRt) * BX + tx + XL;
+            const float *coly = sy + (ty * kRt) * BX + tx + XL;
+            u64 a1[kRt], a2[kRt];
 #pragma unroll
-        for (int r = 0; r < kRt; ++r) { a1[r] = 0ull; a2[r] = 0ull; }
-        static_for<1, M + 1>([&](auto OX) {
-            constexpr int ox = decltype(OX)::value;
-            constexpr int My = isqrt_c(M * M - ox * ox);
-            u64 wp[WL], wm[WL];
+            for (int r = 0; r < kRt; ++r) { a1[r] = 0ull; a2[r] = 0ull; }
+            static_for<1, M + 1>([&](auto OX) {
+                constexpr int ox = decltype(OX)::value;
+                constexpr int My = isqrt_c(M * M - ox * ox);
+                u64 wp[WL], wm[WL];
 #pragma unroll
-            for (int i = 0; i < WL; ++i) {
-                wp[i] = pk(colx[i * BX + ox], coly[i * BX + ox]);
-                wm[i] = pk(colx[i * BX - ox], coly[i * BX - ox]);
-            }
-            static_for<-My, My + 1>([&](auto OY) {
+                for (int i = 0; i < WL; ++i) {
+                    wp[i] = pk(colx[i * BX + ox], coly[i * BX + ox]);
+                    wm[i] = pk(colx[i * BX - ox], coly[i * BX - ox]);
+                }
+                static_for<-My, My + 1>([&](auto OY) {
+                    constexpr int oy = decltype(OY)::value;
+                    constexpr int pi = pair_index2(M, ox, oy);
+                    const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
+                    const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
+#pragma unroll
+                    for (int r = 0; r < kRt; ++r) {
+                        const u64 s = fadd2(wp[r + M + oy], wm[r + M - oy]);
+                        a1[r] = ffma2(c1, s, a1[r]);
+                        a2[r] = ffma2(c2, s, a2[r]);
+                    }
+                });
+            });
+            u64 w0[WL];
+#pragma unroll
+            for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
+            static_for<1, M + 1>([&](auto OY) {
                 constexpr int oy = decltype(OY)::value;
-                constexpr int pi = pair_index2(M, ox, oy);
+                constexpr int pi = pair_index2(M, 0, oy);
                 const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
                 const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
 #pragma unroll
                 for (int r = 0; r < kRt; ++r) {
-                    const u64 s = fadd2(wp[r + M + oy], wm[r + M - oy]);
+                    const u64 s = fadd2(w0[r + M + oy], w0[r + M - oy]);
                     a1[r] = ffma2(c1, s, a1[r]);
                     a2[r] = ffma2(c2, s, a2[r]);
                 }
             });
-        });
-        u64 w0[WL];
-#pragma unroll
-        for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
-        static_for<1, M + 1>([&](auto OY) {
-            constexpr int oy = decltype(OY)::value;
-            constexpr int pi = pair_index2(M, 0, oy);
-            const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
-            const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
-#pragma unroll
-            for (int r = 0; r < kRt; ++r) {
-                const u64 s = fadd2(w0[r + M + oy], w0[r + M - oy]);
-                a1[r] = ffma2(c1, s, a1[r]);
-                a2[r] = ffma2(c2, s, a2[r]);
-            }
-        });
 
-        float *ob = out + (int64_t)b * 2 * N;
-        const int gx = x0 + tx;
-        float dot = 0.f;
-        // Tiles whose every output keeps a full horizon inside the grid need no
-        // edge table, no bounds test and (unless asked) no projection.
+            float *ob = out + (int64_t)b * 2 * N;
+            const int gx = x0 + tx;
+            // outputs whose horizon stays inside the grid: interior Kd, no tests
+            auto interior_epilogue = [&]() {
+                const float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
+                float *o0 = ob + (int64_t)(y0 + ty * kRt) * nx + gx;
+#pragma unroll
+                for (int r = 0; r < kRt; ++r) {
+                    const float2 up = upk(w0[r + M]);
+                    const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                    const float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
+                    const float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
+                    o0[(int64_t)r * nx] = fx * scale;
+                    o0[(int64_t)r * nx + N] = fy * scale;
+                }
+            };
+            if constexpr (!edge) {
+                interior_epilogue();
+            } else {
+                // General epilogue.  Every branch below is uniform over the tile or
+                // the warp, so tiles and warps that need no edge handling do not
+                // execute it, predicated off or otherwise.
+                const bool full = (x0 + kTXt <= nx) && (y0 + kTYt <= ny);   // no bounds test needed
+                const bool lane_xe = (gx < M) || (gx >= nx - M);
+                const bool warp_xe = __any_sync(0xffffffffu, lane_xe);     // warp holds an x-edge output
+                const int gy0 = y0 + ty * kRt;
+                const bool warp_ye = (gy0 < M) || (gy0 + kRt > ny - M);     // warp holds a y-edge row
+                if (full && !warp_xe && !warp_ye && !project_out && !dot_partial) {
+                    interior_epilogue();   // this warp's outputs are all interior
+                    return;
+                }
+                const float kxx0 = tab.v[4 * NP], kxy0 = tab.v[4 * NP + 1], kyy0 = tab.v[4 * NP + 2];
+                float *o0 = ob + (int64_t)gy0 * nx + gx;
+                const uint8_t *m0 = cons + (int64_t)gy0 * nx + gx;
+                float dot = 0.f;
+#pragma unroll
+                for (int r = 0; r < kRt; ++r) {
+                    const int gy = gy0 + r;
+                    if (!full && !(gx < nx && gy < ny)) continue;
+                    const float2 up = upk(w0[r + M]);
+                    const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                    const float ax = x1.x + x2.y, ay = x1.y + x2.x;
+                    float kxx = kxx0, kxy = kxy0, kyy = kyy0;
+                    if (warp_xe || gy < M || gy >= ny - M) {   // warp-uniform
+                        const int c0 = min(gx, M), c1 = min(nx - 1 - gx, M), d0 = min(gy, M), d1 = min(ny - 1 - gy, M);
+                        const int cls = ((c0 * (M + 1) + c1) * (M + 1) + d0) * (M + 1) + d1;
+                        if constexpr (M <= 3) {
+                            kxx = s_kd[3 * cls];
+                            kxy = s_kd[3 * cls + 1];
+                            kyy = s_kd[3 * cls + 2];
+                        } else {
+                            kxx = __ldg(kd + 3 * cls);
+                            kxy = __ldg(kd + 3 * cls + 1);
+                            kyy = __ldg(kd + 3 * cls + 2);
+                        }
+                    }
+                    float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
+                    float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
+                    if (project_out) {
+                        const uint8_t m = __ldg(m0 + (int64_t)r * nx);
+                        if (m & 1) fx = 0.f;
+                        if (m & 2) fy = 0.f;
+                    }
+                    fx *= scale;
+                    fy *= scale;
+                    o0[(int64_t)r * nx] = fx;
+                    o0[(int64_t)r * nx + N] = fy;
+                    if (dot_partial) dot = __fmaf_rn(up.x, fx, __fmaf_rn(up.y, fy, dot));
+                }
+                if (dot_partial) dot_blk_total += (double)dot;
+            }
+        };
         const bool interior = (x0 >= M) && (x0 + kTXt <= nx - M) && (y0 >= M) && (y0 + kTYt <= ny - M);
-        if (interior && !project_out && !dot_partial) {
-            const float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
-            float *o0 = ob + (int64_t)(y0 + ty * kRt) * nx + gx;
-#pragma unroll
-            for (int r = 0; r < kRt; ++r) {
-                const float2 up = upk(w0[r + M]);
-                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
-                const float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
-                const float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
-                o0[(int64_t)r * nx] = fx * scale;
-                o0[(int64_t)r * nx + N] = fy * scale;
-            }
-            __syncthreads();   // all reads of this buffer done before it is refilled
-            continue;
-        }
-#pragma unroll
-        for (int r = 0; r < kRt; ++r) {
-            const int gy = y0 + ty * kRt + r;
-            if (gx < nx && gy < ny) {
-                const int64_t p = (int64_t)gy * nx + gx;
-                const float2 up = upk(w0[r + M]);
-                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
-                const float ax = x1.x + x2.y, ay = x1.y + x2.x;
-                float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
-                const int c0 = min(gx, M), c1 = min(nx - 1 - gx, M), d0 = min(gy, M), d1 = min(ny - 1 - gy, M);
-                if (c0 != M || c1 != M || d0 != M || d1 != M) {
-                    const int cls = ((c0 * (M + 1) + c1) * (M + 1) + d0) * (M + 1) + d1;
-                    kxx = __ldg(kd + 3 * cls);
-                    kxy = __ldg(kd + 3 * cls + 1);
-                    kyy = __ldg(kd + 3 * cls + 2);
-                }
-                float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
-                float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
-                if (project_out) {
-                    const uint8_t m = __ldg(cons + p);
-                    if (m & 1) fx = 0.f;
-                    if (m & 2) fy = 0.f;
-                }
-                fx *= scale;
-                fy *= scale;
-                ob[p] = fx;
-                ob[N + p] = fy;
-                dot = __fmaf_rn(up.x, fx, __fmaf_rn(up.y, fy, dot));
-            }
-        }
-        dot_blk_total += (double)dot;
+        if (interior && !project_out && !dot_partial)
+            tile_body(std::false_type{});
+        else
+            tile_body(std::true_type{});
         __syncthreads();   // all reads of buf[cur] done before it is refilled
     }
     if (s_abort) {
-        // let a copy still in flight land (bounded) before the CTA exits
-        if (threadIdx.x == 0 && t_abort + (int)gridDim.x < ntiles) mbar_wait(&bars[(it & 1) ^ 1], ((it + 1) >> 1) & 1);
+        // let the copies still in flight land (bounded waits) before the CTA exits
+        if (threadIdx.x == 0)
+            for (int k = it; k < n_issued; ++k) mbar_wait(&bars[k % kStages], (k / kStages) & 1);
         return;
     }
     if (dot_partial) {
@@ -356,7 +413,7 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(PD_ERR_CUDA, "tensor map encode failed");
-    const size_t smem = 2ull * 2 * BX * BY * sizeof(float);
+    const size_t smem = (size_t)kStages * 2 * BX * BY * sizeof(float);
     auto kern = k_tbt2d_tma<M>;
     static int attr_done[64] = {0};
     int dev = 0;
