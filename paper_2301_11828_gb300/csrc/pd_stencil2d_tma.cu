@@ -234,30 +234,46 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
                 }
                 static_for<-My, My + 1>([&](auto OY) {
                     constexpr int oy = decltype(OY)::value;
-                    constexpr int pi = pair_index2(M, ox, oy);
-                    const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
-                    const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
+                    if constexpr (oy != 0) {
+                        constexpr int pi = pair_index2(M, ox, oy);
+                        const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
+                        const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
 #pragma unroll
-                    for (int r = 0; r < kRt; ++r) {
-                        const u64 s = fadd2(wp[r + M + oy], wm[r + M - oy]);
-                        a1[r] = ffma2(c1, s, a1[r]);
-                        a2[r] = ffma2(c2, s, a2[r]);
+                        for (int r = 0; r < kRt; ++r) {
+                            const u64 s = fadd2(wp[r + M + oy], wm[r + M - oy]);
+                            a1[r] = ffma2(c1, s, a1[r]);
+                            a2[r] = ffma2(c2, s, a2[r]);
+                        }
                     }
                 });
+                // Axis pair (ox, 0): c(o) = diag(c_xx, 0) exactly, so only the x
+                // component is summed (scalar: one add and one FMA per output).
+                {
+                    constexpr int pi = pair_index2(M, ox, 0);
+                    const float cxx = tab.v[4 * pi];
+#pragma unroll
+                    for (int r = 0; r < kRt; ++r) {
+                        const float2 p2 = upk(wp[r + M]), m2 = upk(wm[r + M]);
+                        float2 acc = upk(a1[r]);
+                        acc.x = __fmaf_rn(cxx, p2.x + m2.x, acc.x);
+                        a1[r] = pk(acc.x, acc.y);
+                    }
+                }
             });
             u64 w0[WL];
 #pragma unroll
             for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
+            // Axis pairs (0, oy): c(o) = diag(0, c_yy) exactly; only the y component.
             static_for<1, M + 1>([&](auto OY) {
                 constexpr int oy = decltype(OY)::value;
                 constexpr int pi = pair_index2(M, 0, oy);
-                const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
-                const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
+                const float cyy = tab.v[4 * pi + 1];
 #pragma unroll
                 for (int r = 0; r < kRt; ++r) {
-                    const u64 s = fadd2(w0[r + M + oy], w0[r + M - oy]);
-                    a1[r] = ffma2(c1, s, a1[r]);
-                    a2[r] = ffma2(c2, s, a2[r]);
+                    const float2 p2 = upk(w0[r + M + oy]), m2 = upk(w0[r + M - oy]);
+                    float2 acc = upk(a1[r]);
+                    acc.y = __fmaf_rn(cyy, p2.y + m2.y, acc.y);
+                    a1[r] = pk(acc.x, acc.y);
                 }
             });
 
@@ -292,7 +308,9 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
                     interior_epilogue();   // this warp's outputs are all interior
                     return;
                 }
-                const float kxx0 = tab.v[4 * NP], kxy0 = tab.v[4 * NP + 1], kyy0 = tab.v[4 * NP + 2];
+                // Edge class of output (gx, gy): clipped face distances, lane part xc
+                // once per tile, row part per output row (warp-uniform).
+                const int xc = min(gx, M) * (M + 1) + min(nx - 1 - gx, M);
                 float *o0 = ob + (int64_t)gy0 * nx + gx;
                 const uint8_t *m0 = cons + (int64_t)gy0 * nx + gx;
                 float dot = 0.f;
@@ -303,19 +321,16 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
                     const float2 up = upk(w0[r + M]);
                     const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
                     const float ax = x1.x + x2.y, ay = x1.y + x2.x;
-                    float kxx = kxx0, kxy = kxy0, kyy = kyy0;
-                    if (warp_xe || gy < M || gy >= ny - M) {   // warp-uniform
-                        const int c0 = min(gx, M), c1 = min(nx - 1 - gx, M), d0 = min(gy, M), d1 = min(ny - 1 - gy, M);
-                        const int cls = ((c0 * (M + 1) + c1) * (M + 1) + d0) * (M + 1) + d1;
-                        if constexpr (M <= 3) {
-                            kxx = s_kd[3 * cls];
-                            kxy = s_kd[3 * cls + 1];
-                            kyy = s_kd[3 * cls + 2];
-                        } else {
-                            kxx = __ldg(kd + 3 * cls);
-                            kxy = __ldg(kd + 3 * cls + 1);
-                            kyy = __ldg(kd + 3 * cls + 2);
-                        }
+                    const int cls = xc * ((M + 1) * (M + 1)) + min(gy, M) * (M + 1) + min(ny - 1 - gy, M);
+                    float kxx, kxy, kyy;
+                    if constexpr (M <= 3) {
+                        kxx = s_kd[3 * cls];
+                        kxy = s_kd[3 * cls + 1];
+                        kyy = s_kd[3 * cls + 2];
+                    } else {
+                        kxx = __ldg(kd + 3 * cls);
+                        kxy = __ldg(kd + 3 * cls + 1);
+                        kyy = __ldg(kd + 3 * cls + 2);
                     }
                     float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
                     float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
