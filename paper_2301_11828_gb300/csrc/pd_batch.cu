@@ -120,9 +120,13 @@ __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const 
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const T sx = px[r + M + oy] + mx[r + M - oy];
-                const T sy = py[r + M + oy] + my[r + M - oy];
-                ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
-                ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
+                if constexpr (oy == 0) {
+                    ax[r] = dfma(cxx, sx, ax[r]);   // axis pair: c_xy = c_yy = 0 exactly
+                } else {
+                    const T sy = py[r + M + oy] + my[r + M - oy];
+                    ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
+                    ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
+                }
             }
         });
     });
@@ -135,14 +139,9 @@ __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const 
     static_for<1, M + 1>([&](auto OY) {
         constexpr int oy = decltype(OY)::value;
         constexpr int pi = pair_index2(M, 0, oy);
-        const T cxx = coef[3 * pi], cxy = coef[3 * pi + 1], cyy = coef[3 * pi + 2];
+        const T cyy = coef[3 * pi + 2];   // axis pair: c_xx = c_xy = 0 exactly
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T sx = cx[r + M + oy] + cx[r + M - oy];
-            const T sy = cy[r + M + oy] + cy[r + M - oy];
-            ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
-            ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
-        }
+        for (int r = 0; r < R; ++r) ay[r] = dfma(cyy, cy[r + M + oy] + cy[r + M - oy], ay[r]);
     });
     const T *kd = (sizeof(T) == 4) ? (const T *)d.kd32 : (const T *)d.kd64;
     T dot = T(0);

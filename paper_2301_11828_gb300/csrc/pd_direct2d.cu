@@ -93,10 +93,17 @@ k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
                     const T eq = we[r + M + oy];
                     const bool on = ((mk[r][k >> 5] >> (k & 31)) & 1u) && (eq != T(0));
                     const T wgt = on ? T(0.5) * (ep[r] + eq) : T(0);
-                    const T dx = upx[r] - wx[r + M + oy];
-                    const T dy = upy[r] - wy[r + M + oy];
-                    ax[r] = dfma(wgt, dfma(cxx, dx, cxy * dy), ax[r]);
-                    ay[r] = dfma(wgt, dfma(cxy, dx, cyy * dy), ay[r]);
+                    // c_xy and c_yy vanish for (ox, 0), c_xx and c_xy for (0, oy)
+                    if constexpr (oy == 0) {
+                        ax[r] = dfma(wgt, cxx * (upx[r] - wx[r + M]), ax[r]);
+                    } else if constexpr (ox == 0) {
+                        ay[r] = dfma(wgt, cyy * (upy[r] - wy[r + M + oy]), ay[r]);
+                    } else {
+                        const T dx = upx[r] - wx[r + M + oy];
+                        const T dy = upy[r] - wy[r + M + oy];
+                        ax[r] = dfma(wgt, dfma(cxx, dx, cxy * dy), ax[r]);
+                        ay[r] = dfma(wgt, dfma(cxy, dx, cyy * dy), ay[r]);
+                    }
                 }
             }
         });

@@ -12,7 +12,9 @@
 // of R consecutive y outputs.  The (64 + 2M) x (4R + 2M) halo box of both
 // components is staged in shared memory once.  For each x offset ox a thread
 // loads the y-windows (R + 2M values) of columns x + ox and x - ox into
-// registers and applies every (ox, oy) pair to its R outputs.
+// registers and applies every (ox, oy) pair to its R outputs.  Block entries
+// that vanish by geometry (c_xy and c_yy of (ox, 0), c_xx and c_xy of (0, oy))
+// are skipped at compile time.
 #include "pd_stencil.cuh"
 
 namespace pd {
@@ -79,9 +81,13 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const T sx = px[r + M + oy] + mx[r + M - oy];
-                const T sy = py[r + M + oy] + my[r + M - oy];
-                ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
-                ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
+                if constexpr (oy == 0) {
+                    ax[r] = dfma(cxx, sx, ax[r]);   // axis pair: c_xy = c_yy = 0 exactly
+                } else {
+                    const T sy = py[r + M + oy] + my[r + M - oy];
+                    ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
+                    ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
+                }
             }
         });
     });
@@ -94,14 +100,9 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
     static_for<1, M + 1>([&](auto OY) {
         constexpr int oy = decltype(OY)::value;
         constexpr int pi = pair_index2(M, 0, oy);
-        const T cxx = tab.v[3 * pi], cxy = tab.v[3 * pi + 1], cyy = tab.v[3 * pi + 2];
+        const T cyy = tab.v[3 * pi + 2];   // axis pair: c_xx = c_xy = 0 exactly
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T sx = cx[r + M + oy] + cx[r + M - oy];
-            const T sy = cy[r + M + oy] + cy[r + M - oy];
-            ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
-            ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
-        }
+        for (int r = 0; r < R; ++r) ay[r] = dfma(cyy, cy[r + M + oy] + cy[r + M - oy], ay[r]);
     });
 
     T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads

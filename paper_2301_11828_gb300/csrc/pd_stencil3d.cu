@@ -10,6 +10,36 @@
 
 namespace pd {
 
+// acc[.][r] += c(o) s for one offset pair, s = u~_{p+o} + u~_{p-o}.  Entry c_ab
+// carries the factor o_a o_b, so it vanishes exactly when o_a or o_b is zero;
+// the flags (compile-time constants once the loops are unrolled) skip those
+// entries and the sums they would need.  Kept terms run in the order
+// c_xz, c_xy, c_xx / c_yz, c_yy, c_xy / c_zz, c_yz, c_xz.
+template <typename T, int R>
+__device__ __forceinline__ void pair3(T (&acc)[3][R], int r, bool nx_, bool ny_, bool nz_, T cxx, T cxy, T cxz,
+                                      T cyy, T cyz, T czz, T s0, T s1, T s2)
+{
+    if (nx_) {
+        T a = acc[0][r];
+        if (nz_) a = dfma(cxz, s2, a);
+        if (ny_) a = dfma(cxy, s1, a);
+        acc[0][r] = dfma(cxx, s0, a);
+    }
+    if (ny_) {
+        T a = acc[1][r];
+        if (nz_) a = dfma(cyz, s2, a);
+        a = dfma(cyy, s1, a);
+        if (nx_) a = dfma(cxy, s0, a);
+        acc[1][r] = a;
+    }
+    if (nz_) {
+        T a = dfma(czz, s2, acc[2][r]);
+        if (ny_) a = dfma(cyz, s1, a);
+        if (nx_) a = dfma(cxz, s0, a);
+        acc[2][r] = a;
+    }
+}
+
 template <typename T, int M>
 __global__ void __launch_bounds__(kThreads)
 k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
@@ -82,14 +112,10 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
                     const T *cf = tab.v + 6 * pi;
                     const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const T s0 = wp[0][r + M + oz] + wm[0][r + M - oz];
-                        const T s1 = wp[1][r + M + oz] + wm[1][r + M - oz];
-                        const T s2 = wp[2][r + M + oz] + wm[2][r + M - oz];
-                        acc[0][r] = dfma(cxx, s0, dfma(cxy, s1, dfma(cxz, s2, acc[0][r])));
-                        acc[1][r] = dfma(cxy, s0, dfma(cyy, s1, dfma(cyz, s2, acc[1][r])));
-                        acc[2][r] = dfma(cxz, s0, dfma(cyz, s1, dfma(czz, s2, acc[2][r])));
-                    }
+                    for (int r = 0; r < R; ++r)
+                        pair3(acc, r, ox != 0, oy != 0, oz != 0, cxx, cxy, cxz, cyy, cyz, czz,
+                              wp[0][r + M + oz] + wm[0][r + M - oz], wp[1][r + M + oz] + wm[1][r + M - oz],
+                              wp[2][r + M + oz] + wm[2][r + M - oz]);
                 }
             }
         });
@@ -106,14 +132,9 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
         const T *cf = tab.v + 6 * pi;
         const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const T s0 = w0[0][r + M + oz] + w0[0][r + M - oz];
-            const T s1 = w0[1][r + M + oz] + w0[1][r + M - oz];
-            const T s2 = w0[2][r + M + oz] + w0[2][r + M - oz];
-            acc[0][r] = dfma(cxx, s0, dfma(cxy, s1, dfma(cxz, s2, acc[0][r])));
-            acc[1][r] = dfma(cxy, s0, dfma(cyy, s1, dfma(cyz, s2, acc[1][r])));
-            acc[2][r] = dfma(cxz, s0, dfma(cyz, s1, dfma(czz, s2, acc[2][r])));
-        }
+        for (int r = 0; r < R; ++r)
+            pair3(acc, r, false, false, true, cxx, cxy, cxz, cyy, cyz, czz, T(0), T(0),
+                  w0[2][r + M + oz] + w0[2][r + M - oz]);
     }
 
     T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
