@@ -64,6 +64,8 @@ typedef enum {
 /* ---- modes for pd_cg_solve ---- */
 #define PD_CG_F64   0x1u  /* plain CG, FP64 vectors and FP64 matvec */
 #define PD_CG_MIXED 0x2u  /* FP32-matvec CG, FP64 solution, FP64 residual replacement every 10x drop */
+#define PD_CG_GRAPH 0x10u /* option for PD_CG_MIXED: run the FP32 inner loop as CUDA-graph-replayed
+                             launches even where the persistent kernel applies */
 
 typedef struct {
     int dim;          /* 2 or 3 */
@@ -83,6 +85,7 @@ typedef struct {
     int f64_matvecs;       /* FP64 operator applications */
     double rel_residual;   /* ||P(b - K u)|| / ||P b||, FP64, recomputed at the end */
     double seconds;        /* wall time of the solve, device-synchronised */
+    int persistent;        /* 1 if the FP32 inner loop ran as the persistent kernel */
 } pd_cg_stats;
 
 typedef struct {
@@ -124,9 +127,15 @@ int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_
 /* Solves P K P u = P b (Eq. mat:e2 with h = 0 on Omega_c) by conjugate
  * gradients.  b, u: DEVICE double [dim][N]; u is the initial guess on entry
  * and the solution on exit (its constrained components are set to 0).
- * mode: PD_CG_F64 or PD_CG_MIXED.  Stops when ||P(b - K u)|| <= rtol ||P b||
- * in FP64.  stats may be NULL.  Returns PD_ERR_NOT_CONVERGED after max_iter
- * inner iterations with u holding the last iterate and stats filled. */
+ * mode: PD_CG_F64 or PD_CG_MIXED, optionally | PD_CG_GRAPH.  Stops when
+ * ||P(b - K u)|| <= rtol ||P b|| in FP64.  stats may be NULL.  Returns
+ * PD_ERR_NOT_CONVERGED after max_iter inner iterations with u holding the last
+ * iterate and stats filled.  On a 2D grid with a constant modulus, no broken
+ * bonds and a row length that is a multiple of 4, the FP32 inner loop of
+ * PD_CG_MIXED runs as one persistent cooperative kernel (all CTAs resident,
+ * grid barriers with bounded waits; PD_ERR_TIMEOUT if a wait gives up);
+ * elsewhere, or with PD_CG_GRAPH, as chunks of 32 iterations replayed from a
+ * CUDA graph.  Both give the same iterates up to FP32 rounding order. */
 int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter,
                 uint32_t mode, pd_cg_stats *stats, void *stream);
 

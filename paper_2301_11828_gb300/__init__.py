@@ -31,6 +31,7 @@ PD_IGNORE_BROKEN = 0x200
 PD_NO_TMA = 0x400
 PD_CG_F64 = 0x1
 PD_CG_MIXED = 0x2
+PD_CG_GRAPH = 0x10
 
 _STATUS = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM", 4: "PD_ERR_NOT_CONVERGED",
            5: "PD_ERR_TIMEOUT", 6: "PD_ERR_STATE"}
@@ -51,7 +52,7 @@ class pd_grid_info(ctypes.Structure):
 
 class pd_cg_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("f64_matvecs", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("persistent", ctypes.c_int)]
 
 
 class pd_step_stats(ctypes.Structure):

@@ -25,6 +25,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "pd_cg.cuh"
 #include "pd_internal.cuh"
 #include "pd_reduce.cuh"
 
@@ -36,17 +37,6 @@ constexpr int kBlk = 256;
 constexpr int kRedMax = 152 * 8;      // upper bound of the streaming kernels' grid (grid-stride)
 constexpr int kChunk = 32;            // inner iterations per graph launch
 
-struct CgScal {
-    double rr;       // r.r of the current iterate
-    double pq;       // p.q, written by the fused matvec dot
-    double rr_new;   // r.r after the update (last block)
-    double tol2;     // inner loop stops when rr <= tol2
-    double beta;
-    double aux;      // scratch for the host-driven reductions
-    int done;
-    int iters;
-    unsigned int retire[4];
-};
 
 // 16 bytes of T: the streaming kernels move whole packs with one vector load
 // or store.  A kernel gets the number of packs `nv` it may treat that way (0
@@ -236,6 +226,8 @@ k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64
         sc->tol2 = tau2 * sc->rr;
         sc->done = (sc->rr > sc->tol2) ? 0 : 1;
         sc->iters = 0;
+        sc->beta = 0.0;   // persistent loop: p = r + 0 * p_old on its first iteration
+        sc->pbuf = 0;
     }
 }
 
@@ -277,11 +269,12 @@ k_correct_zero(double *u, float *x32, double s, int64_t L, int64_t nv)
 // r32 = r64 * inv: the true residual replaces the recursive one.  The inner loop
 // stopped in the update of iteration k, so p still holds p_{k-1} and sc->beta
 // holds beta_k; the new direction is p_k = r_true + beta_k p_{k-1}, i.e. the
-// direction CG would have formed had its recursive residual been exact.
+// direction CG would have formed had its recursive residual been exact.  The
+// persistent loop forms p itself from r and p_old (form_p = 0).
 // sc->rr = r32.r32, sc->tol2 = tol2 (absolute), the inner loop is re-armed.
 __global__ void __launch_bounds__(kBlk)
 k_replace(float *r32, float *p32, const double *__restrict__ r64, int64_t L, int64_t nv, double inv, double tol2,
-          CgScal *sc, double *partial)
+          CgScal *sc, double *partial, int form_p)
 {
     __shared__ double red[kBlk / 32];
     const float beta = (float)sc->beta;
@@ -299,12 +292,12 @@ k_replace(float *r32, float *p32, const double *__restrict__ r64, int64_t L, int
             pv.v[e] = v.v[e] + beta * pv.v[e];
             acc += v.v[e] * v.v[e];
         }
-        stp(p32, j, pv);
+        if (form_p) stp(p32, j, pv);
         stp(r32, j, v);
     }
     for (int64_t i = nv * 4 + t0; i < L; i += st) {
         const float v = (float)(r64[i] * inv);
-        p32[i] = v + beta * p32[i];
+        if (form_p) p32[i] = v + beta * p32[i];
         r32[i] = v;
         acc += v * v;
     }
@@ -331,6 +324,10 @@ struct CgWs {
     void *base = nullptr;
     double *r64, *q64, *p64;    // FP64 residual, operator output, direction
     float *r32, *p32, *q32, *x32;
+    float *p32b;                // persistent loop: second direction buffer
+    uint8_t *tile_flags;        // persistent loop: tiles holding a constrained node
+    CgBar *gbar;                // persistent loop: grid barrier
+    int64_t flags_stamp = -1;   // op_stamp the tile flags were computed for
     CgScal *sc;
     double *partial;            // >= max(red, stencil CTAs) doubles
     double *partial2;
@@ -348,7 +345,9 @@ int ensure_ws(pd_grid *g, CgWs *&w)
     const int nblk = std::max(stencil_blocks(g, true, g->has_E || g->broken_total > 0),
                               stencil_blocks(g, false, g->has_E || g->broken_total > 0));
     const size_t nparts = (size_t)std::max(nblk, kRedMax) + 64;
-    const size_t need = sizeof(double) * 3 * L + sizeof(float) * 4 * L + sizeof(CgScal) + 2 * sizeof(double) * nparts + 1024;
+    const size_t ntile = (size_t)((g->n[0] + 63) / 64) * (size_t)((g->n[1] + 31) / 32) * (size_t)g->n[2];
+    const size_t need = sizeof(double) * 3 * L + sizeof(float) * 5 * L + sizeof(CgScal) + 2 * sizeof(double) * nparts +
+                        ntile + sizeof(CgBar) + 2304;
     w = (CgWs *)g->cg;
     if (w && w->bytes >= need) return PD_OK;
     if (!w) {
@@ -382,10 +381,15 @@ int ensure_ws(pd_grid *g, CgWs *&w)
     w->p32 = (float *)take(sizeof(float) * L);
     w->q32 = (float *)take(sizeof(float) * L);
     w->x32 = (float *)take(sizeof(float) * L);
+    w->p32b = (float *)take(sizeof(float) * L);
+    w->tile_flags = (uint8_t *)take(ntile);
+    w->gbar = (CgBar *)take(sizeof(CgBar));
+    w->flags_stamp = -1;
     w->sc = (CgScal *)take(sizeof(CgScal));
     w->partial = (double *)take(sizeof(double) * nparts);
     w->partial2 = (double *)take(sizeof(double) * nparts);
     PD_CUDA(cudaMemset(w->sc, 0, sizeof(CgScal)));
+    PD_CUDA(cudaMemset(w->gbar, 0, sizeof(CgBar)));
     return PD_OK;
 }
 
@@ -477,6 +481,42 @@ int inner_loop(pd_grid *g, CgWs *w, bool f64, double *x64, int budget, cudaStrea
     return hs->done ? PD_OK : PD_ERR_NOT_CONVERGED;
 }
 
+// The FP32 inner loop as persistent cooperative launches (pd_cg_persist.cu):
+// one launch runs until convergence or kPersistChunk iterations.
+int inner_loop_persist(pd_grid *g, CgWs *w, int budget, cudaStream_t s, int *done_iters)
+{
+    constexpr int kPersistChunk = 8192;
+    if (cg_persist_ctas(g) > 1024 || (size_t)2 * cg_persist_ctas(g) > (size_t)kRedMax + 64)
+        return fail(PD_ERR_STATE, "persistent CG: too many CTAs for the partial buffer");
+    if (w->flags_stamp != g->op_stamp) {
+        int rc = cg_persist_tile_flags(g, w->tile_flags, s);
+        if (rc) return rc;
+        w->flags_stamp = g->op_stamp;
+    }
+    CgVecs v;
+    v.x = w->x32;
+    v.r = w->r32;
+    v.q = w->q32;
+    v.p[0] = w->p32;
+    v.p[1] = w->p32b;
+    volatile CgScal *hs = (volatile CgScal *)g->h_pinned;
+    volatile int *herr = (volatile int *)((char *)g->h_pinned + 2048);
+    int issued = 0;
+    while (issued < budget) {
+        const int n = std::min(kPersistChunk, budget - issued);
+        int rc = cg_persist_run(g, v, w->sc, w->gbar, w->partial, w->tile_flags, n, s);
+        if (rc) return rc;
+        issued += n;
+        PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, s));
+        PD_CUDA(cudaMemcpyAsync((void *)herr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PD_CUDA(cudaStreamSynchronize(s));
+        if (*herr) return fail(PD_ERR_TIMEOUT, "persistent CG: a device wait gave up (error word set)");
+        if (hs->done) break;
+    }
+    *done_iters = hs->iters;
+    return hs->done ? PD_OK : PD_ERR_NOT_CONVERGED;
+}
+
 // r64 = P(b - K u) with the FP64 operator; returns |r|^2 on the host.
 int true_residual(pd_grid *g, CgWs *w, const double *b, const double *u, cudaStream_t s, double *rr)
 {
@@ -517,6 +557,8 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
     if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
     if (!b || !u) return fail(PD_ERR_INVALID, "b and u must be device pointers");
     if (!(rtol > 0) || max_iter < 1) return fail(PD_ERR_INVALID, "rtol > 0 and max_iter >= 1 required");
+    const bool graph_only = (mode & PD_CG_GRAPH) != 0;
+    mode &= ~(uint32_t)PD_CG_GRAPH;
     if (mode != PD_CG_F64 && mode != PD_CG_MIXED) return fail(PD_ERR_INVALID, "mode must be PD_CG_F64 or PD_CG_MIXED");
     cudaStream_t s = (cudaStream_t)stream;
     const auto t0 = std::chrono::steady_clock::now();
@@ -539,6 +581,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
     }
     const double bnorm = std::sqrt(bb) > 0 ? std::sqrt(bb) : 1.0;
     int total_iters = 0, outer = 0, f64mv = 0;
+    bool used_persist = false;
     double rel = 0.0;
     int status = PD_ERR_NOT_CONVERGED;
 
@@ -569,6 +612,8 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
         // history is not lost as it is by a restart.  FP32 vectors are scaled by
         // the initial residual norm s0 so they stay O(1).
         constexpr double kRU = 0.1;
+        const bool persist = !graph_only && cg_persist_eligible(g);
+        used_persist = persist;
         double rr;
         rc = true_residual(g, w, b, u, s, &rr);
         if (rc) return rc;
@@ -582,10 +627,12 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
             double rr_ref = rr / (s0 * s0);
             k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->r64, L, L / 4, 1.0 / s0,
                                                   std::max(kRU * kRU, tgt2 / rr_ref), w->sc, w->partial2);
+
             for (int phase = 0; phase < 1000; ++phase) {
                 ++outer;
                 int it = 0;
-                rc = inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it);
+                rc = persist ? inner_loop_persist(g, w, max_iter - total_iters, s, &it)
+                             : inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it);
                 total_iters += it;
                 if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
                 k_correct_zero<<<blocks, kBlk, 0, s>>>(u, w->x32, s0, L, aligned16(u) ? L / 4 : 0);
@@ -599,8 +646,9 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
                 rr_ref = rr / (s0 * s0);
                 k_replace<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->r64, L, L / 4, 1.0 / s0,
                                                   std::max(kRU * kRU * rr_ref, tgt2),
-                                                  w->sc, w->partial2);
+                                                  w->sc, w->partial2, persist ? 0 : 1);
                 PD_CUDA(cudaGetLastError());
+
             }
         }
     }
@@ -611,6 +659,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
         stats->f64_matvecs = f64mv;
         stats->rel_residual = rel;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->persistent = used_persist ? 1 : 0;
     }
     if (status != PD_OK) return fail(PD_ERR_NOT_CONVERGED, "CG reached its iteration cap");
     return PD_OK;

@@ -1,0 +1,218 @@
+// pd_tma2d.cuh -- shared pieces of the TMA-fed FP32 2D stencil kernels
+// (the batched matvec in pd_stencil2d_tma.cu and the persistent CG in
+// pd_cg_persist.cu): packed FP32x2 helpers, mbarrier / TMA wrappers, the tile
+// geometry, the packed coefficient table and the per-tile pair sums of the TBT
+// form (Sec. 3.2-3.4).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "pd_stencil.cuh"
+
+namespace pd {
+namespace tma2d {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk(float a, float b)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk(u64 r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b)
+{
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"((const void *)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr int kTXt = 64;                 // outputs per tile along x
+constexpr int kRt = 8;                   // outputs per thread along y
+constexpr int kTYt = kGY2 * kRt;         // outputs per tile along y (32)
+
+template <int M>
+__host__ __device__ constexpr int x_lead() { return M <= 4 ? 4 : 8; }   // 16-byte aligned halo on the left
+template <int M>
+__host__ __device__ constexpr int box_x() { return kTXt + 2 * x_lead<M>(); }
+template <int M>
+__host__ __device__ constexpr int box_y() { return kTYt + 2 * M; }
+
+// Pair coefficients packed for the FP32x2 form: (cxx, cyy) and (cxy, cxy) per pair,
+// then the interior Kd (xx, xy, yy, pad).
+template <int M>
+struct __align__(16) PackTab {
+    static constexpr int kPairs = count_offsets(2, M) / 2;
+    float v[4 * kPairs + 4];
+};
+
+// Pair sums of the TBT form for the kRt outputs of one thread.  colx / coly point
+// at the thread's column (first halo row) in the x / y planes of a staged box of
+// row length BX.  On return a1, a2 hold the packed accumulators of
+// sum_{o in half} c(o) (u~_{p+o} + u~_{p-o}) (f_x = a1.x + a2.y, f_y = a1.y + a2.x)
+// and w0 the thread's own column (w0[r + M] = u_p of output r).
+template <int M>
+__device__ __forceinline__ void tile_pairs(const float *colx, const float *coly, const PackTab<M> &tab,
+                                           u64 (&a1)[kRt], u64 (&a2)[kRt], u64 (&w0)[kRt + 2 * M])
+{
+    constexpr int BX = box_x<M>(), WL = kRt + 2 * M;
+#pragma unroll
+    for (int r = 0; r < kRt; ++r) { a1[r] = 0ull; a2[r] = 0ull; }
+    static_for<1, M + 1>([&](auto OX) {
+        constexpr int ox = decltype(OX)::value;
+        constexpr int My = isqrt_c(M * M - ox * ox);
+        u64 wp[WL], wm[WL];
+#pragma unroll
+        for (int i = 0; i < WL; ++i) {
+            wp[i] = pk(colx[i * BX + ox], coly[i * BX + ox]);
+            wm[i] = pk(colx[i * BX - ox], coly[i * BX - ox]);
+        }
+        static_for<-My, My + 1>([&](auto OY) {
+            constexpr int oy = decltype(OY)::value;
+            if constexpr (oy != 0) {
+                constexpr int pi = pair_index2(M, ox, oy);
+                const u64 c1 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi]);
+                const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
+#pragma unroll
+                for (int r = 0; r < kRt; ++r) {
+                    const u64 s = fadd2(wp[r + M + oy], wm[r + M - oy]);
+                    a1[r] = ffma2(c1, s, a1[r]);
+                    a2[r] = ffma2(c2, s, a2[r]);
+                }
+            }
+        });
+        // Axis pair (ox, 0): c(o) = diag(c_xx, 0) exactly, so only the x
+        // component is summed (scalar: one add and one FMA per output).
+        {
+            constexpr int pi = pair_index2(M, ox, 0);
+            const float cxx = tab.v[4 * pi];
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const float2 p2 = upk(wp[r + M]), m2 = upk(wm[r + M]);
+                float2 acc = upk(a1[r]);
+                acc.x = __fmaf_rn(cxx, p2.x + m2.x, acc.x);
+                a1[r] = pk(acc.x, acc.y);
+            }
+        }
+    });
+#pragma unroll
+    for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
+    // Axis pairs (0, oy): c(o) = diag(0, c_yy) exactly; only the y component.
+    static_for<1, M + 1>([&](auto OY) {
+        constexpr int oy = decltype(OY)::value;
+        constexpr int pi = pair_index2(M, 0, oy);
+        const float cyy = tab.v[4 * pi + 1];
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) {
+            const float2 p2 = upk(w0[r + M + oy]), m2 = upk(w0[r + M - oy]);
+            float2 acc = upk(a1[r]);
+            acc.y = __fmaf_rn(cyy, p2.y + m2.y, acc.y);
+            a1[r] = pk(acc.x, acc.y);
+        }
+    });
+}
+
+// ---- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (nullptr if absent).
+EncodeTiledFn encode_fn();
+
+// Tensor map over `batch` fields of two FP32 planes [2*batch][ny][nx] with the
+// halo box of horizon M; false if the driver rejects it.
+template <int M>
+inline bool make_map(CUtensorMap *map, const void *base, int nx, int ny, int64_t batch)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(2 * batch)};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x<M>(), (cuuint32_t)box_y<M>(), 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Pair coefficients in the order tile_pairs reads them, then the interior Kd.
+template <int M>
+PackTab<M> make_pack(const pd_grid *g)
+{
+    PackTab<M> t{};
+    double c[6], tot[3] = {0, 0, 0};
+    auto put = [&](int ox, int oy) {
+        const int pi = pair_index2(M, ox, oy);
+        coef_of(g, ox, oy, 0, false, c);
+        t.v[4 * pi + 0] = (float)c[0];
+        t.v[4 * pi + 1] = (float)c[2];
+        t.v[4 * pi + 2] = (float)c[1];
+        t.v[4 * pi + 3] = (float)c[1];
+        for (int i = 0; i < 3; ++i) tot[i] += 2 * c[i];
+    };
+    for (int ox = 1; ox <= M; ++ox) {
+        const int My = isqrt_c(M * M - ox * ox);
+        for (int oy = -My; oy <= My; ++oy) put(ox, oy);
+    }
+    for (int oy = 1; oy <= M; ++oy) put(0, oy);
+    constexpr int NP = PackTab<M>::kPairs;
+    for (int i = 0; i < 3; ++i) t.v[4 * NP + i] = (float)tot[i];
+    return t;
+}
+
+}  // namespace tma2d
+}  // namespace pd

@@ -103,3 +103,32 @@ def test_iteration_cap_reports_not_converged(pd):
     with pytest.raises(pd.PDError) as e:
         pd.pd_cg_solve(g.handle, b, torch.zeros_like(b), 1e-8, 5, pd.PD_CG_MIXED)
     assert e.value.code == pd.PD_ERR_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("shape,M", [((512, 512), 3), ((200, 136), 2), ((260, 72), 4), ((128, 96), 6)])
+def test_persistent_inner_loop_matches_graph_loop(pd, shape, M):
+    """The FP32 inner loop as one persistent cooperative kernel and as graph-replayed
+    launches: both reach the true FP64 residual and the same solution.  They differ
+    only in the grouping of the FP32/FP64 sums, which FP32 CG amplifies, so the
+    iteration counts are compared loosely."""
+    n = shape
+    w = syn.plate_static(n[0], M, tag=7, u_amp=0.0)
+    w.n = n
+    w.h = 1.0 / n[0]
+    w.constrained = syn.clamp_left(2, n, M)
+    w.b = syn.traction_right(2, n, M, 1e-3)
+    g = pd.Grid(2, n, w.h, M, constrained=w.constrained)
+    b = torch.tensor(w.b, device="cuda")
+    al = oracle.alpha(2, 1.0, w.delta)
+    res = {}
+    for mode in (pd.PD_CG_MIXED, pd.PD_CG_MIXED | pd.PD_CG_GRAPH):
+        u = torch.zeros_like(b)
+        st = pd.pd_cg_solve(g.handle, b, u, 1e-8, 200000, mode)
+        un = u.cpu().numpy()
+        assert st.rel_residual <= 1e-8
+        assert _true_rel(w, un, al) <= 1.05e-8
+        res[mode] = (un, st.iterations, st.persistent)
+    (u_p, it_p, used_p), (u_g, it_g, used_g) = res[pd.PD_CG_MIXED], res[pd.PD_CG_MIXED | pd.PD_CG_GRAPH]
+    assert used_p == 1 and used_g == 0
+    assert abs(it_p - it_g) <= 0.25 * it_g + 10
+    assert rel_l2(u_p, u_g) <= 1e-4
