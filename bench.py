@@ -14,6 +14,7 @@ the FP32/FP64 x stencil/FFT x delta = 3h/6h variants, the static CG solve
 the dynamic crack loop, and the CPU oracle timed on this host's cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
+  python bench.py --case fft2d|stencil2d_f64|stencil3d|fft3d|crack|cg [--steps K] [--warmup W]
 """
 from __future__ import annotations
 
@@ -450,6 +451,75 @@ def _extras(torch, pd, syn, dev):
     return out
 
 
+CASES = ("fft2d", "stencil2d_f64", "stencil3d", "fft3d", "crack", "cg")
+
+
+def run_case(args):
+    """One secondary workload in a loop (for ncu launch lists and captures); prints one JSON line.
+
+    fft2d: K u, 1024^2 plate, M=3, FP32 FFT tiles, 8 fields.  stencil2d_f64: the same with the FP64
+    stencil, 4 fields.  stencil3d / fft3d: K u on the 128^3 cube, M=3, FP32.  crack: one Verlet step
+    with bond breaking on the pre-notched 512^2 plate.  cg: 64 iterations of the mixed CG on the
+    1024^2 plate (graph-replayed inner loop)."""
+    import numpy as np
+    import torch
+    import paper_2301_11828_gb300 as pd
+    import synthetic as syn
+    pd.load_library()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    case = args.case
+    if case in ("fft2d", "stencil2d_f64"):
+        w = syn.large_plate(3)
+        g = pd.Grid(2, w.n, w.h, w.M)
+        dt, B, meth = (torch.float32, 8, pd.PD_METHOD_FFT) if case == "fft2d" else (torch.float64, 4, pd.PD_METHOD_STENCIL)
+        U = torch.rand((B, 2, NSIDE, NSIDE), dtype=dt, device=dev) * 2 - 1
+        O = torch.empty_like(U)
+        step, units = (lambda: g.matvec(U, O, flags=meth)), B * 2 * w.N
+    elif case in ("stencil3d", "fft3d"):
+        w = syn.cube(128, 3)
+        g = pd.Grid(3, w.n, w.h, w.M, constrained=w.constrained)
+        U = torch.tensor(w.u, dtype=torch.float32, device=dev)
+        O = torch.empty_like(U)
+        meth = pd.PD_METHOD_STENCIL if case == "stencil3d" else pd.PD_METHOD_FFT
+        step, units = (lambda: g.matvec(U, O, flags=meth | pd.PD_PROJECT)), 3 * w.N
+    elif case == "crack":
+        w = syn.crack_plate(512, 3)
+        lay = w.extra["vel_layers"]
+        cons = np.zeros((2,) + lay.shape, dtype=np.uint8)
+        cons[1] = lay != 0
+        vp = np.zeros((2,) + lay.shape)
+        vp[1] = lay * w.extra["v0"]
+        g = pd.Grid(2, w.n, w.h, w.M, constrained=cons, E_field=torch.tensor(w.extra["E_field"], device=dev), s0=w.s0)
+        g.break_segment(w.extra["notch"], w.extra["notch_den"])
+        vpt = torch.tensor(vp, device=dev)
+        u = torch.zeros((2,) + lay.shape, dtype=torch.float64, device=dev)
+        v = vpt.clone()
+        step, units = (lambda: g.step(u, v, None, nsteps=1, dt=2.99e-3, v_prescribed=vpt)), 2 * w.N
+    elif case == "cg":
+        w = syn.large_plate(3)
+        g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+        b = torch.tensor(w.b, device=dev)
+        u = torch.zeros_like(b)
+
+        def step():
+            u.zero_()
+            pd.pd_cg_solve(g.handle, b, u, 1e-30, 64, pd.PD_CG_MIXED, allow_not_converged=True)
+        units = 64
+    else:
+        raise SystemExit(f"unknown case {case}")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dt_s = (time.perf_counter() - t0) / args.steps
+    print(json.dumps({"case": case, "steps": args.steps, "ms_per_step": dt_s * 1e3,
+                      "units_per_step": units, "units_per_s": units / dt_s}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,7 +530,11 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--case", choices=CASES, default=None,
+                    help="run one secondary workload in a loop instead of the headline (profiling)")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -127,6 +127,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_ctot64);
     cudaFree(g->d_ctot32);
     cudaFree(g->d_off);
+    cudaFree(g->d_brk_thr);
     cudaFree(g->d_coef);
     cudaFree(g->d_coef1);
     cudaFree(g->ws);
@@ -278,6 +279,8 @@ int pd_create_grid(int dim, const int64_t n[3], double h, double delta, const ui
     if (cudaMemset(g->d_count, 0, sizeof(unsigned long long) * 8) != cudaSuccess)
         return bail(PD_ERR_CUDA, "counters");
     if (cudaMallocHost(&g->h_pinned, 4096) != cudaSuccess) return bail(PD_ERR_OOM, "pinned mailbox");
+    if (cudaMalloc(&g->d_brk_thr, sizeof(double) * (size_t)g->nnb) != cudaSuccess)
+        return bail(PD_ERR_OOM, "breaking thresholds");
     if (cudaMalloc(&g->d_err, sizeof(int)) != cudaSuccess) return bail(PD_ERR_OOM, "error word");
     if (cudaMemset(g->d_err, 0, sizeof(int)) != cudaSuccess) return bail(PD_ERR_CUDA, "error word");
     if (constrained) {

@@ -103,11 +103,46 @@ k_df_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int
 }
 
 // ------------------------------------------------------------------ breaking
+// Eq. fra:s1 is evaluated in a fixed operation order, each step rounded once:
+//     X_c = xi_c + (u_q,c - u_p,c),  l2 = sum_c X_c X_c,  r2 = sum_c xi_c xi_c,
+//     s = (sqrt(l2) - sqrt(r2)) / sqrt(r2),  broken iff s >= s0.
+// For a fixed offset, s is a monotone non-decreasing function of l2 (a rounded
+// square root, a rounded subtraction of a constant and a rounded division by a
+// positive constant all are), so the test is exactly l2 >= T for the smallest
+// double T that passes it.  k_break_thr finds T per offset by bisection over
+// the bit patterns of the non-negative doubles, with the same rounded
+// operations; k_break then needs no square root or division per bond.
+template <int DIM>
+__global__ void k_break_thr(int nnb, const int32_t *__restrict__ off, double h, double s0, double *thr)
+{
+    const int kk = nnb / 2 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= nnb) return;
+    const int ox = off[3 * kk], oy = off[3 * kk + 1], oz = off[3 * kk + 2];
+    const double xi0 = __dmul_rn(h, (double)ox), xi1 = __dmul_rn(h, (double)oy), xi2 = __dmul_rn(h, (double)oz);
+    double r2 = __dadd_rn(__dmul_rn(xi0, xi0), __dmul_rn(xi1, xi1));
+    if (DIM == 3) r2 = __dadd_rn(r2, __dmul_rn(xi2, xi2));
+    const double r = __dsqrt_rn(r2);
+    auto broken = [&](unsigned long long bits) {
+        return __ddiv_rn(__dsub_rn(__dsqrt_rn(__longlong_as_double((long long)bits)), r), r) >= s0;
+    };
+    unsigned long long lo = 0ull, hi = 0x7ff0000000000000ull;   // +0 (not broken for s0 > 0), +inf (broken)
+    if (broken(lo)) {
+        thr[kk] = 0.0;
+        return;
+    }
+    while (hi - lo > 1ull) {
+        const unsigned long long mid = lo + (hi - lo) / 2;
+        if (broken(mid)) hi = mid;
+        else lo = mid;
+    }
+    thr[kk] = __longlong_as_double((long long)hi);
+}
+
 template <int DIM, typename TU>
 __global__ void __launch_bounds__(kBlk)
 k_break(const TU *__restrict__ u, int64_t N, int nx, int ny, int nz, int nnb, const int32_t *__restrict__ off,
-        uint32_t *mask, double h, double s0, int32_t *break_step, int32_t step_id, uint32_t *brflag,
-        int32_t *brlist, unsigned long long *count)
+        uint32_t *mask, double h, const double *__restrict__ thr, int32_t *break_step, int32_t step_id,
+        uint32_t *brflag, int32_t *brlist, unsigned long long *count)
 {
     unsigned long long newly = 0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
@@ -124,21 +159,17 @@ k_break(const TU *__restrict__ u, int64_t N, int nx, int ny, int nz, int nnb, co
             const int qi = i + ox, qj = j + oy, qk = k + oz;
             if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
             const int64_t q = ((int64_t)qk * ny + qj) * nx + qi;
-            // Eq. fra:s1 in a fixed operation order, each step rounded once.
+            // Eq. fra:s1 in a fixed operation order, each step rounded once (see k_break_thr).
             const double xi0 = __dmul_rn(h, (double)ox), xi1 = __dmul_rn(h, (double)oy),
                          xi2 = __dmul_rn(h, (double)oz);
             const double X0 = __dadd_rn(xi0, __dsub_rn((double)u[q], up[0]));
             const double X1 = __dadd_rn(xi1, __dsub_rn((double)u[N + q], up[1]));
             double l2 = __dadd_rn(__dmul_rn(X0, X0), __dmul_rn(X1, X1));
-            double r2 = __dadd_rn(__dmul_rn(xi0, xi0), __dmul_rn(xi1, xi1));
             if (DIM == 3) {
                 const double X2 = __dadd_rn(xi2, __dsub_rn((double)u[2 * N + q], up[2]));
                 l2 = __dadd_rn(l2, __dmul_rn(X2, X2));
-                r2 = __dadd_rn(r2, __dmul_rn(xi2, xi2));
             }
-            const double l = __dsqrt_rn(l2), r = __dsqrt_rn(r2);
-            const double s = __ddiv_rn(__dsub_rn(l, r), r);
-            if (s >= s0) {
+            if (l2 >= thr[kk]) {
                 atomicAnd(wp, ~bit);
                 const int km = nnb - 1 - kk;
                 atomicAnd(mask + (int64_t)(km >> 5) * N + q, ~(1u << (km & 31)));
@@ -338,11 +369,20 @@ int launch_df_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t bat
 int launch_break(pd_grid *g, const void *u, bool f64, int32_t *break_step, int32_t step_id, cudaStream_t s)
 {
     if (!(g->s0 > 0.0)) return PD_OK;
+    if (g->brk_thr_s0 != g->s0) {   // thresholds for this s0 (stream-ordered, no allocation)
+        const int nh = g->nnb - g->nnb / 2;
+        if (g->dim == 2)
+            k_break_thr<2><<<(nh + 127) / 128, 128, 0, s>>>(g->nnb, g->d_off, g->h, g->s0, g->d_brk_thr);
+        else
+            k_break_thr<3><<<(nh + 127) / 128, 128, 0, s>>>(g->nnb, g->d_off, g->h, g->s0, g->d_brk_thr);
+        PD_CUDA(cudaGetLastError());
+        g->brk_thr_s0 = g->s0;
+    }
     const int blocks = grid_blocks(g->N);
     const int nx = (int)g->n[0], ny = (int)g->n[1], nz = (int)g->n[2];
 #define PD_BRK(D, TU)                                                                                          \
     k_break<D, TU><<<blocks, kBlk, 0, s>>>((const TU *)u, g->N, nx, ny, nz, g->nnb, g->d_off, g->d_mask, g->h, \
-                                            g->s0, break_step, step_id, g->d_brflag, g->d_brlist, g->d_count)
+                                            g->d_brk_thr, break_step, step_id, g->d_brflag, g->d_brlist, g->d_count)
     if (g->dim == 2) {
         if (f64) PD_BRK(2, double); else PD_BRK(2, float);
     } else {

@@ -213,6 +213,31 @@ def test_break_bonds_bit_exact(pd, dim, n, M, dtype):
     assert np.array_equal(g.offsets(), oracle.offsets(dim, M))
 
 
+@pytest.mark.parametrize("dim,n,M", [(2, (48, 40), 3), (2, (33, 29), 5), (3, (14, 12, 10), 3)])
+def test_break_near_threshold_bit_exact(pd, dim, n, M):
+    """Stretches within a few ulps of s0: the kernel's per-offset threshold on
+    |xi + eta|^2 must decide exactly as the oracle's square root and division do.
+    A uniform stretch by (1 + s0) puts every bond on the threshold; perturbations of
+    1e-16 .. 1e-13 (relative) scatter them to both sides."""
+    from helpers import mask_to_mu
+    h = 1.0 / 64
+    s0 = 1e-3
+    rng = np.random.default_rng(77)
+    for trial, rel in enumerate((1e-16, 1e-15, 1e-14, 1e-13)):
+        g = pd.Grid(dim, n, h, M, s0=s0)
+        mu = oracle.intact_mu(dim, n, M)
+        coords = np.meshgrid(*[(np.arange(k) + 0.5) * h for k in reversed(n)], indexing="ij")[::-1]
+        u_np = np.stack([s0 * c for c in coords]) * (1 + rel * rng.standard_normal((dim,) + tuple(reversed(n))))
+        u_t = torch.tensor(u_np, dtype=torch.float64, device="cuda")
+        nb = g.break_bonds(u_t)
+        nb_or = oracle.break_bonds(dim, n, h, M, s0, u_np, mu)
+        assert nb == nb_or
+        got = mask_to_mu(g.bond_mask().cpu().numpy(), g.nnb)
+        assert np.array_equal(got, mu)
+        n_pairs = mu.size // 2
+        assert 0 < nb_or < n_pairs, (rel, nb_or)   # both sides of the threshold occur
+
+
 @pytest.mark.parametrize("nside", [32, 512])
 def test_prenotch_bit_exact(pd, nside):
     from helpers import mask_to_mu
