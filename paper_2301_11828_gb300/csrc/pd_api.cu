@@ -279,7 +279,7 @@ int pd_create_grid(int dim, const int64_t n[3], double h, double delta, const ui
     if (cudaMemset(g->d_count, 0, sizeof(unsigned long long) * 8) != cudaSuccess)
         return bail(PD_ERR_CUDA, "counters");
     if (cudaMallocHost(&g->h_pinned, 4096) != cudaSuccess) return bail(PD_ERR_OOM, "pinned mailbox");
-    if (cudaMalloc(&g->d_brk_thr, sizeof(double) * (size_t)g->nnb) != cudaSuccess)
+    if (cudaMalloc(&g->d_brk_thr, sizeof(double) * 4 * (size_t)g->nnb) != cudaSuccess)
         return bail(PD_ERR_OOM, "breaking thresholds");
     if (cudaMalloc(&g->d_err, sizeof(int)) != cudaSuccess) return bail(PD_ERR_OOM, "error word");
     if (cudaMemset(g->d_err, 0, sizeof(int)) != cudaSuccess) return bail(PD_ERR_CUDA, "error word");

@@ -206,7 +206,7 @@ k_batch_matvec(const PlateDesc *__restrict__ desc, int np, int ntiles, const T *
             case 3: dot = tile_body<T, 3, R>(d, coef, in, out, x0, y0, s_x, s_y); break;
             default: dot = tile_body<T, 4, R>(d, coef, in, out, x0, y0, s_x, s_y); break;
         }
-        const double s = block_sum((double)dot, red);
+        const double s = block_sum(dot, red);
         if (threadIdx.x == 0 && partial) partial[t] = s;
         __syncthreads();
     }
@@ -254,7 +254,7 @@ k_batch_update(const PlateDesc *__restrict__ desc, const int *__restrict__ cplat
             r[i] = ri;
             acc += ri * ri;
         }
-        const double s = block_sum((double)acc, red);
+        const double s = block_sum(acc, red);
         if (threadIdx.x == 0) rr_cur[c] = s;
         __syncthreads();
     }
@@ -349,7 +349,7 @@ k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate
             x32[i] = 0.f;
             acc += v * v;
         }
-        const double s = block_sum((double)acc, red);
+        const double s = block_sum(acc, red);
         if (threadIdx.x == 0) rr[c] = s;
         __syncthreads();
     }

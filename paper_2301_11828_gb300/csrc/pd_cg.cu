@@ -125,7 +125,7 @@ k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_
         r[i] = ri;
         acc += ri * ri;
     }
-    const double bs = block_sum((double)acc, red);
+    const double bs = block_sum(acc, red);
     if (grid_last(bs, partial, &sc->rr_new, &sc->retire[0], red)) {
         const double rn = sc->rr_new;
         sc->beta = (sc->rr > 0.0) ? rn / sc->rr : 0.0;
@@ -153,6 +153,58 @@ k_cg_p(T *p, const T *__restrict__ r, int64_t L, int64_t nv, const CgScal *sc)
     for (int64_t i = nv * Pk<T>::n + t0; i < L; i += st) p[i] = r[i] + beta * p[i];
 }
 
+// Update of the graph-replayed fused loop: p_new sits in direction buffer
+// pbuf ^ 1 (written by the direction/operator kernel).  x += alpha p_new,
+// r -= alpha q, r.r; the last block forms beta, tests convergence and makes
+// p_new the next p_old.  Every block reads pbuf before the last block flips it.
+__global__ void __launch_bounds__(kBlk, 4)
+k_cg_update2(float *x, float *r, const float *p0, const float *p1, const float *__restrict__ q, int64_t L, int64_t nv,
+             CgScal *sc, double *partial)
+{
+    __shared__ double red[kBlk / 32];
+    __shared__ int s_done, s_pbuf;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_pbuf = sc->pbuf;
+        s_alpha = (sc->pq != 0.0) ? sc->rr / sc->pq : 0.0;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const float *__restrict__ p = s_pbuf ? p0 : p1;
+    const float a = (float)s_alpha;
+    float acc = 0.f;
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    for (int64_t j = t0; j < nv; j += st) {
+        Pk<float> xv = ldp(x, j), rv = ldp(r, j);
+        const Pk<float> pv = ldp(p, j), qv = ldp(q, j);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            xv.v[e] += a * pv.v[e];
+            rv.v[e] -= a * qv.v[e];
+            acc += rv.v[e] * rv.v[e];
+        }
+        stp(x, j, xv);
+        stp(r, j, rv);
+    }
+    for (int64_t i = nv * 4 + t0; i < L; i += st) {
+        const float xi = x[i] + a * p[i];
+        const float ri = r[i] - a * q[i];
+        x[i] = xi;
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    const double bs = block_sum(acc, red);
+    if (grid_last(bs, partial, &sc->rr_new, &sc->retire[0], red)) {
+        const double rn = sc->rr_new;
+        sc->beta = (sc->rr > 0.0) ? rn / sc->rr : 0.0;
+        sc->rr = rn;
+        sc->iters += 1;
+        sc->pbuf ^= 1;
+        if (!(rn > sc->tol2)) sc->done = 1;   // also stops on NaN
+    }
+}
+
 // out = a . b (accumulated per thread in the kernel's precision, FP64 across threads)
 template <typename T>
 __global__ void __launch_bounds__(kBlk)
@@ -168,7 +220,7 @@ k_dot(const T *__restrict__ a, const T *__restrict__ b, int64_t L, int64_t nv, d
         for (int e = 0; e < Pk<T>::n; ++e) acc += av.v[e] * bv.v[e];
     }
     for (int64_t i = nv * Pk<T>::n + t0; i < L; i += st) acc += a[i] * b[i];
-    const double bs = block_sum((double)acc, red);
+    const double bs = block_sum(acc, red);
     grid_last(bs, partial, out, retire, red);
 }
 
@@ -221,7 +273,7 @@ k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64
         x32[i] = 0.f;
         acc += v * v;
     }
-    const double bs = block_sum((double)acc, red);
+    const double bs = block_sum(acc, red);
     if (grid_last(bs, partial, &sc->rr, &sc->retire[1], red)) {
         sc->tol2 = tau2 * sc->rr;
         sc->done = (sc->rr > sc->tol2) ? 0 : 1;
@@ -301,7 +353,7 @@ k_replace(float *r32, float *p32, const double *__restrict__ r64, int64_t L, int
         r32[i] = v;
         acc += v * v;
     }
-    const double bs = block_sum((double)acc, red);
+    const double bs = block_sum(acc, red);
     if (grid_last(bs, partial, &sc->rr, &sc->retire[1], red)) {
         sc->tol2 = tol2;
         sc->done = (sc->rr > tol2) ? 0 : 1;
@@ -334,9 +386,9 @@ struct CgWs {
     int red = 0;                // grid of the streaming kernels: resident CTAs on all SMs, <= kRedMax
     int red64 = 0;              // the same for the FP64 update
     cudaStream_t cap = nullptr; // capture stream
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [0] FP32 inner, [1] FP64 plain
-    const void *graph_key[2] = {nullptr, nullptr};
-    int64_t graph_stamp[2] = {-1, -1};
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // [0] FP32 inner, [1] FP64 plain, [2] FP32 fused
+    const void *graph_key[3] = {nullptr, nullptr, nullptr};
+    int64_t graph_stamp[3] = {-1, -1, -1};
 };
 
 int ensure_ws(pd_grid *g, CgWs *&w)
@@ -363,7 +415,7 @@ int ensure_ws(pd_grid *g, CgWs *&w)
         w->red64 = std::max(1, std::min(kRedMax, sms * std::max(occ, 1)));
     }
     if (w->base) cudaFree(w->base);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
         if (w->graph[i]) {
             cudaGraphExecDestroy(w->graph[i]);
             w->graph[i] = nullptr;
@@ -393,10 +445,38 @@ int ensure_ws(pd_grid *g, CgWs *&w)
     return PD_OK;
 }
 
-// One inner iteration on FP32 (mixed) or FP64 (plain) vectors.
-int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s)
+CgVecs cg_vecs(CgWs *w)
+{
+    CgVecs v;
+    v.x = w->x32;
+    v.r = w->r32;
+    v.q = w->q32;
+    v.p[0] = w->p32;
+    v.p[1] = w->p32b;
+    return v;
+}
+
+int ensure_tile_flags(pd_grid *g, CgWs *w, cudaStream_t s)
+{
+    if (w->flags_stamp == g->op_stamp) return PD_OK;
+    int rc = cg_persist_tile_flags(g, w->tile_flags, s);
+    if (rc == PD_OK) w->flags_stamp = g->op_stamp;
+    return rc;
+}
+
+// One inner iteration on FP32 (mixed) or FP64 (plain) vectors.  With `fused`
+// (FP32 on a TMA-eligible 2D grid) it is two launches: direction + operator
+// (k_cg_dirmv) and the update; otherwise matvec, update and direction.
+int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s, bool fused = false)
 {
     const int64_t L = (int64_t)g->dim * g->N;
+    if (fused && !f64) {
+        int rc = cg_dirmv_run(g, cg_vecs(w), w->sc, w->partial, w->tile_flags, s);
+        if (rc) return rc;
+        k_cg_update2<<<w->red, kBlk, 0, s>>>(w->x32, w->r32, w->p32, w->p32b, w->q32, L, L / 4, w->sc, w->partial2);
+        PD_CUDA(cudaGetLastError());
+        return PD_OK;
+    }
     const bool fuse = !(g->broken_total > 0 && !g->has_E);
     const uint32_t fl = (f64 ? PD_F64 : PD_F32) | PD_PROJECT | kInputProjected;
     void *p = f64 ? (void *)w->p64 : (void *)w->p32;
@@ -430,12 +510,17 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s)
 
 // Runs inner iterations until the device flag is set or `budget` iterations
 // were issued.  Chunks of kChunk iterations run as one captured graph.
-int inner_loop(pd_grid *g, CgWs *w, bool f64, double *x64, int budget, cudaStream_t s, int *done_iters)
+int inner_loop(pd_grid *g, CgWs *w, bool f64, double *x64, int budget, cudaStream_t s, int *done_iters,
+               bool fused = false)
 {
-    const int gi = f64 ? 1 : 0;
+    const int gi = f64 ? 1 : (fused ? 2 : 0);
+    if (fused) {
+        int rc0 = ensure_tile_flags(g, w, s);
+        if (rc0) return rc0;
+    }
     // one plain iteration first: sets kernel attributes outside any capture
     int issued = 0;
-    int rc = iteration(g, w, f64, x64, s);
+    int rc = iteration(g, w, f64, x64, s, fused);
     if (rc) return rc;
     ++issued;
     const void *key = x64;
@@ -447,7 +532,7 @@ int inner_loop(pd_grid *g, CgWs *w, bool f64, double *x64, int budget, cudaStrea
         cudaGraph_t graph = nullptr;
         bool ok = cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            for (int i = 0; i < kChunk && ok; ++i) ok = (iteration(g, w, f64, x64, w->cap) == PD_OK);
+            for (int i = 0; i < kChunk && ok; ++i) ok = (iteration(g, w, f64, x64, w->cap, fused) == PD_OK);
             ok = (cudaStreamEndCapture(w->cap, &graph) == cudaSuccess) && ok;
         }
         if (ok && cudaGraphInstantiate(&w->graph[gi], graph, 0) != cudaSuccess) {
@@ -466,7 +551,7 @@ int inner_loop(pd_grid *g, CgWs *w, bool f64, double *x64, int budget, cudaStrea
             PD_CUDA(cudaGraphLaunch(w->graph[gi], s));
         } else {
             for (int i = 0; i < n; ++i) {
-                rc = iteration(g, w, f64, x64, s);
+                rc = iteration(g, w, f64, x64, s, fused);
                 if (rc) return rc;
             }
         }
@@ -476,7 +561,13 @@ int inner_loop(pd_grid *g, CgWs *w, bool f64, double *x64, int budget, cudaStrea
         if (hs->done) break;
     }
     PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, s));
+    volatile int *herr = (volatile int *)((char *)g->h_pinned + 2048);
+    PD_CUDA(cudaMemcpyAsync((void *)herr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
+    if (*herr) {   // a kernel gave up a bounded wait: its reductions may not have retired
+        PD_CUDA(cudaMemsetAsync(w->sc, 0, sizeof(CgScal), s));
+        return fail(PD_ERR_TIMEOUT, "CG: a device wait gave up (error word set)");
+    }
     *done_iters = hs->iters;
     return hs->done ? PD_OK : PD_ERR_NOT_CONVERGED;
 }
@@ -488,17 +579,9 @@ int inner_loop_persist(pd_grid *g, CgWs *w, int budget, cudaStream_t s, int *don
     constexpr int kPersistChunk = 8192;
     if (cg_persist_ctas(g) > 1024 || (size_t)2 * cg_persist_ctas(g) > (size_t)kRedMax + 64)
         return fail(PD_ERR_STATE, "persistent CG: too many CTAs for the partial buffer");
-    if (w->flags_stamp != g->op_stamp) {
-        int rc = cg_persist_tile_flags(g, w->tile_flags, s);
-        if (rc) return rc;
-        w->flags_stamp = g->op_stamp;
-    }
-    CgVecs v;
-    v.x = w->x32;
-    v.r = w->r32;
-    v.q = w->q32;
-    v.p[0] = w->p32;
-    v.p[1] = w->p32b;
+    int rc0 = ensure_tile_flags(g, w, s);
+    if (rc0) return rc0;
+    const CgVecs v = cg_vecs(w);
     volatile CgScal *hs = (volatile CgScal *)g->h_pinned;
     volatile int *herr = (volatile int *)((char *)g->h_pinned + 2048);
     int issued = 0;
@@ -510,7 +593,11 @@ int inner_loop_persist(pd_grid *g, CgWs *w, int budget, cudaStream_t s, int *don
         PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(CgScal), cudaMemcpyDeviceToHost, s));
         PD_CUDA(cudaMemcpyAsync((void *)herr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         PD_CUDA(cudaStreamSynchronize(s));
-        if (*herr) return fail(PD_ERR_TIMEOUT, "persistent CG: a device wait gave up (error word set)");
+        if (*herr) {
+            PD_CUDA(cudaMemsetAsync(w->sc, 0, sizeof(CgScal), s));
+            PD_CUDA(cudaMemsetAsync(w->gbar, 0, sizeof(CgBar), s));
+            return fail(PD_ERR_TIMEOUT, "persistent CG: a device wait gave up (error word set)");
+        }
         if (hs->done) break;
     }
     *done_iters = hs->iters;
@@ -539,7 +626,7 @@ void cg_release(pd_grid *g)
 {
     CgWs *w = (CgWs *)g->cg;
     if (!w) return;
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
         if (w->graph[i]) cudaGraphExecDestroy(w->graph[i]);
     if (w->base) cudaFree(w->base);
     if (w->cap) cudaStreamDestroy(w->cap);
@@ -613,6 +700,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
         // the initial residual norm s0 so they stay O(1).
         constexpr double kRU = 0.1;
         const bool persist = !graph_only && cg_persist_eligible(g);
+        const bool fused = !persist && cg_dirmv_eligible(g);
         used_persist = persist;
         double rr;
         rc = true_residual(g, w, b, u, s, &rr);
@@ -632,7 +720,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
                 ++outer;
                 int it = 0;
                 rc = persist ? inner_loop_persist(g, w, max_iter - total_iters, s, &it)
-                             : inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it);
+                             : inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it, fused);
                 total_iters += it;
                 if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
                 k_correct_zero<<<blocks, kBlk, 0, s>>>(u, w->x32, s0, L, aligned16(u) ? L / 4 : 0);
@@ -646,7 +734,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
                 rr_ref = rr / (s0 * s0);
                 k_replace<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->r64, L, L / 4, 1.0 / s0,
                                                   std::max(kRU * kRU * rr_ref, tgt2),
-                                                  w->sc, w->partial2, persist ? 0 : 1);
+                                                  w->sc, w->partial2, (persist || fused) ? 0 : 1);
                 PD_CUDA(cudaGetLastError());
 
             }

@@ -61,6 +61,12 @@ struct CgVecs {
 int cg_persist_run(pd_grid *g, const CgVecs &v, CgScal *sc, CgBar *gbar, double *part, const uint8_t *tile_flags,
                    int budget, cudaStream_t s);
 
+// The graph-replayed form of the same loop on 2D TMA-eligible grids (any size):
+// per iteration cg_dirmv_run (direction p = r + beta p_old formed from the TMA
+// boxes, q = P K P p, p.q into sc->pq) then the update kernel of pd_cg.cu.
+bool cg_dirmv_eligible(const pd_grid *g);
+int cg_dirmv_run(pd_grid *g, const CgVecs &v, CgScal *sc, double *partial, const uint8_t *tile_flags, cudaStream_t s);
+
 // tile_flags[t] = 1 when tile t (64 x 32 outputs, row-major over tiles) holds a
 // constrained node.
 int cg_persist_tile_flags(pd_grid *g, uint8_t *tile_flags, cudaStream_t s);

@@ -131,6 +131,116 @@ __device__ __forceinline__ bool grid_allreduce2(double v0, double v1, CgBar *B, 
     return *s_fail == 0;
 }
 
+// The direction and operator part of one CG iteration for the tiles t = first,
+// first + stride, ...: TMA brings the halo boxes of r and p_old into sr / sp,
+// p = r + beta p_old is formed in shared memory, its interior written to pn, and
+// q = P K P p (with the per-thread partial of p.q added to dot) written to q.
+// Shared by the persistent loop and the graph-replayed one.  False (in every
+// thread) when a TMA wait gave up; the error word is then set.
+template <int M>
+__device__ __forceinline__ bool cg_dir_tiles(const CUtensorMap *map_r, const CUtensorMap *mp, float *sr, float *sp,
+                                             float *pn, float *q, float b32, int nx, int ny, int64_t N, int tiles_x,
+                                             int ntiles, int first, int stride, const uint8_t *__restrict__ cons,
+                                             const uint8_t *__restrict__ tile_flags, const float *s_kd,
+                                             const float *__restrict__ kd, const PackTab<M> &tab, uint64_t *bar_,
+                                             uint32_t &phase, int *s_fail, int *err, double &dot_cta)
+{
+    constexpr int XL = x_lead<M>(), BX = box_x<M>(), WL = kRt + 2 * M;
+    constexpr int PLANE = BX * box_y<M>();
+    constexpr uint32_t kBytes = 2u * PLANE * sizeof(float);
+    constexpr int NP = PackTab<M>::kPairs;
+    const int tx = threadIdx.x % kTXt, ty = threadIdx.x / kTXt;
+    uint64_t &bar = *bar_;
+    const int G = stride;
+    for (int t = first; t < ntiles; t += G) {
+        const int x0 = (t % tiles_x) * kTXt, y0 = (t / tiles_x) * kTYt;
+        if (threadIdx.x == 0) {
+            // r and p_old were written through the generic proxy before this launch or the last grid barrier
+            asm volatile("fence.proxy.async;" ::: "memory");
+            mbar_expect_tx(&bar, 2 * kBytes);
+            tma_load_3d(sr, map_r, x0 - XL, y0 - M, 0, &bar);
+            tma_load_3d(sp, mp, x0 - XL, y0 - M, 0, &bar);
+        }
+        if (!mbar_wait(&bar, phase)) {
+            atomicCAS(err, 0, 1);
+            *s_fail = 1;
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (*s_fail) {
+            if (threadIdx.x == 0) mbar_wait(&bar, phase ^ 1u);   // let the copies land (bounded)
+            return false;
+        }
+        // p = r + beta p_old over the whole box (zero outside the grid stays zero)
+        for (int e = threadIdx.x; e < PLANE; e += kThreads) {
+            sp[e] = sr[e] + b32 * sp[e];
+            sp[PLANE + e] = sr[PLANE + e] + b32 * sp[PLANE + e];
+        }
+        __syncthreads();
+
+        u64 a1[kRt], a2[kRt], w0[WL];
+        tile_pairs<M>(sp + (ty * kRt) * BX + tx + XL, sp + PLANE + (ty * kRt) * BX + tx + XL, tab, a1, a2, w0);
+
+        const int gx = x0 + tx, gy0 = y0 + ty * kRt;
+        const int64_t o0 = (int64_t)gy0 * nx + gx;
+        float dot = 0.f;
+        const bool interior = (x0 >= M) && (x0 + kTXt <= nx - M) && (y0 >= M) && (y0 + kTYt <= ny - M);
+        if (interior && !tile_flags[t]) {
+            const float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const float2 up = upk(w0[r + M]);
+                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                const float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
+                const float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
+                const int64_t p = o0 + (int64_t)r * nx;
+                q[p] = fx;
+                q[N + p] = fy;
+                pn[p] = up.x;
+                pn[N + p] = up.y;
+                dot = __fmaf_rn(up.x, fx, __fmaf_rn(up.y, fy, dot));
+            }
+        } else {
+            const int xc = min(gx, M) * (M + 1) + min(nx - 1 - gx, M);
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const int gy = gy0 + r;
+                if (gx >= nx || gy >= ny) continue;
+                const float2 up = upk(w0[r + M]);
+                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                const float ax = x1.x + x2.y, ay = x1.y + x2.x;
+                const int cls = xc * ((M + 1) * (M + 1)) + min(gy, M) * (M + 1) + min(ny - 1 - gy, M);
+                float kxx, kxy, kyy;
+                if constexpr (M <= 3) {
+                    kxx = s_kd[3 * cls];
+                    kxy = s_kd[3 * cls + 1];
+                    kyy = s_kd[3 * cls + 2];
+                } else {
+                    kxx = __ldg(kd + 3 * cls);
+                    kxy = __ldg(kd + 3 * cls + 1);
+                    kyy = __ldg(kd + 3 * cls + 2);
+                }
+                float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
+                float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
+                const int64_t p = o0 + (int64_t)r * nx;
+                if (cons) {
+                    const uint8_t m = __ldg(cons + p);
+                    if (m & 1) fx = 0.f;
+                    if (m & 2) fy = 0.f;
+                }
+                q[p] = fx;
+                q[N + p] = fy;
+                pn[p] = up.x;
+                pn[N + p] = up.y;
+                dot = __fmaf_rn(up.x, fx, __fmaf_rn(up.y, fy, dot));
+            }
+        }
+        dot_cta += (double)dot;
+        __syncthreads();   // the boxes are read; the next tile may overwrite them
+    }
+    return true;
+}
+
 template <int M>
 __global__ void __launch_bounds__(kThreads, (M <= 4 ? 3 : 2))
 k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_p0,
@@ -178,92 +288,9 @@ k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ 
 
         // ---- A. direction and operator over this CTA's tiles
         double dot_cta = 0.0;
-        for (int t = blockIdx.x; t < ntiles; t += G) {
-            const int x0 = (t % tiles_x) * kTXt, y0 = (t / tiles_x) * kTYt;
-            if (threadIdx.x == 0) {
-                // r and p_old were written through the generic proxy before the last grid barrier
-                asm volatile("fence.proxy.async;" ::: "memory");
-                mbar_expect_tx(&bar, 2 * kBytes);
-                tma_load_3d(sr, &map_r, x0 - XL, y0 - M, 0, &bar);
-                tma_load_3d(sp, mp, x0 - XL, y0 - M, 0, &bar);
-            }
-            if (!mbar_wait(&bar, phase)) {
-                atomicCAS(err, 0, 1);
-                s_fail = 1;
-            }
-            phase ^= 1u;
-            __syncthreads();
-            if (s_fail) {
-                if (threadIdx.x == 0) mbar_wait(&bar, phase ^ 1u);   // let the copies land (bounded)
-                return;
-            }
-            // p = r + beta p_old over the whole box (zero outside the grid stays zero)
-            for (int e = threadIdx.x; e < PLANE; e += kThreads) {
-                sp[e] = sr[e] + b32 * sp[e];
-                sp[PLANE + e] = sr[PLANE + e] + b32 * sp[PLANE + e];
-            }
-            __syncthreads();
-
-            u64 a1[kRt], a2[kRt], w0[WL];
-            tile_pairs<M>(sp + (ty * kRt) * BX + tx + XL, sp + PLANE + (ty * kRt) * BX + tx + XL, tab, a1, a2, w0);
-
-            const int gx = x0 + tx, gy0 = y0 + ty * kRt;
-            const int64_t o0 = (int64_t)gy0 * nx + gx;
-            float dot = 0.f;
-            const bool interior = (x0 >= M) && (x0 + kTXt <= nx - M) && (y0 >= M) && (y0 + kTYt <= ny - M);
-            if (interior && !tile_flags[t]) {
-                const float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
-#pragma unroll
-                for (int r = 0; r < kRt; ++r) {
-                    const float2 up = upk(w0[r + M]);
-                    const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
-                    const float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
-                    const float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
-                    const int64_t p = o0 + (int64_t)r * nx;
-                    v.q[p] = fx;
-                    v.q[N + p] = fy;
-                    pn[p] = up.x;
-                    pn[N + p] = up.y;
-                    dot = __fmaf_rn(up.x, fx, __fmaf_rn(up.y, fy, dot));
-                }
-            } else {
-                const int xc = min(gx, M) * (M + 1) + min(nx - 1 - gx, M);
-#pragma unroll
-                for (int r = 0; r < kRt; ++r) {
-                    const int gy = gy0 + r;
-                    if (gx >= nx || gy >= ny) continue;
-                    const float2 up = upk(w0[r + M]);
-                    const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
-                    const float ax = x1.x + x2.y, ay = x1.y + x2.x;
-                    const int cls = xc * ((M + 1) * (M + 1)) + min(gy, M) * (M + 1) + min(ny - 1 - gy, M);
-                    float kxx, kxy, kyy;
-                    if constexpr (M <= 3) {
-                        kxx = s_kd[3 * cls];
-                        kxy = s_kd[3 * cls + 1];
-                        kyy = s_kd[3 * cls + 2];
-                    } else {
-                        kxx = __ldg(kd + 3 * cls);
-                        kxy = __ldg(kd + 3 * cls + 1);
-                        kyy = __ldg(kd + 3 * cls + 2);
-                    }
-                    float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
-                    float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
-                    const int64_t p = o0 + (int64_t)r * nx;
-                    if (cons) {
-                        const uint8_t m = __ldg(cons + p);
-                        if (m & 1) fx = 0.f;
-                        if (m & 2) fy = 0.f;
-                    }
-                    v.q[p] = fx;
-                    v.q[N + p] = fy;
-                    pn[p] = up.x;
-                    pn[N + p] = up.y;
-                    dot = __fmaf_rn(up.x, fx, __fmaf_rn(up.y, fy, dot));
-                }
-            }
-            dot_cta += (double)dot;
-            __syncthreads();   // the boxes are read; the next tile may overwrite them
-        }
+        if (!cg_dir_tiles<M>(&map_r, mp, sr, sp, pn, v.q, b32, nx, ny, N, tiles_x, ntiles, blockIdx.x, G, cons,
+                             tile_flags, s_kd, kd, tab, &bar, phase, &s_fail, err, dot_cta))
+            return;
         double pq, unused;
         if (!grid_allreduce2(block_sum(dot_cta, red), 0.0, gbar, part, err, &s_fail, s_val, pq, unused)) return;
 
@@ -290,7 +317,7 @@ k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ 
             reinterpret_cast<float4 *>(v.r)[j] = rv;
         }
         double rn;
-        if (!grid_allreduce2(block_sum((double)acc, red), 0.0, gbar, part, err, &s_fail, s_val, rn, unused)) return;
+        if (!grid_allreduce2(block_sum(acc, red), 0.0, gbar, part, err, &s_fail, s_val, rn, unused)) return;
         beta = (rr > 0.0) ? rn / rr : 0.0;
         rr = rn;
         ++iters;
@@ -304,6 +331,47 @@ k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ 
         sc->done = done;
         sc->pbuf = pbuf;
     }
+}
+
+// The direction and operator step of one graph-replayed CG iteration (the
+// update that follows is k_cg_update2 in pd_cg.cu): reads beta and the index of
+// p_old from sc, forms p and q = P K P p for every tile and reduces p.q into
+// sc->pq (last block, fixed order).
+template <int M>
+__global__ void __launch_bounds__(kThreads, (M <= 4 ? 3 : 2))
+k_cg_dirmv(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_p0,
+           const __grid_constant__ CUtensorMap map_p1, const __grid_constant__ CgVecs v, int nx, int ny, int64_t N,
+           int tiles_x, int ntiles, const uint8_t *__restrict__ cons, const uint8_t *__restrict__ tile_flags,
+           const float *__restrict__ kd, PackTab<M> tab, CgScal *sc, double *partial, int *err)
+{
+    constexpr int BX = box_x<M>(), BY = box_y<M>();
+    constexpr int PLANE = BX * BY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *const sr = reinterpret_cast<float *>(smem_raw);
+    float *const sp = sr + 2 * PLANE;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_fail;
+    __shared__ double red[kThreads / 32];
+    constexpr int KDS = (M <= 3) ? 3 * (M + 1) * (M + 1) * (M + 1) * (M + 1) : 1;
+    __shared__ float s_kd[KDS];
+    if (sc->done) return;   // uniform: the solve converged earlier in this chunk
+    if (M <= 3)
+        for (int i = threadIdx.x; i < KDS; i += kThreads) s_kd[i] = __ldg(kd + i);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    __syncthreads();
+    const int pbuf = sc->pbuf;
+    const CUtensorMap *mp = pbuf ? &map_p1 : &map_p0;
+    uint32_t phase = 0;
+    double dot_cta = 0.0;
+    if (!cg_dir_tiles<M>(&map_r, mp, sr, sp, v.p[pbuf ^ 1], v.q, (float)sc->beta, nx, ny, N, tiles_x, ntiles,
+                         blockIdx.x, gridDim.x, cons, tile_flags, s_kd, kd, tab, &bar, phase, &s_fail, err, dot_cta))
+        return;
+    const double s = block_sum(dot_cta, red);
+    grid_finish(s, gridDim.x, blockIdx.x, partial, &sc->pq, &sc->retire[2], red);
 }
 
 // one thread per tile: does the tile's 64 x 32 output block hold a constrained node?
@@ -346,6 +414,29 @@ int launch(pd_grid *g, const CgVecs &v, CgScal *sc, CgBar *gbar, double *part, c
                     (void *)&tiles_x, (void *)&ntiles, (void *)&cons, (void *)&tile_flags, (void *)&kd, (void *)&tab,
                     (void *)&sc, (void *)&gbar, (void *)&part, (void *)&budget, (void *)&err};
     PD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(kThreads), args, smem, s));
+    return PD_OK;
+}
+
+int resident_ctas(int M);
+
+template <int M>
+int launch_dirmv(pd_grid *g, const CgVecs &v, CgScal *sc, double *partial, const uint8_t *tile_flags, cudaStream_t s)
+{
+    constexpr int BX = box_x<M>(), BY = box_y<M>();
+    const int nx = (int)g->n[0], ny = (int)g->n[1];
+    CUtensorMap mr, m0, m1;
+    if (!make_map<M>(&mr, v.r, nx, ny, 1) || !make_map<M>(&m0, v.p[0], nx, ny, 1) ||
+        !make_map<M>(&m1, v.p[1], nx, ny, 1))
+        return fail(PD_ERR_CUDA, "tensor map encode failed");
+    const size_t smem = 4ull * BX * BY * sizeof(float);
+    auto kern = k_cg_dirmv<M>;
+    PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int tiles_x = (nx + kTXt - 1) / kTXt;
+    const int ntiles = cg_persist_ntiles(g);
+    const int G = std::max(1, std::min(ntiles, resident_ctas(M)));
+    kern<<<G, kThreads, smem, s>>>(mr, m0, m1, v, nx, ny, g->N, tiles_x, ntiles, g->has_cons ? g->d_cons : nullptr,
+                                   tile_flags, g->d_kd32, make_pack<M>(g), sc, partial, g->d_err);
+    PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
 
@@ -402,6 +493,29 @@ bool cg_persist_eligible(const pd_grid *g)
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
     const int res = resident_ctas(g->M);
     return res > 0 && cg_persist_ntiles(g) <= res;
+}
+
+bool cg_dirmv_eligible(const pd_grid *g)
+{
+    if (g->dim != 2 || g->has_E || g->broken_total > 0 || g->no_tma) return false;
+    if (g->auto_choice[0] == 2) return false;   // the FFT method was chosen for FP32
+    if (g->M < 1 || g->M > 8 || g->n[0] % 4 != 0) return false;
+    return encode_fn() != nullptr && resident_ctas(g->M) > 0;
+}
+
+int cg_dirmv_run(pd_grid *g, const CgVecs &v, CgScal *sc, double *partial, const uint8_t *tile_flags, cudaStream_t s)
+{
+    switch (g->M) {
+        case 1: return launch_dirmv<1>(g, v, sc, partial, tile_flags, s);
+        case 2: return launch_dirmv<2>(g, v, sc, partial, tile_flags, s);
+        case 3: return launch_dirmv<3>(g, v, sc, partial, tile_flags, s);
+        case 4: return launch_dirmv<4>(g, v, sc, partial, tile_flags, s);
+        case 5: return launch_dirmv<5>(g, v, sc, partial, tile_flags, s);
+        case 6: return launch_dirmv<6>(g, v, sc, partial, tile_flags, s);
+        case 7: return launch_dirmv<7>(g, v, sc, partial, tile_flags, s);
+        case 8: return launch_dirmv<8>(g, v, sc, partial, tile_flags, s);
+    }
+    return fail(PD_ERR_INVALID, "horizon M not compiled for 2D");
 }
 
 int cg_persist_tile_flags(pd_grid *g, uint8_t *tile_flags, cudaStream_t s)

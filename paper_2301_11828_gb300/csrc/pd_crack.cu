@@ -122,6 +122,10 @@ __global__ void k_break_thr(int nnb, const int32_t *__restrict__ off, double h, 
     double r2 = __dadd_rn(__dmul_rn(xi0, xi0), __dmul_rn(xi1, xi1));
     if (DIM == 3) r2 = __dadd_rn(r2, __dmul_rn(xi2, xi2));
     const double r = __dsqrt_rn(r2);
+    double *xi = thr + nnb;   // xi_c = h o_c, rounded once, for k_break
+    xi[3 * kk] = xi0;
+    xi[3 * kk + 1] = xi1;
+    xi[3 * kk + 2] = xi2;
     auto broken = [&](unsigned long long bits) {
         return __ddiv_rn(__dsub_rn(__dsqrt_rn(__longlong_as_double((long long)bits)), r), r) >= s0;
     };
@@ -160,8 +164,8 @@ k_break(const TU *__restrict__ u, int64_t N, int nx, int ny, int nz, int nnb, co
             if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
             const int64_t q = ((int64_t)qk * ny + qj) * nx + qi;
             // Eq. fra:s1 in a fixed operation order, each step rounded once (see k_break_thr).
-            const double xi0 = __dmul_rn(h, (double)ox), xi1 = __dmul_rn(h, (double)oy),
-                         xi2 = __dmul_rn(h, (double)oz);
+            const double xi0 = __ldg(thr + nnb + 3 * kk), xi1 = __ldg(thr + nnb + 3 * kk + 1),
+                         xi2 = __ldg(thr + nnb + 3 * kk + 2);
             const double X0 = __dadd_rn(xi0, __dsub_rn((double)u[q], up[0]));
             const double X1 = __dadd_rn(xi1, __dsub_rn((double)u[N + q], up[1]));
             double l2 = __dadd_rn(__dmul_rn(X0, X0), __dmul_rn(X1, X1));

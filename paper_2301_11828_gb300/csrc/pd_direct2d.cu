@@ -128,7 +128,7 @@ k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
         }
     }
     if (dot_partial)
-        finish_block_dot((double)dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
+        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
                          blockIdx.x + gridDim.x * blockIdx.y, b);
 }
 

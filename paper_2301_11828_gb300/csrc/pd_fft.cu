@@ -238,7 +238,7 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
     }
     if (dot_partial) {
         __shared__ double red[kT / 32];
-        const double s = block_sum((double)dot, red);
+        const double s = block_sum(dot, red);
         grid_finish(s, gridDim.x * gridDim.y, blockIdx.x + gridDim.x * blockIdx.y, dot_partial + b * gridDim.x * gridDim.y,
                     dot_out + b, retire + b, red);
     }

@@ -238,7 +238,7 @@ k_fft3d_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int n
     }
     if (dot_partial) {
         __shared__ double red[kT3 / 32];
-        const double s = block_sum((double)dot, red);
+        const double s = block_sum(dot, red);
         grid_finish(s, per, tix, dot_partial + b * per, dot_out + b, retire + b, red);
     }
 }

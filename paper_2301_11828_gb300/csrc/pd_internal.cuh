@@ -96,7 +96,7 @@ struct pd_grid {
     double *d_coef = nullptr;       // [nnb][ncoef] bond blocks at the current modulus
     double *d_coef1 = nullptr;      // [nnb][ncoef] bond blocks at E = 1
     unsigned long long *d_count = nullptr;   // [0] |Omega_br|, [1] broken total, [2] newly broken (scratch)
-    double *d_brk_thr = nullptr;    // [nnb] breaking threshold on |xi + eta|^2 per offset (upper half used)
+    double *d_brk_thr = nullptr;    // [nnb] threshold on |xi + eta|^2, then [nnb][3] xi = h o (upper half used)
     double brk_thr_s0 = -1.0;       // s0 the thresholds were computed for (< 0: not yet)
     int *d_err = nullptr;                     // device-side error word (bounded waits that ran out)
     double *d_kd64 = nullptr;

@@ -21,6 +21,22 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     return s;
 }
 
+// FP32 values: the butterfly within each warp runs in FP32 (FP64 is a slow pipe
+// on this GPU) and only the per-warp sums are added in FP64.  Result in thread 0.
+__device__ __forceinline__ double block_sum(float v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
 // Grid-wide deterministic reduction of one value per block (the "last block
 // finishes" pattern): every block writes its partial, the block that retires
 // last sums the partials in index order and writes *out, then resets the

@@ -111,7 +111,8 @@ struct CanonTab2 {
 };
 
 // ------------------------------------------------------------------ fused dot epilogue
-__device__ __forceinline__ void finish_block_dot(double v, double *dot_partial, double *dot_out,
+template <typename V>   // float or double: the per-warp part of the sum runs in V
+__device__ __forceinline__ void finish_block_dot(V v, double *dot_partial, double *dot_out,
                                                  unsigned int *retire, int nblk, int bid, int64_t b)
 {
     __shared__ double red[kThreads / 32];

@@ -179,7 +179,7 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
         }
     }
     if (dot_partial)
-        finish_block_dot((double)dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y * nzt,
+        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y * nzt,
                          blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zt), b);
 }
 

@@ -132,3 +132,20 @@ def test_persistent_inner_loop_matches_graph_loop(pd, shape, M):
     assert used_p == 1 and used_g == 0
     assert abs(it_p - it_g) <= 0.25 * it_g + 10
     assert rel_l2(u_p, u_g) <= 1e-4
+
+
+def test_mixed_cg_generic_graph_path(pd):
+    """A row length that is not a multiple of 4 rules out the TMA kernels: the mixed
+    solve then runs the three-launch graph loop and still reaches the true residual."""
+    n, M = (202, 96), 3
+    w = syn.plate_static(n[0], M, tag=8, u_amp=0.0)
+    w.n = n
+    w.h = 1.0 / n[0]
+    w.constrained = syn.clamp_left(2, n, M)
+    w.b = syn.traction_right(2, n, M, 1e-3)
+    g = pd.Grid(2, n, w.h, M, constrained=w.constrained)
+    b = torch.tensor(w.b, device="cuda")
+    u = torch.zeros_like(b)
+    st = pd.pd_cg_solve(g.handle, b, u, 1e-8, 200000, pd.PD_CG_MIXED)
+    assert st.persistent == 0
+    assert _true_rel(w, u.cpu().numpy(), oracle.alpha(2, 1.0, w.delta)) <= 1.05e-8
