@@ -118,6 +118,26 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the job's wall time is the slowest rank's); plain value at N=1."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _weak_value(dof_per_step, steps, world, elapsed_s):
+    """Whole-job GDOF/s: every rank processes its own batch (weak scaling)."""
+    return dof_per_step * steps * world / elapsed_s / 1e9
+
+
+def _rank_seed(rank):
+    """Each rank draws its own independent fields (load cases)."""
+    return 2301_11828 + rank
+
+
 def _time_fn(torch, fn, reps=20, warm=3):
     for _ in range(warm):
         fn()
@@ -204,7 +224,7 @@ def run_ours(args):
     base = torch.tensor(w.u, dtype=torch.float32, device=dev)
     U = torch.empty((B,) + base.shape, dtype=torch.float32, device=dev)
     gen = torch.Generator(device=dev)
-    gen.manual_seed(2301_11828 + rank)
+    gen.manual_seed(_rank_seed(rank))
     U.uniform_(-1.0, 1.0, generator=gen)
     U[0].copy_(base)
     OUT = torch.empty_like(U)
@@ -245,14 +265,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     elapsed = t_s.elapsed_time(t_e) / 1e3
+    elapsed = _max_over_ranks(elapsed, dist, dev)
     if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
         dist.barrier()
     launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
     dof_step = B * 2 * w.N
-    value = dof_step * args.steps * ws / elapsed / 1e9
+    value = _weak_value(dof_step, args.steps, ws, elapsed)
 
     # ---- roofline of the dominant kernel (the stencil launch is the whole step)
     peak, peak_kind = _peaks()
