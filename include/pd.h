@@ -235,8 +235,12 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out);
  * pointers to double [2][N_i]; u_i is the initial guess on entry and the
  * solution on exit.  stats: HOST array of `count` entries or NULL (seconds is
  * the wall time of the whole batch).  Plates are taken in order of size, in
- * groups whose FP32 working set fits in L2; max_iter caps the inner iterations
- * of the slowest plate of each group summed over refinement passes. */
+ * groups whose FP32 working set fits in L2; the groups run concurrently, each
+ * on a stream of the batch, and the call returns with `stream` ordered after
+ * all of them.  Each refinement pass ends after a tenfold drop of the FP32
+ * residual and the next keeps the search direction (reliable updates).
+ * max_iter caps the inner iterations of the slowest plate of each group
+ * summed over refinement passes. */
 int pd_batch_cg_solve(pd_batch *bt, const double *const *b, double *const *u, double rtol, int max_iter,
                       pd_cg_stats *stats, void *stream);
 int pd_batch_destroy(pd_batch *bt);

@@ -13,14 +13,19 @@
 //     re-summed from the tile or chunk partials of that plate in a fixed order
 //     (deterministic), partials of r.r are double-buffered by iteration parity.
 //   * Converged plates drop out: their tiles and chunks return at once.
+//   * Plates are grouped by size (a group's FP32 vectors fit L2); groups are
+//     independent and advance concurrently, each on its own stream with its own
+//     graph, the host serving whichever group's last step has finished.
 // The refinement outer loop (FP64 residual, FP32 inner CG, FP64 update) is
-// the one of PD_CG_MIXED.
+// the one of PD_CG_MIXED: each pass ends after a tenfold drop of the FP32
+// residual, and the next pass keeps the search direction (reliable updates).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pd_reduce.cuh"
@@ -47,8 +52,8 @@ struct PlateDesc {
     double c64[3 * (kMaxPairs + 1)];
 };
 
-// Contiguous tile and chunk ranges of the group being solved (device memory, so
-// that one captured graph serves every group).
+// Contiguous tile and chunk ranges of one group (device memory; each group's
+// captured graph points at its own copy).
 struct BatchRange {
     int tile_begin32, tile_end32, tile_begin64, tile_end64, chunk_begin, chunk_end;
 };
@@ -57,6 +62,8 @@ struct BatchScal {
     double tol2;     // inner stop on r.r (r normalised to |r| = 1 at the start)
     double inv_rn;   // 1 / |r64|
     double rn;       // |r64|
+    double pscale;   // inner start: p = r + pscale p_old (0: new direction)
+    double beta;     // beta of the iteration the inner loop stopped at
     int done;        // inner loop finished (or plate finished)
     int iters;
 };
@@ -285,7 +292,10 @@ k_batch_pupdate(const PlateDesc *__restrict__ desc, const int *__restrict__ cpla
         __syncthreads();
         if (s_stop) {
             // every chunk of the plate reaches the same decision; the flag is read by the next launch
-            if (threadIdx.x == 0) scal[pl].done = 1;
+            if (threadIdx.x == 0) {
+                scal[pl].done = 1;
+                if (c == d.chunk_base) scal[pl].beta = s_beta;   // for the next pass's kept direction
+            }
             __syncthreads();
             continue;
         }
@@ -326,8 +336,10 @@ k_batch_resid(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate
     }
 }
 
-// inner start: r32 = r64 / |r64|, p = r32, x = 0; chunk partials of r32.r32 into rr (the
-// "previous" buffer of the first iteration)
+// inner start: r32 = r64 / |r64|, p = r32 + pscale p_old, x = 0; chunk partials of r32.r32
+// into rr (the "previous" buffer of the first iteration).  pscale = beta_k |r_prev| / |r|
+// keeps the search direction across a residual replacement (p_old was scaled by the
+// previous pass's |r|), which is CG with reliable updates; 0 starts a new direction.
 __global__ void __launch_bounds__(kBT)
 k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, float *r32, float *p32,
               float *x32, const double *__restrict__ r64, double *rr, const BatchScal *__restrict__ scal)
@@ -339,13 +351,14 @@ k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate
         if (scal[pl].done) continue;
         const PlateDesc &d = desc[pl];
         const double inv = scal[pl].inv_rn;
+        const float ps = (float)scal[pl].pscale;
         const int64_t lo = d.off + (int64_t)(c - d.chunk_base) * kChunk;
         const int64_t hi = min(lo + (int64_t)kChunk, d.off + 2 * d.N);
         float acc = 0.f;
         for (int64_t i = lo + threadIdx.x; i < hi; i += kBT) {
             const float v = (float)(r64[i] * inv);
             r32[i] = v;
-            p32[i] = v;
+            p32[i] = (ps != 0.f) ? v + ps * p32[i] : v;
             x32[i] = 0.f;
             acc += v * v;
         }
@@ -406,13 +419,16 @@ struct pd_batch {
     PlateDesc *d_desc32 = nullptr, *d_desc64 = nullptr;
     int *d_cplate = nullptr, *d_active = nullptr;
     BatchScal *d_scal = nullptr;
-    BatchRange *d_range = nullptr;
+    BatchRange *d_range = nullptr;      // [groups] device copies of ranges
     std::vector<BatchRange> ranges;     // per group
     void *ws = nullptr;
     double *u64, *b64, *r64, *q64, *part_t, *rrA, *rrB, *part_c;
     float *r32, *p32, *q32, *x32;
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    std::vector<cudaStream_t> gstream;  // per group: its passes run concurrently with the others
+    std::vector<cudaEvent_t> gevent;    // per group: completion of the last work the host waits for
+    std::vector<cudaGraphExec_t> graph; // per group: 32 inner iterations
+    void *h_pin = nullptr;              // pinned mailbox: BatchScal [np], active [np], part [nch]
     int blocks = 0;
 };
 
@@ -527,8 +543,21 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
         cudaMalloc(&bt->d_cplate, sizeof(int) * bt->nch) != cudaSuccess ||
         cudaMalloc(&bt->d_active, sizeof(int) * count) != cudaSuccess ||
         cudaMalloc(&bt->d_scal, sizeof(BatchScal) * count) != cudaSuccess ||
-        cudaMalloc(&bt->d_range, sizeof(BatchRange)) != cudaSuccess)
+        cudaMalloc(&bt->d_range, sizeof(BatchRange) * bt->groups.size()) != cudaSuccess)
         return bail(PD_ERR_OOM, "batch descriptors");
+    cudaMemcpy(bt->d_range, bt->ranges.data(), sizeof(BatchRange) * bt->groups.size(), cudaMemcpyHostToDevice);
+    if (cudaMallocHost(&bt->h_pin, (sizeof(BatchScal) + sizeof(int)) * count + sizeof(double) * bt->nch + 64) !=
+        cudaSuccess)
+        return bail(PD_ERR_OOM, "batch mailbox");
+    for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return bail(PD_ERR_CUDA, "group stream");
+        bt->gstream.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return bail(PD_ERR_CUDA, "group event");
+        bt->gevent.push_back(ev);
+        bt->graph.push_back(nullptr);
+    }
     cudaMemcpy(bt->d_desc32, d32.data(), sizeof(PlateDesc) * count, cudaMemcpyHostToDevice);
     cudaMemcpy(bt->d_desc64, d64.data(), sizeof(PlateDesc) * count, cudaMemcpyHostToDevice);
     cudaMemcpy(bt->d_cplate, cplate.data(), sizeof(int) * bt->nch, cudaMemcpyHostToDevice);
@@ -564,7 +593,11 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
 int pd_batch_destroy(pd_batch *bt)
 {
     if (!bt) return PD_OK;
-    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    for (auto gr : bt->graph)
+        if (gr) cudaGraphExecDestroy(gr);
+    for (auto st : bt->gstream) cudaStreamDestroy(st);
+    for (auto ev : bt->gevent) cudaEventDestroy(ev);
+    if (bt->h_pin) cudaFreeHost(bt->h_pin);
     if (bt->cap) cudaStreamDestroy(bt->cap);
     cudaFree(bt->d_desc32);
     cudaFree(bt->d_desc64);
@@ -582,16 +615,16 @@ int pd_batch_destroy(pd_batch *bt)
 namespace {
 
 // Two inner iterations (even count keeps the parity of the r.r buffers aligned).
-int batch_two_iterations(pd_batch *bt, cudaStream_t s)
+int batch_two_iterations(pd_batch *bt, const BatchRange *rg, cudaStream_t s)
 {
     for (int k = 0; k < 2; ++k) {
         double *prev = (k == 0) ? bt->rrB : bt->rrA;
         double *cur = (k == 0) ? bt->rrA : bt->rrB;
         k_batch_matvec<float><<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->np, bt->ntiles32, bt->p32, bt->q32,
-                                                         bt->part_t, bt->d_scal, bt->d_range);
-        k_batch_update<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->x32, bt->r32, bt->p32,
+                                                         bt->part_t, bt->d_scal, rg);
+        k_batch_update<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, rg, bt->x32, bt->r32, bt->p32,
                                                   bt->q32, bt->part_t, prev, cur, bt->d_scal);
-        k_batch_pupdate<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->p32, bt->r32, prev, cur,
+        k_batch_pupdate<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, rg, bt->p32, bt->r32, prev, cur,
                                                    bt->d_scal);
     }
     PD_CUDA(cudaGetLastError());
@@ -633,96 +666,170 @@ extern "C" int pd_batch_cg_solve(pd_batch *bt, const double *const *b, double *c
     PD_CUDA(cudaMemcpyAsync(part.data(), bt->part_c, sizeof(double) * bt->nch, cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < bt->nch; ++c) bb[cpl[c]] += part[c];
-    // the inner-loop graph (fixed pointers, reused by every group and pass)
+    // Groups are independent (disjoint plates, tiles and chunks), so each advances
+    // on its own stream as a small state machine and the host serves whichever
+    // group's last step has finished.  Each group replays its own graph of 32
+    // inner iterations (fixed pointers, including its device range).
     constexpr int kPairsPerGraph = 16;   // 32 iterations per replay
-    if (!bt->graph) {
+    constexpr double kRU = 0.1;          // a pass ends after a tenfold drop of the FP32 residual (or at the target)
+    const int ng = (int)bt->groups.size();
+    for (int gi = 0; gi < ng; ++gi) {
+        if (bt->graph[gi]) continue;
         cudaGraph_t gr = nullptr;
         bool ok = cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        for (int k = 0; k < kPairsPerGraph && ok; ++k) ok = batch_two_iterations(bt, bt->cap) == PD_OK;
+        for (int k = 0; k < kPairsPerGraph && ok; ++k) ok = batch_two_iterations(bt, bt->d_range + gi, bt->cap) == PD_OK;
         ok = (cudaStreamEndCapture(bt->cap, &gr) == cudaSuccess) && ok;
-        if (!ok || cudaGraphInstantiate(&bt->graph, gr, 0) != cudaSuccess) bt->graph = nullptr;
+        if (!ok || cudaGraphInstantiate(&bt->graph[gi], gr, 0) != cudaSuccess) bt->graph[gi] = nullptr;
         if (gr) cudaGraphDestroy(gr);
         cudaGetLastError();
     }
-    int status = PD_OK;
-    for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
-        const auto &grp = bt->groups[gi];
-        PD_CUDA(cudaMemcpyAsync(bt->d_range, &bt->ranges[gi], sizeof(BatchRange), cudaMemcpyHostToDevice, s));
-        int group_iters = 0, group_status = PD_ERR_NOT_CONVERGED;
-        for (int pass = 0; pass < 60; ++pass) {
-            // FP64 residual of the group's plates (other plates skip)
-            for (int i = 0; i < np; ++i) {
-                sc[i] = BatchScal{};
-                sc[i].done = (i >= grp.first && i < grp.second) ? 0 : 1;
+    BatchScal *h_sc = (BatchScal *)bt->h_pin;                 // [np]
+    int *h_active = (int *)(h_sc + np);                        // [np]
+    double *h_part = (double *)(((uintptr_t)(h_active + np) + 15) & ~(uintptr_t)15);   // [nch]
+    std::vector<double> beta_last(np, 0.0), rn_prev(np, 0.0);
+    std::vector<int> ran(np, 0);   // the plate ran an inner loop in its group's last pass
+    enum Phase { kResid, kInner, kDone };
+    struct Run {
+        int first, last, cb, ce;   // plates [first, last), chunks [cb, ce)
+        Phase phase = kResid;
+        int pass = 0, group_iters = 0, issued = 0;
+        bool converged = false;
+    };
+    std::vector<Run> run(ng);
+    cudaEvent_t fork = nullptr;
+    PD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    PD_CUDA(cudaEventRecord(fork, s));   // inputs staged on the caller's stream
+    // FP64 residual of a group's plates (its other work is done), its chunk sums to the host
+    auto issue_resid = [&](int gi) -> int {
+        Run &R = run[gi];
+        cudaStream_t st = bt->gstream[gi];
+        for (int i = R.first; i < R.last; ++i) h_sc[i] = BatchScal{};
+        PD_CUDA(cudaMemcpyAsync(bt->d_scal + R.first, h_sc + R.first, sizeof(BatchScal) * (R.last - R.first),
+                                cudaMemcpyHostToDevice, st));
+        k_batch_matvec<double><<<bt->blocks, kBT, 0, st>>>(bt->d_desc64, np, bt->ntiles64, bt->u64, bt->q64, nullptr,
+                                                          bt->d_scal, bt->d_range + gi);
+        k_batch_resid<<<bt->blocks, kBT, 0, st>>>(bt->d_desc64, bt->d_cplate, bt->nch, bt->d_range + gi, bt->r64,
+                                                  bt->b64, bt->q64, bt->part_c, bt->d_scal);
+        PD_CUDA(cudaGetLastError());
+        PD_CUDA(cudaMemcpyAsync(h_part + R.cb, bt->part_c + R.cb, sizeof(double) * (R.ce - R.cb),
+                                cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaEventRecord(bt->gevent[gi], st));
+        R.phase = kResid;
+        return PD_OK;
+    };
+    auto issue_inner = [&](int gi) -> int {
+        cudaStream_t st = bt->gstream[gi];
+        if (bt->graph[gi]) {
+            PD_CUDA(cudaGraphLaunch(bt->graph[gi], st));
+        } else {
+            for (int k = 0; k < kPairsPerGraph; ++k) {
+                int rc = batch_two_iterations(bt, bt->d_range + gi, st);
+                if (rc) return rc;
             }
-            PD_CUDA(cudaMemcpyAsync(bt->d_scal, sc.data(), sizeof(BatchScal) * np, cudaMemcpyHostToDevice, s));
-            k_batch_matvec<double><<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, np, bt->ntiles64, bt->u64, bt->q64,
-                                                              nullptr, bt->d_scal, bt->d_range);
-            k_batch_resid<<<bt->blocks, kBT, 0, s>>>(bt->d_desc64, bt->d_cplate, bt->nch, bt->d_range, bt->r64,
-                                                    bt->b64, bt->q64, bt->part_c, bt->d_scal);
-            PD_CUDA(cudaMemcpyAsync(part.data(), bt->part_c, sizeof(double) * bt->nch, cudaMemcpyDeviceToHost, s));
-            PD_CUDA(cudaStreamSynchronize(s));
-            int n_active = 0;
-            for (int i = grp.first; i < grp.second; ++i) rr[i] = 0.0;
-            for (int c = 0; c < bt->nch; ++c)
-                if (cpl[c] >= grp.first && cpl[c] < grp.second) rr[cpl[c]] += part[c];
-            for (int i = 0; i < np; ++i) {
-                active[i] = 0;
-                sc[i].done = 1;
-                if (i < grp.first || i >= grp.second) continue;
-                ++fmv[i];
-                const double bn = bb[i] > 0 ? std::sqrt(bb[i]) : 1.0;
-                const double rn = std::sqrt(rr[i]);
-                if (rn / bn <= rtol) continue;
-                active[i] = 1;
-                ++outer[i];
-                ++n_active;
-                const double need = 0.3 * rtol * bn / (rn > 0 ? rn : 1.0);
-                const double tau = std::min(0.5, std::max(need, 2e-5));
-                sc[i].tol2 = tau * tau;
-                sc[i].rn = rn;
-                sc[i].inv_rn = rn > 0 ? 1.0 / rn : 0.0;
-                sc[i].done = 0;
-            }
-            if (n_active == 0) {
-                group_status = PD_OK;
-                break;
-            }
-            if (group_iters >= max_iter) break;
-            PD_CUDA(cudaMemcpyAsync(bt->d_scal, sc.data(), sizeof(BatchScal) * np, cudaMemcpyHostToDevice, s));
-            PD_CUDA(cudaMemcpyAsync(bt->d_active, active.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
-            k_batch_start<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->r32, bt->p32, bt->x32,
-                                                    bt->r64, bt->rrB, bt->d_scal);
-            PD_CUDA(cudaGetLastError());
-            int issued = 0;
-            while (group_iters + issued < max_iter) {
-                if (bt->graph) {
-                    PD_CUDA(cudaGraphLaunch(bt->graph, s));
-                } else {
-                    for (int k = 0; k < kPairsPerGraph; ++k) {
-                        int rc = batch_two_iterations(bt, s);
-                        if (rc) return rc;
-                    }
-                }
-                issued += 2 * kPairsPerGraph;
-                PD_CUDA(cudaMemcpyAsync(sc.data(), bt->d_scal, sizeof(BatchScal) * np, cudaMemcpyDeviceToHost, s));
-                PD_CUDA(cudaStreamSynchronize(s));
-                bool all = true;
-                for (int i = grp.first; i < grp.second; ++i) all = all && sc[i].done;
-                if (all) break;
-            }
-            int mx = 0;
-            for (int i = grp.first; i < grp.second; ++i) {
-                iters[i] += sc[i].iters;
-                mx = std::max(mx, sc[i].iters);
-            }
-            group_iters += mx;
-            k_batch_correct<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range, bt->u64, bt->x32,
-                                                      bt->d_scal, bt->d_active);
-            PD_CUDA(cudaGetLastError());
         }
-        if (group_status != PD_OK) status = PD_ERR_NOT_CONVERGED;
+        run[gi].issued += 2 * kPairsPerGraph;
+        PD_CUDA(cudaMemcpyAsync(h_sc + run[gi].first, bt->d_scal + run[gi].first,
+                                sizeof(BatchScal) * (run[gi].last - run[gi].first), cudaMemcpyDeviceToHost, st));
+        PD_CUDA(cudaEventRecord(bt->gevent[gi], st));
+        run[gi].phase = kInner;
+        return PD_OK;
+    };
+    for (int gi = 0; gi < ng; ++gi) {
+        Run &R = run[gi];
+        R.first = bt->groups[gi].first;
+        R.last = bt->groups[gi].second;
+        R.cb = bt->ranges[gi].chunk_begin;
+        R.ce = bt->ranges[gi].chunk_end;
+        PD_CUDA(cudaStreamWaitEvent(bt->gstream[gi], fork, 0));
+        int rc = issue_resid(gi);
+        if (rc) return rc;
     }
+    int status = PD_OK;
+    for (int left = ng; left > 0;) {
+        bool progressed = false;
+        for (int gi = 0; gi < ng; ++gi) {
+            Run &R = run[gi];
+            if (R.phase == kDone) continue;
+            const cudaError_t q = cudaEventQuery(bt->gevent[gi]);
+            if (q == cudaErrorNotReady) continue;
+            PD_CUDA(q);
+            progressed = true;
+            cudaStream_t st = bt->gstream[gi];
+            if (R.phase == kResid) {
+                int n_active = 0;
+                for (int i = R.first; i < R.last; ++i) rr[i] = 0.0;
+                for (int c = R.cb; c < R.ce; ++c) rr[cpl[c]] += h_part[c];
+                for (int i = R.first; i < R.last; ++i) {
+                    const bool kept = ran[i] && std::isfinite(beta_last[i]) && rn_prev[i] > 0.0;
+                    active[i] = 0;
+                    h_sc[i] = BatchScal{};
+                    h_sc[i].done = 1;
+                    ++fmv[i];
+                    const double bn = bb[i] > 0 ? std::sqrt(bb[i]) : 1.0;
+                    const double rn = std::sqrt(rr[i]);
+                    ran[i] = 0;
+                    if (rn / bn <= rtol) continue;
+                    active[i] = 1;
+                    ran[i] = 1;
+                    ++outer[i];
+                    ++n_active;
+                    const double need = 0.3 * rtol * bn / (rn > 0 ? rn : 1.0);
+                    const double tau = std::min(0.5, std::max(kRU, need));
+                    h_sc[i].tol2 = tau * tau;
+                    h_sc[i].rn = rn;
+                    h_sc[i].inv_rn = rn > 0 ? 1.0 / rn : 0.0;
+                    h_sc[i].pscale = (kept && rn > 0) ? beta_last[i] * rn_prev[i] / rn : 0.0;
+                    h_sc[i].done = 0;
+                    rn_prev[i] = rn;
+                }
+                if (n_active == 0 || R.group_iters >= max_iter || R.pass >= 60) {
+                    R.converged = (n_active == 0);
+                    R.phase = kDone;
+                    --left;
+                    continue;
+                }
+                for (int i = R.first; i < R.last; ++i) h_active[i] = active[i];
+                PD_CUDA(cudaMemcpyAsync(bt->d_scal + R.first, h_sc + R.first, sizeof(BatchScal) * (R.last - R.first),
+                                        cudaMemcpyHostToDevice, st));
+                PD_CUDA(cudaMemcpyAsync(bt->d_active + R.first, h_active + R.first, sizeof(int) * (R.last - R.first),
+                                        cudaMemcpyHostToDevice, st));
+                k_batch_start<<<bt->blocks, kBT, 0, st>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range + gi,
+                                                          bt->r32, bt->p32, bt->x32, bt->r64, bt->rrB, bt->d_scal);
+                PD_CUDA(cudaGetLastError());
+                R.issued = 0;
+                int rc = issue_inner(gi);
+                if (rc) return rc;
+            } else {   // kInner: one replay finished
+                bool all = true;
+                for (int i = R.first; i < R.last; ++i) all = all && h_sc[i].done;
+                if (!all && R.group_iters + R.issued < max_iter) {
+                    int rc = issue_inner(gi);
+                    if (rc) return rc;
+                    continue;
+                }
+                int mx = 0;
+                for (int i = R.first; i < R.last; ++i) {
+                    iters[i] += h_sc[i].iters;
+                    mx = std::max(mx, h_sc[i].iters);
+                    beta_last[i] = h_sc[i].beta;
+                }
+                R.group_iters += mx;
+                ++R.pass;
+                k_batch_correct<<<bt->blocks, kBT, 0, st>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range + gi,
+                                                            bt->u64, bt->x32, bt->d_scal, bt->d_active);
+                PD_CUDA(cudaGetLastError());
+                int rc = issue_resid(gi);
+                if (rc) return rc;
+            }
+        }
+        if (!progressed) std::this_thread::yield();
+    }
+    for (int gi = 0; gi < ng; ++gi) {   // join: the caller's stream waits for every group
+        if (!run[gi].converged) status = PD_ERR_NOT_CONVERGED;
+        PD_CUDA(cudaEventRecord(bt->gevent[gi], bt->gstream[gi]));
+        PD_CUDA(cudaStreamWaitEvent(s, bt->gevent[gi], 0));
+    }
+    cudaEventDestroy(fork);
     for (int i = 0; i < np; ++i) {
         const size_t bytes = sizeof(double) * 2 * (size_t)bt->grids[i]->N;
         PD_CUDA(cudaMemcpyAsync(u[bt->order[i]], bt->u64 + bt->offs[i], bytes, cudaMemcpyDeviceToDevice, s));
