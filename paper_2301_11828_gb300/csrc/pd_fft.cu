@@ -18,7 +18,8 @@
 //   3. for each frequency pair (k, -k): unpack U_x, U_y from Z(k), Z(-k)
 //      (both components are real), multiply by the real 2x2 symbol
 //      S(k) = sum_o Kop(o) cos(2 pi k.o / P) / P^2 (Kop(0) = sum c, Kop(o) = -c(o);
-//      the kernel is even, so S is real), repack W = H_x + i H_y;
+//      the kernel is even, so S is real; a quarter of it is staged in shared
+//      memory), repack W = H_x + i H_y;
 //   4. inverse FFTs along y then x;
 //   5. epilogue: K u = Re/Im(w) - (Ctot - Kd_p) u_p on nodes near a face (the
 //      D^e term of Eq. tea:sc), projection, scale, optional fused dot.
@@ -145,8 +146,11 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
 {
     using V = typename C2<T>::t;
     constexpr int TO = P - 2 * M;   // outputs per tile edge
+    constexpr int QH = P / 2 + 1;   // quarter symbol edge
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *Z = reinterpret_cast<V *>(smem_raw);   // [P][PS]
+    T *sq = reinterpret_cast<T *>(Z + P * PS);   // quarter symbol [3][QH][QH]
+    for (int t = threadIdx.x; t < 3 * QH * QH; t += kT) sq[t] = __ldg(sym + t);
 
     const int64_t b = blockIdx.z;
     const T *ub = u + b * 2 * N;
@@ -185,7 +189,12 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
         // U_x = (Z(k) + conj Z(-k)) / 2,  U_y = -i (Z(k) - conj Z(-k)) / 2
         const V ux = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y + zm.y)};
         const V uy = {T(0.5) * (zk.y - zm.y), T(-0.5) * (zk.x - zm.x)};
-        const T sxx = __ldg(sym + t), sxy = __ldg(sym + P * P + t), syy = __ldg(sym + 2 * P * P + t);
+        // S is even in kx and in ky for xx, yy and odd in each for xy (the offset set is
+        // symmetric under ox -> -ox and oy -> -oy), so a quarter of it is stored
+        const int qx = kx <= P / 2 ? kx : P - kx, qy = ky <= P / 2 ? ky : P - ky;
+        const int qi = qy * QH + qx;
+        const T sgn = ((kx > P / 2) != (ky > P / 2)) ? T(-1) : T(1);
+        const T sxx = sq[qi], sxy = sgn * sq[QH * QH + qi], syy = sq[2 * QH * QH + qi];
         const V hx = {sxx * ux.x + sxy * uy.x, sxx * ux.y + sxy * uy.y};
         const V hy = {sxy * ux.x + syy * uy.x, sxy * ux.y + syy * uy.y};
         // W(k) = H_x + i H_y ; W(-k) = conj H_x + i conj H_y
@@ -270,7 +279,7 @@ template <typename T, int M>
 int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
     constexpr int TO = P - 2 * M;
-    const size_t smem = sizeof(typename C2<T>::t) * P * PS;
+    const size_t smem = sizeof(typename C2<T>::t) * P * PS + sizeof(T) * 3 * (P / 2 + 1) * (P / 2 + 1);
     auto kern = k_fft_tile<T, M>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((unsigned)((g->n[0] + TO - 1) / TO), (unsigned)((g->n[1] + TO - 1) / TO), (unsigned)a.batch);
@@ -306,20 +315,21 @@ int run_t(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 
 }  // namespace
 
-// Tile symbol S[c][ky][kx] (c = xx, xy, yy) at the current modulus, scaled by 1/P^2.
+// Tile symbol S[c][ky][kx] (c = xx, xy, yy) at the current modulus, scaled by 1/P^2,
+// for 0 <= kx, ky <= P/2 (the kernel extends it by symmetry).
 int fft_prepare(pd_grid *g)
 {
     if (g->dim != 2) return PD_OK;
     int rc = upload_twiddles();
     if (rc) return rc;
     const double pi = 3.14159265358979323846;
-    std::vector<double> S(3 * P * P, 0.0);
+    constexpr int QH = P / 2 + 1;   // kx, ky in [0, P/2]: the rest follows by symmetry
+    std::vector<double> S(3 * QH * QH, 0.0);
     double ct[3] = {0, 0, 0};
     for (int k = 0; k < g->nnb; ++k)
         for (int c = 0; c < 3; ++c) ct[c] += g->coef1[3 * k + c] * g->E;
-    std::vector<double> cosx(P * P);
-    for (int ky = 0; ky < P; ++ky)
-        for (int kx = 0; kx < P; ++kx) {
+    for (int ky = 0; ky < QH; ++ky)
+        for (int kx = 0; kx < QH; ++kx) {
             double acc[3] = {ct[0], ct[1], ct[2]};
             for (int k = 0; k < g->nnb; ++k) {
                 const int ox = g->off[3 * k], oy = g->off[3 * k + 1];
@@ -327,7 +337,7 @@ int fft_prepare(pd_grid *g)
                 const double cs = std::cos(2.0 * pi * ph / P);
                 for (int c = 0; c < 3; ++c) acc[c] -= g->coef1[3 * k + c] * g->E * cs;
             }
-            for (int c = 0; c < 3; ++c) S[(size_t)c * P * P + ky * P + kx] = acc[c] / ((double)P * P);
+            for (int c = 0; c < 3; ++c) S[(size_t)c * QH * QH + ky * QH + kx] = acc[c] / ((double)P * P);
         }
     std::vector<float> S32(S.begin(), S.end());
     if (!g->d_sym64) {
