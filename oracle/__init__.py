@@ -167,6 +167,67 @@ def cg(dim, n, h, M, alpha_, b, cons=None, E=None, mu=None, x0=None, rtol=1e-8, 
     return x, it, rel.value
 
 
+def adr_density(dim: int, h: float, M: int, alpha_: float) -> np.ndarray:
+    """Fictitious diagonal density of the ADR method (Sec. 2.3, after Kilic and
+    Madenci): D_i = 1/4 dt^2 sum_j |K_ij| with dt = 1, the Gershgorin bound that
+    keeps the central-difference scheme stable.  The interior row has the
+    largest sum, so one value per component serves every node.  Returns [dim]."""
+    T = kernel_table(dim, h, M, alpha_)
+    return np.array([0.25 * np.abs(T[a]).sum() for a in range(dim)])
+
+
+def adr(matvec, b, D, rtol=1e-8, maxit=100000, u0=None, dt=1.0, record=None):
+    """Adaptive dynamic relaxation with the central-difference explicit
+    integration of Algorithm 1 (CDEI) for the static problem K u = b.
+
+    matvec(u) = P K P u; b is projected by the caller; D: fictitious density per
+    component.  f^n = -matvec(u^n) is the internal force, so f^n + b is the
+    residual.  The paper leaves the damping to its reference [KM]: c^n =
+    2 sqrt(u^T K1 u / u^T u) with the diagonal local stiffness
+    K1_ii = -(f_i^n - f_i^(n-1)) / (D_i dt v_i^(n-1/2)) (0 where v_i = 0), and
+    c^n = 0 when the quotient is not positive.  Stops when the relative residual
+    |f^n + b| / |b| <= rtol, checked at u^n before the update.
+    Returns (u, iterations, relative residual); record (a list) receives c^n."""
+    Dn = np.asarray(D, dtype=np.float64).reshape((-1,) + (1,) * (np.ndim(b) - 1))
+    b = np.asarray(b, dtype=np.float64)
+    u = np.zeros_like(b) if u0 is None else np.array(u0, dtype=np.float64)
+    bn = np.linalg.norm(b)
+    bn = bn if bn > 0 else 1.0
+    f = -matvec(u)
+    rel = np.linalg.norm(f + b) / bn
+    if rel <= rtol:
+        return u, 0, rel
+    v = dt * (f + b) / Dn / 2.0           # first half step of Algorithm 1
+    u = u + dt * v
+    f_old = f
+    it = 1
+    while it < maxit:
+        f = -matvec(u)
+        rel = np.linalg.norm(f + b) / bn
+        if rel <= rtol:
+            break
+        with np.errstate(divide="ignore", invalid="ignore"):
+            k1 = np.where(v != 0.0, -(f - f_old) / (Dn * dt * v), 0.0)
+        num = float(np.sum(u * k1 * u))
+        den = float(np.sum(u * u))
+        c = 2.0 * math.sqrt(num / den) if (num > 0.0 and den > 0.0) else 0.0
+        if record is not None:
+            record.append(c)
+        v = ((2.0 - c * dt) * v + 2.0 * dt * (f + b) / Dn) / (2.0 + c * dt)
+        u = u + dt * v
+        f_old = f
+        it += 1
+    return u, it, rel
+
+
+def adr_solve(dim, n, h, M, alpha_, b, cons=None, mu=None, rtol=1e-8, maxit=100000, u0=None, record=None):
+    """ADR (Algorithm 1) on P K P u = P b with the oracle's direct-sum operator."""
+    b = _f64(b)
+    P = 1.0 if cons is None else (1 - np.asarray(cons, dtype=np.float64))
+    mv = lambda x: stiffness(dim, n, h, M, alpha_, x, cons=cons, mu=mu)
+    return adr(mv, b * P, adr_density(dim, h, M, alpha_), rtol=rtol, maxit=maxit, u0=u0, record=record)
+
+
 def intact_mu(dim, n, M) -> np.ndarray:
     """All-intact bond state, uint8 [N][nnb]."""
     return np.ones((int(np.prod(n)), len(offsets(dim, M))), dtype=np.uint8)

@@ -466,3 +466,51 @@ def test_dynamic_modulus_gradient_matches_finite_differences():
             res.append(0.5 * (usp[-1] ** 2).sum())
         fd = (res[0] - res[1]) / (2 * eps)
         assert g[idx] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(g).max())
+
+
+# ---------------------------------------------------------------- ADR (Algorithm 1)
+def test_adr_single_dof_critical_damping():
+    """One spring k with fictitious mass d: the local-stiffness estimate is exact
+    (k/d), so the damping is the critical value 2 sqrt(k/d) of a 1-DOF
+    oscillator, and the iteration settles at the static answer b/k."""
+    k, d, b = 3.0, 5.0, np.array([2.0])
+    rec = []
+    u, it, rel = oracle.adr(lambda x: k * x, b, np.array([d]), rtol=1e-12, maxit=10000, record=rec)
+    assert rec and abs(rec[0] - 2.0 * np.sqrt(k / d)) <= 1e-14
+    assert abs(u[0] - b[0] / k) <= 1e-11 and rel <= 1e-12
+
+
+def test_adr_uncoupled_springs_converge():
+    """Diagonal stiffness (uncoupled DOFs) with the Gershgorin density d = k/4 x 1.2:
+    the answer is b / k componentwise."""
+    rng = np.random.default_rng(5)
+    kk = rng.uniform(0.5, 4.0, (2, 7))
+    b = rng.uniform(-1.0, 1.0, (2, 7))
+    D = np.array([0.25 * kk[0].max() * 1.2, 0.25 * kk[1].max() * 1.2])
+    u, it, rel = oracle.adr(lambda x: kk * x, b, D, rtol=1e-11, maxit=200000)
+    assert np.max(np.abs(u - b / kk)) <= 1e-9
+
+
+@pytest.mark.parametrize("M", [2, 3])
+def test_adr_reaches_the_cg_solution(M):
+    """ADR on the plate (clamp left, traction right) converges to the solution of
+    the same projected system found by textbook CG."""
+    w = syn.plate_static(24, M, tag=3, u_amp=0.0)
+    al = oracle.alpha(2, 1.0, w.delta)
+    u, it, rel = oracle.adr_solve(2, w.n, w.h, w.M, al, w.b, cons=w.constrained, rtol=1e-10, maxit=200000)
+    x, _, _ = oracle.cg(2, w.n, w.h, w.M, al, w.b, cons=w.constrained, rtol=1e-13)
+    assert rel <= 1e-10
+    assert np.linalg.norm(u - x) / np.linalg.norm(x) <= 1e-7
+
+
+def test_adr_density_is_the_gershgorin_row_sum():
+    """D = 1/4 sum_j |K_ij| for an interior row, against the dense matrix."""
+    n, M, h = (12, 11), 3, 1.0 / 12
+    al = oracle.alpha(2, 1.0, M * h)
+    Kd = -oracle.dense_matrix(2, n, h, M, al)
+    D = oracle.adr_density(2, h, M, al)
+    N = n[0] * n[1]
+    p = 5 * n[0] + 6   # interior node (full horizon)
+    for a in range(2):
+        row = Kd[a * N + p]
+        assert abs(0.25 * np.abs(row).sum() - D[a]) <= 1e-12 * D[a]
