@@ -139,6 +139,23 @@ int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_
 int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter,
                 uint32_t mode, pd_cg_stats *stats, void *stream);
 
+/* The paper's quasi-static solver: adaptive dynamic relaxation with the
+ * central-difference explicit integration of Algorithm 1 (Sec. 2.3), dt = 1,
+ * on P K P u = P b.  The paper leaves the fictitious density D and the damping
+ * c to its reference (Kilic and Madenci): D_i = 1/4 sum_j |K_ij| (Gershgorin,
+ * interior row), c^n = 2 sqrt(u^T K1 u / u^T u) with the diagonal local
+ * stiffness K1_ii = -(f_i^n - f_i^(n-1)) / (D_i v_i^(n-1/2)), 0 when not
+ * positive.  FP64 throughout; any operator method of pd_matvec, broken bonds
+ * included; constant modulus only (PD_ERR_INVALID with a modulus field).
+ * b, u: DEVICE double [dim][N]; u is the initial guess on entry and the
+ * solution on exit (constrained components set to 0).  Stops when
+ * ||P(b - K u)|| <= rtol ||P b|| at an iterate, before its update; at most
+ * max_iter updates (stats->iterations counts them), PD_ERR_NOT_CONVERGED after
+ * that with u holding the last iterate and stats filled (outer = 0,
+ * persistent = 0). */
+int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter, pd_cg_stats *stats,
+                 void *stream);
+
 /* Velocity-Verlet (Algorithm 2) with acceleration a = (f + b)/rho, f = A(mu) u,
  * and bond breaking (Eqs. mu, fra:s1) after each drift.  u, v: DEVICE double
  * [dim][N], updated in place; b: DEVICE double [dim][N] or NULL.

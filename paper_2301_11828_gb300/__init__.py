@@ -67,6 +67,7 @@ SIGNATURES = {
     "pd_matvec": (_I, [_VP, _VP, _VP, _U32, _VP]),
     "pd_matvec_batch": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
     "pd_cg_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
+    "pd_adr_solve": (_I, [_VP, _VP, _VP, _D, _I, ctypes.POINTER(pd_cg_stats), _VP]),
     "pd_step": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats), _VP]),
     "pd_step_noalloc": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats),
                              _VP]),
@@ -162,6 +163,16 @@ def pd_matvec(g, u, out, flags: int, stream=None):
 
 def pd_matvec_batch(g, batch: int, u, out, flags: int, stream=None):
     _check(load_library().pd_matvec_batch(g, int(batch), _dptr(u), _dptr(out), int(flags), _stream(stream)))
+
+
+def pd_adr_solve(g, b, u, rtol: float, max_iter: int, stream=None, allow_not_converged=False):
+    import torch
+    st = pd_cg_stats()
+    rc = load_library().pd_adr_solve(g, _dptr(b, torch.float64), _dptr(u, torch.float64), float(rtol), int(max_iter),
+                                     ctypes.byref(st), _stream(stream))
+    if not (allow_not_converged and rc == PD_ERR_NOT_CONVERGED):
+        _check(rc)
+    return st
 
 
 def pd_cg_solve(g, b, u, rtol: float, max_iter: int, mode: int, stream=None, allow_not_converged=False):
@@ -329,6 +340,14 @@ class Grid:
         else:
             pd_matvec_batch(self.handle, batch, u, out, flags | _dtype_flag(u), stream)
         return out
+
+    def adr_solve(self, b, u=None, rtol=1e-8, max_iter=1000000, stream=None):
+        """The paper's ADR/CDEI static solver (Algorithm 1), FP64."""
+        import torch
+        if u is None:
+            u = torch.zeros_like(b)
+        st = pd_adr_solve(self.handle, b, u, rtol, max_iter, stream)
+        return u, st
 
     def cg_solve(self, b, u=None, rtol=1e-8, max_iter=100000, mode=PD_CG_MIXED, stream=None):
         import torch

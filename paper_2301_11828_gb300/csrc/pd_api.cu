@@ -132,6 +132,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_coef1);
     cudaFree(g->ws);
     cg_release(g);
+    adr_release(g);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     delete g;
 }

@@ -119,6 +119,7 @@ struct pd_grid {
     int auto_choice[2] = {0, 0};
 
     void *cg = nullptr;        // CG workspace and captured graphs (pd_cg.cu)
+    void *adr = nullptr;       // ADR workspace and captured graph (pd_adr.cu)
     bool no_tma = false;       // use the plain FP32 stencil instead of the TMA-fed one
     int64_t op_stamp = 0;      // bumped whenever the operator changes (material, bond state)
 };
@@ -170,6 +171,7 @@ constexpr uint32_t kForceMu = 0x80000000u;
 constexpr uint32_t kInputProjected = 0x40000000u;
 int upload_coefs(pd_grid *g);
 void cg_release(pd_grid *g);
+void adr_release(pd_grid *g);
 int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, cudaStream_t s,
            double *dot_partial = nullptr, double *dot_out = nullptr, unsigned int *retire = nullptr,
            double scale = 1.0);
