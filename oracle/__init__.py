@@ -62,13 +62,13 @@ def lib():
             L.or_alpha.restype = ctypes.c_double
             L.or_bond_block.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp]
             L.or_force.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                   dp, dp, dp, dp]
+                                   dp, dp, dp, dp, dp]
             L.or_force.restype = ctypes.c_int
             L.or_stiffness.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                       dp, dp, dp, dp, dp]
+                                       dp, dp, dp, dp, dp, dp]
             L.or_stiffness.restype = ctypes.c_int
             L.or_cg.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                dp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
+                                dp, dp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_double)]
             L.or_cg.restype = ctypes.c_int
             L.or_break.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
@@ -76,12 +76,17 @@ def lib():
             L.or_prenotch.argtypes = [i64p, ctypes.c_int, i64p, ctypes.c_int64, dp]
             L.or_prenotch.restype = ctypes.c_int64
             L.or_vv.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp,
-                                dp, ctypes.c_double, dp, dp, dp, ctypes.c_double, ctypes.c_double,
+                                dp, dp, ctypes.c_double, dp, dp, dp, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_int, dp, dp]
             L.or_vv.restype = ctypes.c_int64
             L.or_grad_modulus.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-                                          dp, dp, dp, dp]
+                                          dp, dp, dp, dp, dp]
             L.or_grad_modulus.restype = ctypes.c_int
+            L.or_surface_nu.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, dp]
+            L.or_surface_nu.restype = ctypes.c_int
+            L.or_row_abs_max.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                         dp, dp]
+            L.or_row_abs_max.restype = ctypes.c_int
             L.or_threads.argtypes = []
             L.or_threads.restype = ctypes.c_int
             _lib = L
@@ -137,31 +142,32 @@ def bond_block(dim: int, o, h: float, M: int, alpha_: float) -> np.ndarray:
     return out.reshape(3, 3)[:dim, :dim]
 
 
-def force(dim, n, h, M, alpha_, u, E=None, mu=None) -> np.ndarray:
-    """f = A(mu) u by direct summation (Eq. mat:f1).  u: [dim][...] float64."""
+def force(dim, n, h, M, alpha_, u, E=None, mu=None, nu=None) -> np.ndarray:
+    """f = A(mu) u by direct summation (Eq. mat:f1).  u: [dim][...] float64.
+    nu: surface-correction factors (``surface_nu``) or None."""
     u = _f64(u)
     f = np.empty_like(u)
-    rc = lib().or_force(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(_u8(mu)), _ptr(u), _ptr(f))
+    rc = lib().or_force(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(_u8(mu)), _ptr(_f64(nu)), _ptr(u), _ptr(f))
     assert rc > 0
     return f
 
 
-def stiffness(dim, n, h, M, alpha_, u, cons=None, E=None, mu=None) -> np.ndarray:
+def stiffness(dim, n, h, M, alpha_, u, cons=None, E=None, mu=None, nu=None) -> np.ndarray:
     """out = P K P u with K = -A and P zeroing constrained components."""
     u = _f64(u)
     out = np.empty_like(u)
-    rc = lib().or_stiffness(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(_u8(mu)), _ptr(_u8(cons)),
+    rc = lib().or_stiffness(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(_u8(mu)), _ptr(_f64(nu)), _ptr(_u8(cons)),
                             _ptr(u), _ptr(out))
     assert rc > 0
     return out
 
 
-def cg(dim, n, h, M, alpha_, b, cons=None, E=None, mu=None, x0=None, rtol=1e-8, maxit=100000):
+def cg(dim, n, h, M, alpha_, b, cons=None, E=None, mu=None, x0=None, rtol=1e-8, maxit=100000, nu=None):
     """Textbook CG on P K P x = P b.  Returns (x, iterations, true relative residual)."""
     b = _f64(b)
     x = np.zeros_like(b) if x0 is None else _f64(x0).copy()
     rel = ctypes.c_double(0.0)
-    it = lib().or_cg(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(_u8(mu)), _ptr(_u8(cons)),
+    it = lib().or_cg(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(_u8(mu)), _ptr(_f64(nu)), _ptr(_u8(cons)),
                      _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(rel))
     assert it >= 0
     return x, it, rel.value
@@ -220,12 +226,31 @@ def adr(matvec, b, D, rtol=1e-8, maxit=100000, u0=None, dt=1.0, record=None):
     return u, it, rel
 
 
-def adr_solve(dim, n, h, M, alpha_, b, cons=None, mu=None, rtol=1e-8, maxit=100000, u0=None, record=None):
-    """ADR (Algorithm 1) on P K P u = P b with the oracle's direct-sum operator."""
+def adr_solve(dim, n, h, M, alpha_, b, cons=None, mu=None, rtol=1e-8, maxit=100000, u0=None, record=None,
+              nu=None):
+    """ADR (Algorithm 1) on P K P u = P b with the oracle's direct-sum operator.
+    With surface-correction factors nu the density is 1/4 of the largest
+    absolute row sum over all rows (edge rows can exceed the interior one)."""
     b = _f64(b)
     P = 1.0 if cons is None else (1 - np.asarray(cons, dtype=np.float64))
-    mv = lambda x: stiffness(dim, n, h, M, alpha_, x, cons=cons, mu=mu)
-    return adr(mv, b * P, adr_density(dim, h, M, alpha_), rtol=rtol, maxit=maxit, u0=u0, record=record)
+    mv = lambda x: stiffness(dim, n, h, M, alpha_, x, cons=cons, mu=mu, nu=nu)
+    D = adr_density(dim, h, M, alpha_) if nu is None else 0.25 * row_abs_max(dim, n, h, M, alpha_, nu)
+    return adr(mv, b * P, D, rtol=rtol, maxit=maxit, u0=u0, record=record)
+
+
+def surface_nu(dim, n, h, M) -> np.ndarray:
+    """Surface-correction factor per node (volume method, the reading of the
+    remark on Omega_e in Sec. 3.3): nu_p = V_full / V_p, shape node_shape(n)."""
+    nu = np.empty(int(np.prod(n)), dtype=np.float64)
+    assert lib().or_surface_nu(dim, _n64(n), h, M, _ptr(nu)) > 0
+    return nu.reshape(tuple(reversed([int(v) for v in n])))
+
+
+def row_abs_max(dim, n, h, M, alpha_, nu=None) -> np.ndarray:
+    """Largest absolute row sum of K per component (bonds intact, no projection)."""
+    out = np.zeros(3)
+    assert lib().or_row_abs_max(dim, _n64(n), h, M, alpha_, _ptr(_f64(nu)), _ptr(out)) > 0
+    return out[:dim]
 
 
 def intact_mu(dim, n, M) -> np.ndarray:
@@ -247,16 +272,17 @@ def prenotch(n, M, seg, den, mu) -> int:
 
 
 def vv(dim, n, h, M, alpha_, u, v, nsteps, dt, rho=1.0, b=None, E=None, mu=None, s0=0.0,
-       cons=None, vpres=None) -> int:
+       cons=None, vpres=None, nu=None) -> int:
     """Velocity-Verlet (Algorithm 2) in place on u, v (float64 contiguous); returns bonds broken."""
     assert u.dtype == np.float64 and v.dtype == np.float64
-    return int(lib().or_vv(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(mu), s0, _ptr(_u8(cons)),
+    return int(lib().or_vv(dim, _n64(n), h, M, alpha_, _ptr(_f64(E)), _ptr(mu), _ptr(_f64(nu)), s0, _ptr(_u8(cons)),
                            _ptr(_f64(vpres)), _ptr(_f64(b)), rho, dt, nsteps, _ptr(u), _ptr(v)))
 
 
-def grad_modulus(dim, n, h, M, alpha1, u, lam_, mu=None) -> np.ndarray:
+def grad_modulus(dim, n, h, M, alpha1, u, lam_, mu=None, nu=None) -> np.ndarray:
     g = np.empty(int(np.prod(n)), dtype=np.float64)
-    lib().or_grad_modulus(dim, _n64(n), h, M, alpha1, _ptr(_u8(mu)), _ptr(_f64(u)), _ptr(_f64(lam_)), _ptr(g))
+    lib().or_grad_modulus(dim, _n64(n), h, M, alpha1, _ptr(_u8(mu)), _ptr(_f64(nu)), _ptr(_f64(u)),
+                          _ptr(_f64(lam_)), _ptr(g))
     return g.reshape(tuple(reversed([int(v) for v in n])))
 
 

@@ -112,9 +112,11 @@ void or_bond_block(int dim, const int32_t *o, double h, int M, double alpha, dou
  * alpha: the micromodulus constant; when E is not NULL, alpha is the value
  *        for E = 1 and the bond (p, q) uses modulus (E_p + E_q) / 2.
  * mu:    NULL (all bonds intact) or [N][nnb] bytes.
+ * nu:    NULL, or the per-node surface-correction factors of or_surface_nu:
+ *        the bond (p, q) is then scaled by v_pq = (nu_p + nu_q) / 2.
  */
 int or_force(int dim, const int64_t *n, double h, int M, double alpha,
-             const double *E, const uint8_t *mu, const double *u, double *f)
+             const double *E, const uint8_t *mu, const double *nu, const double *u, double *f)
 {
     int32_t off[3 * 16384];
     int nnb = or_offsets(dim, M, off, 16384);
@@ -135,6 +137,7 @@ int or_force(int dim, const int64_t *n, double h, int M, double alpha,
             if (mu && !mu[p * nnb + k]) continue;
             int64_t q = qi + nx * (qj + ny * qk);
             double scale = E ? 0.5 * (E[p] + E[q]) : 1.0;
+            if (nu) scale *= 0.5 * (nu[p] + nu[q]);
             for (int a = 0; a < dim; ++a) {
                 double s = 0.0;
                 for (int b = 0; b < dim; ++b)
@@ -151,14 +154,14 @@ int or_force(int dim, const int64_t *n, double h, int M, double alpha,
 /* Stiffness product with the volume constraint: out = P K P u, K = -A, where
  * P zeroes the constrained components (cons[c * N + p] != 0). */
 int or_stiffness(int dim, const int64_t *n, double h, int M, double alpha,
-                 const double *E, const uint8_t *mu, const uint8_t *cons,
+                 const double *E, const uint8_t *mu, const double *nu, const uint8_t *cons,
                  const double *u, double *out)
 {
     const int64_t N = n[0] * n[1] * ((dim == 3) ? n[2] : 1);
     double *up = malloc(sizeof(double) * (size_t)(dim * N));
     if (!up) return -2;
     for (int64_t t = 0; t < dim * N; ++t) up[t] = (cons && cons[t]) ? 0.0 : u[t];
-    int rc = or_force(dim, n, h, M, alpha, E, mu, up, out);
+    int rc = or_force(dim, n, h, M, alpha, E, mu, nu, up, out);
     for (int64_t t = 0; t < dim * N; ++t) out[t] = (cons && cons[t]) ? 0.0 : -out[t];
     free(up);
     return rc;
@@ -181,7 +184,7 @@ static double dot(const double *a, const double *b, int64_t len)
  * negative error); *relres receives ||P(b - K x)|| / ||P b|| recomputed from
  * scratch at the end. */
 int or_cg(int dim, const int64_t *n, double h, int M, double alpha, const double *E,
-          const uint8_t *mu, const uint8_t *cons, const double *b, double *x,
+          const uint8_t *mu, const double *nu, const uint8_t *cons, const double *b, double *x,
           double rtol, int maxit, double *relres)
 {
     const int64_t N = n[0] * n[1] * ((dim == 3) ? n[2] : 1), L = dim * N;
@@ -196,12 +199,12 @@ int or_cg(int dim, const int64_t *n, double h, int M, double alpha, const double
     if (bnorm == 0.0) bnorm = 1.0;
     int it = 0;
     for (int restart = 0; restart < 8 && it < maxit; ++restart) {
-        or_stiffness(dim, n, h, M, alpha, E, mu, cons, x, q);
+        or_stiffness(dim, n, h, M, alpha, E, mu, nu, cons, x, q);
         for (int64_t t = 0; t < L; ++t) { r[t] = pb[t] - q[t]; p[t] = r[t]; }
         double rr = dot(r, r, L);
         if (sqrt(rr) / bnorm <= rtol) break;
         for (; it < maxit; ++it) {
-            or_stiffness(dim, n, h, M, alpha, E, mu, cons, p, q);
+            or_stiffness(dim, n, h, M, alpha, E, mu, nu, cons, p, q);
             double a = rr / dot(p, q, L);
             for (int64_t t = 0; t < L; ++t) { x[t] += a * p[t]; r[t] -= a * q[t]; }
             double rr_new = dot(r, r, L);
@@ -211,7 +214,7 @@ int or_cg(int dim, const int64_t *n, double h, int M, double alpha, const double
             for (int64_t t = 0; t < L; ++t) p[t] = r[t] + beta * p[t];
         }
     }
-    or_stiffness(dim, n, h, M, alpha, E, mu, cons, x, q);
+    or_stiffness(dim, n, h, M, alpha, E, mu, nu, cons, x, q);
     for (int64_t t = 0; t < L; ++t) r[t] = pb[t] - q[t];
     *relres = sqrt(dot(r, r, L)) / bnorm;
     free(r); free(p); free(q); free(pb);
@@ -340,13 +343,13 @@ int64_t or_prenotch(const int64_t *n, int M, const int64_t *seg, int64_t den, ui
  * Returns the number of bonds broken during the call.
  */
 int64_t or_vv(int dim, const int64_t *n, double h, int M, double alpha, const double *E,
-              uint8_t *mu, double s0, const uint8_t *cons, const double *vpres,
+              uint8_t *mu, const double *nu, double s0, const uint8_t *cons, const double *vpres,
               const double *b, double rho, double dt, int nsteps, double *u, double *v)
 {
     const int64_t N = n[0] * n[1] * ((dim == 3) ? n[2] : 1), L = dim * N;
     double *a = malloc(sizeof(double) * L), *an = malloc(sizeof(double) * L);
     if (!a || !an) { free(a); free(an); return -2; }
-    or_force(dim, n, h, M, alpha, E, mu, u, a);
+    or_force(dim, n, h, M, alpha, E, mu, nu, u, a);
     for (int64_t t = 0; t < L; ++t) a[t] = (a[t] + (b ? b[t] : 0.0)) / rho;
     int64_t broken = 0;
     for (int s = 0; s < nsteps; ++s) {
@@ -355,7 +358,7 @@ int64_t or_vv(int dim, const int64_t *n, double h, int M, double alpha, const do
             else u[t] += dt * v[t] + 0.5 * dt * dt * a[t];
         }
         if (mu && s0 > 0.0) broken += or_break(dim, n, h, M, s0, u, mu);
-        or_force(dim, n, h, M, alpha, E, mu, u, an);
+        or_force(dim, n, h, M, alpha, E, mu, nu, u, an);
         for (int64_t t = 0; t < L; ++t) {
             an[t] = (an[t] + (b ? b[t] : 0.0)) / rho;
             if (cons && cons[t]) v[t] = vpres ? vpres[t] : 0.0;
@@ -376,10 +379,11 @@ int64_t or_vv(int dim, const int64_t *n, double h, int M, double alpha, const do
  *   dL/dE_r = -(alpha1/2) sum_{q in N(r), intact} (lam_q - lam_r)^T Chat(q - r) (u_q - u_r)
  * where lam solves K_P lam = P dL/du and alpha1 Chat is the bond block at
  * E = 1 (alpha = alpha1).  u and lam are the projected (constrained-zero)
- * vectors.  Writes g[N].
+ * vectors.  With surface-correction factors nu (nullable) each bond term also
+ * carries v_rq = (nu_r + nu_q) / 2.  Writes g[N].
  */
 int or_grad_modulus(int dim, const int64_t *n, double h, int M, double alpha1,
-                    const uint8_t *mu, const double *u, const double *lam, double *g)
+                    const uint8_t *mu, const double *nu, const double *u, const double *lam, double *g)
 {
     int32_t off[3 * 16384];
     int nnb = or_offsets(dim, M, off, 16384);
@@ -397,15 +401,106 @@ int or_grad_modulus(int dim, const int64_t *n, double h, int M, double alpha1,
             if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
             if (mu && !mu[p * nnb + k]) continue;
             int64_t q = qi + nx * (qj + ny * qk);
+            double t = 0.0;
             for (int a = 0; a < dim; ++a)
                 for (int b = 0; b < dim; ++b)
-                    acc += (lam[a * N + q] - lam[a * N + p]) * blk[k][a][b] *
-                           (u[b * N + q] - u[b * N + p]);
+                    t += (lam[a * N + q] - lam[a * N + p]) * blk[k][a][b] *
+                         (u[b * N + q] - u[b * N + p]);
+            acc += nu ? 0.5 * (nu[p] + nu[q]) * t : t;
         }
         g[p] = -0.5 * acc;
     }
     free(blk);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Surface correction (the remark on Omega_e in Sec. 3.3 and Eq. scr)         */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The paper scales the bonds of nodes with an incomplete horizon by a
+ * factor v_pq and leaves the factor to its reference; the reading taken here
+ * is the volume method: with V_p the partial volume of the part of the
+ * horizon of p inside the grid,
+ *   V_p = sum over neighbours q of p inside the grid of lambda(|x_q - x_p|) h^dim,
+ * and V_full the same sum over the complete horizon,
+ *   nu_p = V_full / V_p   (1 on every node with a complete horizon),
+ * and every bond uses the mean of its two ends, v_pq = (nu_p + nu_q) / 2, so
+ * that A stays symmetric.  The common factor h^dim cancels in the ratio.
+ * Writes nu[N]; returns the offset count.
+ */
+int or_surface_nu(int dim, const int64_t *n, double h, int M, double *nu)
+{
+    int32_t off[3 * 16384];
+    int nnb = or_offsets(dim, M, off, 16384);
+    if (nnb < 0) return -1;
+    double *lam = malloc(sizeof(double) * (size_t)nnb);
+    if (!lam) return -2;
+    double full = 0.0;
+    for (int k = 0; k < nnb; ++k) {
+        double r2 = 0.0;
+        for (int a = 0; a < dim; ++a) r2 += (h * off[3 * k + a]) * (h * off[3 * k + a]);
+        lam[k] = or_lambda(sqrt(r2), M * h, h);
+        full += lam[k];
+    }
+    const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
+    const int64_t N = nx * ny * nz;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < N; ++p) {
+        int64_t i = p % nx, j = (p / nx) % ny, kz = p / (nx * ny);
+        double V = 0.0;
+        for (int k = 0; k < nnb; ++k) {
+            int64_t qi = i + off[3 * k], qj = j + off[3 * k + 1], qk = kz + off[3 * k + 2];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
+            V += lam[k];
+        }
+        nu[p] = full / V;
+    }
+    free(lam);
+    return nnb;
+}
+
+/*
+ * Largest absolute row sum of K (all bonds intact, no projection) per
+ * component: out[a] = max_p sum over columns (q, b) of |K_(p,a),(q,b)|, where
+ * the diagonal block of row p is sum_q v_pq C_pq and the off-diagonal blocks
+ * are -v_pq C_pq (nu NULL: v = 1).  This is the Gershgorin bound behind the
+ * fictitious density of the ADR method.
+ */
+int or_row_abs_max(int dim, const int64_t *n, double h, int M, double alpha, const double *nu, double *out)
+{
+    int32_t off[3 * 16384];
+    int nnb = or_offsets(dim, M, off, 16384);
+    if (nnb < 0) return -1;
+    double (*blk)[3][3] = malloc(sizeof(double[3][3]) * (size_t)nnb);
+    if (!blk) return -2;
+    for (int k = 0; k < nnb; ++k) bond_block(dim, off + 3 * k, h, M, alpha, blk[k]);
+    const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
+    const int64_t N = nx * ny * nz;
+    for (int a = 0; a < 3; ++a) out[a] = 0.0;
+    for (int64_t p = 0; p < N; ++p) {
+        int64_t i = p % nx, j = (p / nx) % ny, kz = p / (nx * ny);
+        double diag[3][3] = {{0}}, offsum[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < nnb; ++k) {
+            int64_t qi = i + off[3 * k], qj = j + off[3 * k + 1], qk = kz + off[3 * k + 2];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
+            int64_t q = qi + nx * (qj + ny * qk);
+            double v = nu ? 0.5 * (nu[p] + nu[q]) : 1.0;
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) {
+                    diag[a][b] += v * blk[k][a][b];
+                    offsum[a] += fabs(v * blk[k][a][b]);
+                }
+        }
+        for (int a = 0; a < dim; ++a) {
+            double r = offsum[a];
+            for (int b = 0; b < dim; ++b) r += fabs(diag[a][b]);
+            if (r > out[a]) out[a] = r;
+        }
+    }
+    free(blk);
+    return nnb;
 }
 
 /* Number of threads the OpenMP loops above use (1 without OpenMP). */

@@ -514,3 +514,101 @@ def test_adr_density_is_the_gershgorin_row_sum():
     for a in range(2):
         row = Kd[a * N + p]
         assert abs(0.25 * np.abs(row).sum() - D[a]) <= 1e-12 * D[a]
+
+
+# --------------------------------------------------------------------------- surface correction
+
+def test_surface_nu_hand_values():
+    """nu = V_full / V_p with lambda-weighted partial volumes, worked by hand.
+
+    2D M = 1: the four axis bonds have lambda = 1/2, V_full = 2: corner 2/1,
+    edge 2/1.5.  2D M = 2: axis-1 and diagonal bonds lambda = 1, axis-2 bonds
+    lambda = 1/2, V_full = 10: corner 10/4, edge 10/6.5, the node one step in
+    from two faces 10/9.  3D M = 1: V_full = 3: corner 3/1.5, edge 3/2, face
+    3/2.5.  Catches an unweighted count, an inverted ratio and an off-by-one in
+    the in-grid test."""
+    nu = oracle.surface_nu(2, (5, 4), 1.0 / 8, 1)
+    assert nu[0, 0] == 2.0 and nu[3, 4] == 2.0
+    assert abs(nu[0, 2] - 4.0 / 3.0) <= 1e-15 and abs(nu[2, 0] - 4.0 / 3.0) <= 1e-15
+    assert np.all(nu[1:3, 1:4] == 1.0)
+    nu = oracle.surface_nu(2, (9, 8), 1.0 / 16, 2)
+    assert abs(nu[0, 0] - 2.5) <= 1e-15
+    assert abs(nu[4, 0] - 10.0 / 6.5) <= 1e-15
+    assert abs(nu[1, 1] - 10.0 / 9.0) <= 1e-15
+    assert np.all(nu[2:6, 2:7] == 1.0)
+    nu = oracle.surface_nu(3, (4, 4, 4), 1.0 / 4, 1)
+    assert nu[0, 0, 0] == 2.0 and nu[3, 3, 3] == 2.0
+    assert nu[0, 0, 1] == 1.5 and nu[0, 1, 1] == 1.2
+    assert np.all(nu[1:3, 1:3, 1:3] == 1.0)
+
+
+@pytest.mark.parametrize("dim,n,M", [(2, (8, 8), 2), (2, (11, 7), 3), (3, (5, 6, 7), 2)])
+def test_surface_corrected_force_equals_symmetrised_dense(dim, n, M):
+    """A_sc off the diagonal is (N A + A N) / 2 with N = diag(nu) (the bond
+    factor (nu_p + nu_q) / 2), and each diagonal block is minus the sum of its
+    row's off-diagonal blocks; built from the dense matrix, against the direct
+    sum with nu.  Catches a one-sided factor (nu_p only), a product instead of
+    the mean, and a diagonal left uncorrected."""
+    h = 1.0 / 16
+    al = oracle.alpha(dim, 1.0, M * h)
+    A = oracle.dense_matrix(dim, n, h, M, al)
+    N = int(np.prod(n))
+    nu = oracle.surface_nu(dim, n, h, M).reshape(-1)
+    Nm = np.tile(nu, dim)
+    same = np.tile(np.eye(N, dtype=bool), (dim, dim))
+    Aoff = np.where(same, 0.0, A)
+    Asc = 0.5 * (Nm[:, None] * Aoff + Aoff * Nm[None, :])
+    for a in range(dim):
+        for b in range(dim):
+            blk = Asc[a * N:(a + 1) * N, b * N:(b + 1) * N]
+            Asc[a * N + np.arange(N), b * N + np.arange(N)] = -blk.sum(axis=1)
+    rng = np.random.default_rng(7)
+    u = rng.uniform(-1, 1, (dim,) + tuple(reversed(n)))
+    f = oracle.force(dim, n, h, M, al, u, nu=nu)
+    assert _rel(f.reshape(-1), Asc @ u.reshape(-1)) <= 1e-13
+    # symmetric, and the rigid motions still give zero force on every row
+    K = -Asc
+    assert np.abs(K - K.T).max() <= 1e-13 * np.abs(K).max()
+    assert np.abs(oracle.force(dim, n, h, M, al, np.ones_like(u), nu=nu)).max() <= 1e-12 * np.abs(K).max()
+
+
+def test_surface_corrected_row_abs_max_matches_dense():
+    """The ADR density with the correction: the largest absolute row sum of
+    K_sc over all rows, against the dense matrix; without it, the interior row."""
+    n, M, h = (12, 11), 3, 1.0 / 16
+    al = oracle.alpha(2, 1.0, M * h)
+    A = oracle.dense_matrix(2, n, h, M, al)
+    N = n[0] * n[1]
+    nu = oracle.surface_nu(2, n, h, M).reshape(-1)
+    Nm = np.tile(nu, 2)
+    same = np.tile(np.eye(N, dtype=bool), (2, 2))
+    Aoff = np.where(same, 0.0, A)
+    Asc = 0.5 * (Nm[:, None] * Aoff + Aoff * Nm[None, :])
+    for a in range(2):
+        for b in range(2):
+            blk = Asc[a * N:(a + 1) * N, b * N:(b + 1) * N]
+            Asc[a * N + np.arange(N), b * N + np.arange(N)] = -blk.sum(axis=1)
+    rs = np.abs(Asc).sum(axis=1)
+    got = oracle.row_abs_max(2, n, h, M, al, nu)
+    for a in range(2):
+        assert abs(got[a] - rs[a * N:(a + 1) * N].max()) <= 1e-12 * got[a]
+    plain = oracle.row_abs_max(2, n, h, M, al)
+    assert np.allclose(plain, 4 * oracle.adr_density(2, h, M, al), rtol=1e-12, atol=0)
+    assert np.all(got > plain)   # corrected edge rows are heavier than the interior row here
+
+
+def test_surface_corrected_adr_reaches_the_corrected_cg_solution():
+    """ADR with the correction (and its density) converges to the solution of
+    the corrected system that CG finds."""
+    n, M = (24, 20), 3
+    h = 1.0 / n[0]
+    al = oracle.alpha(2, 1.0, M * h)
+    cons = syn.clamp_left(2, n, M)
+    b = syn.traction_right(2, n, M, 1e-3)
+    nu = oracle.surface_nu(2, n, h, M)
+    u, it, rel = oracle.adr_solve(2, n, h, M, al, b, cons=cons, rtol=1e-10, maxit=200000, nu=nu)
+    x, _, _ = oracle.cg(2, n, h, M, al, b, cons=cons, rtol=1e-13, nu=nu)
+    x0, _, _ = oracle.cg(2, n, h, M, al, b, cons=cons, rtol=1e-13)
+    assert rel <= 1e-10
+    assert np.linalg.norm(u - x) / np.linalg.norm(x) <= 1e-7
+    assert np.linalg.norm(x - x0) / np.linalg.norm(x0) > 1e-3   # the correction changes the answer
