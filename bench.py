@@ -10,11 +10,12 @@ its own batch (weak scaling, no collective on the data path).
 Also reported in the same line: the roofline of the dominant kernel, the SM
 clocks seen during the timed region, an end-to-end figure with host buffers,
 the FP32/FP64 x stencil/FFT x delta = 3h/6h variants, the static CG solve
-(mixed precision vs FP64) to a relative residual of 1e-8, the 128^3 cube and
+(mixed precision vs FP64) to a relative residual of 1e-8, the paper's ADR
+solver on the same plate and for the step counts of its 2D runs, the 128^3 cube and
 the dynamic crack loop, and the CPU oracle timed on this host's cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
-  python bench.py --case fft2d|stencil2d_f64|stencil3d|fft3d|crack|cg [--steps K] [--warmup W]
+  python bench.py --case fft2d|stencil2d_f64|stencil3d|fft3d|crack|cg|adr [--steps K] [--warmup W]
 """
 from __future__ import annotations
 
@@ -375,7 +376,32 @@ def _extras(torch, pd, syn, dev):
     if cg["mixed"]["seconds"] > 0:
         cg["speedup_mixed_vs_f64"] = round(cg["f64"]["seconds"] / cg["mixed"]["seconds"], 3)
     out["cg_1024_rtol1e-8"] = cg
+    # the paper's static solver (ADR/CDEI, Algorithm 1, FP64) on the same plate and rtol
+    u = torch.zeros_like(b)
+    pd.pd_adr_solve(g.handle, b, u, 1e-8, 64, allow_not_converged=True)   # warm: workspace, graph
+    u.zero_()
+    torch.cuda.synchronize()
+    st = pd.pd_adr_solve(g.handle, b, u, 1e-8, 1_000_000, allow_not_converged=True)
+    out["adr_1024_rtol1e-8"] = {"seconds": round(st.seconds, 4), "iterations": st.iterations,
+                                "rel_residual": st.rel_residual,
+                                "us_per_iteration": round(st.seconds / max(1, st.iterations) * 1e6, 2)}
     g.close()
+    # ADR for the step counts of the paper's 2D static runs (plate meshes 400x200 .. 1600x800)
+    adr = {}
+    for nx, ny, steps in ((400, 200, 3000), (800, 400, 4000), (1600, 800, 5000)):
+        n = (nx, ny)
+        cons = syn.clamp_left(2, n, 3)
+        bb = torch.tensor(syn.traction_right(2, n, 3, 1e-3), device=dev)
+        g = pd.Grid(2, n, 1.0 / nx, 3, constrained=cons)
+        u = torch.zeros_like(bb)
+        pd.pd_adr_solve(g.handle, bb, u, 1e-30, 64, allow_not_converged=True)
+        u.zero_()
+        torch.cuda.synchronize()
+        st = pd.pd_adr_solve(g.handle, bb, u, 1e-30, steps, allow_not_converged=True)
+        adr[f"{nx}x{ny}"] = {"steps": st.iterations, "seconds": round(st.seconds, 4),
+                             "dof_steps_per_s": 2 * nx * ny * st.iterations / st.seconds}
+        g.close()
+    out["adr_plate_fixed_steps"] = adr
     # 64 uneven plates (sides 128..512, M in {3,4}): one batched solve vs one solve per plate
     plates = syn.batched_plates(64)
     grids = [pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained) for w in plates]
@@ -469,7 +495,7 @@ def _extras(torch, pd, syn, dev):
     return out
 
 
-CASES = ("fft2d", "stencil2d_f64", "stencil3d", "fft3d", "crack", "cg")
+CASES = ("fft2d", "stencil2d_f64", "stencil3d", "fft3d", "crack", "cg", "adr")
 
 
 def run_case(args):
@@ -478,7 +504,7 @@ def run_case(args):
     fft2d: K u, 1024^2 plate, M=3, FP32 FFT tiles, 8 fields.  stencil2d_f64: the same with the FP64
     stencil, 4 fields.  stencil3d / fft3d: K u on the 128^3 cube, M=3, FP32.  crack: one Verlet step
     with bond breaking on the pre-notched 512^2 plate.  cg: 64 iterations of the mixed CG on the
-    1024^2 plate (graph-replayed inner loop)."""
+    1024^2 plate (graph-replayed inner loop).  adr: 64 ADR iterations (Algorithm 1, FP64) on that plate."""
     import numpy as np
     import torch
     import paper_2301_11828_gb300 as pd
@@ -514,6 +540,16 @@ def run_case(args):
         u = torch.zeros((2,) + lay.shape, dtype=torch.float64, device=dev)
         v = vpt.clone()
         step, units = (lambda: g.step(u, v, None, nsteps=1, dt=2.99e-3, v_prescribed=vpt)), 2 * w.N
+    elif case == "adr":
+        w = syn.large_plate(3)
+        g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+        b = torch.tensor(w.b, device=dev)
+        u = torch.zeros_like(b)
+
+        def step():
+            u.zero_()
+            pd.pd_adr_solve(g.handle, b, u, 1e-30, 64, allow_not_converged=True)
+        units = 64
     elif case == "cg":
         w = syn.large_plate(3)
         g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)

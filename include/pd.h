@@ -61,6 +61,10 @@ typedef enum {
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
 #define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
 
+/* ---- modes for pd_set_surface_correction ---- */
+#define PD_SC_NONE   0    /* the paper's operator A = A^ + D^e + D^f (default) */
+#define PD_SC_VOLUME 1    /* bonds scaled by v_pq = (nu_p + nu_q)/2, nu_p = V_full / V_p */
+
 /* ---- modes for pd_cg_solve ---- */
 #define PD_CG_F64   0x1u  /* plain CG, FP64 vectors and FP64 matvec */
 #define PD_CG_MIXED 0x2u  /* FP32-matvec CG, FP64 solution, FP64 residual replacement every 10x drop */
@@ -113,6 +117,20 @@ int pd_create_grid(int dim, const int64_t n[3], double h, double delta,
 int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s0,
                     const double *E_field);
 
+/* Surface correction on incomplete horizons (the remark on Omega_e in Sec. 3.3,
+ * Eq. scr in Sec. 5.2): A_pq = v_pq A^_pq.  The paper takes v_pq from its
+ * reference; PD_SC_VOLUME is the volume method: V_p = sum of lambda over the
+ * in-grid part of the horizon of p, nu_p = V_full / V_p (1 on a full horizon),
+ * v_pq = (nu_p + nu_q) / 2, so K stays symmetric.  Every later use of the
+ * operator (pd_matvec, pd_cg_solve, pd_adr_solve, pd_step, the adjoints and the
+ * modulus gradient) includes it, as a direct correction over the nodes closer
+ * than 2M to a face added after the TBT/FFT product; the fused-dot and
+ * persistent CG paths step aside.  Builds a compacted node list (4 bytes per
+ * node of that band) and a table of (M+1)^(2 dim) doubles; PD_SC_NONE frees
+ * them.  Errors: PD_ERR_INVALID (unknown mode, 2^31 nodes or more),
+ * PD_ERR_CUDA.  A batch (pd_batch_create) refuses grids with the correction. */
+int pd_set_surface_correction(pd_grid *g, int mode);
+
 /* out = K u = -A u (or P K P u with PD_PROJECT), u and out DEVICE [dim][N] of
  * the dtype in flags; u and out must not overlap.  Broken bonds are honoured
  * unless PD_IGNORE_BROKEN.  Errors: PD_ERR_INVALID (dtype flag missing, FFT
@@ -143,7 +161,7 @@ int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, int max_ite
  * central-difference explicit integration of Algorithm 1 (Sec. 2.3), dt = 1,
  * on P K P u = P b.  The paper leaves the fictitious density D and the damping
  * c to its reference (Kilic and Madenci): D_i = 1/4 sum_j |K_ij| (Gershgorin,
- * interior row), c^n = 2 sqrt(u^T K1 u / u^T u) with the diagonal local
+ * interior row; with the surface correction, the largest row), c^n = 2 sqrt(u^T K1 u / u^T u) with the diagonal local
  * stiffness K1_ii = -(f_i^n - f_i^(n-1)) / (D_i v_i^(n-1/2)), 0 when not
  * positive.  FP64 throughout; any operator method of pd_matvec, broken bonds
  * included; constant modulus only (PD_ERR_INVALID with a modulus field).

@@ -32,6 +32,8 @@ PD_NO_TMA = 0x400
 PD_CG_F64 = 0x1
 PD_CG_MIXED = 0x2
 PD_CG_GRAPH = 0x10
+PD_SC_NONE = 0
+PD_SC_VOLUME = 1
 
 _STATUS = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM", 4: "PD_ERR_NOT_CONVERGED",
            5: "PD_ERR_TIMEOUT", 6: "PD_ERR_STATE"}
@@ -64,6 +66,7 @@ _VP, _I, _U32, _D, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes
 SIGNATURES = {
     "pd_create_grid": (_I, [_I, ctypes.POINTER(_I64), _D, _D, _VP, ctypes.POINTER(_VP)]),
     "pd_set_material": (_I, [_VP, _D, _D, _D, _D, _VP]),
+    "pd_set_surface_correction": (_I, [_VP, _I]),
     "pd_matvec": (_I, [_VP, _VP, _VP, _U32, _VP]),
     "pd_matvec_batch": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
     "pd_cg_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
@@ -155,6 +158,10 @@ def pd_set_material(g, E=1.0, rho=1.0, thickness=1.0, s0=0.0, E_field=None):
     import torch
     _check(load_library().pd_set_material(g, float(E), float(rho), float(thickness), float(s0),
                                           _dptr(E_field, torch.float64)))
+
+
+def pd_set_surface_correction(g, mode: int):
+    _check(load_library().pd_set_surface_correction(g, int(mode)))
 
 
 def pd_matvec(g, u, out, flags: int, stream=None):
@@ -310,10 +317,12 @@ class Grid:
     """Owns one pd_grid.  Vectors are torch CUDA tensors shaped [dim, (nz,) ny, nx]."""
 
     def __init__(self, dim: int, n: Sequence[int], h: float, M: int, constrained=None, E=1.0, rho=1.0,
-                 thickness=1.0, s0=0.0, E_field=None):
+                 thickness=1.0, s0=0.0, E_field=None, surface_correction: int = PD_SC_NONE):
         self.dim, self.n, self.h, self.M = dim, tuple(int(v) for v in n), float(h), int(M)
         self.handle = pd_create_grid(dim, self.n, h, M * h, constrained)
         self.set_material(E, rho, thickness, s0, E_field)
+        if surface_correction:
+            pd_set_surface_correction(self.handle, surface_correction)
         info = pd_get_info(self.handle)
         self.nnb, self.mask_words, self.alpha = info.nnb, info.mask_words, info.alpha
 
@@ -324,6 +333,10 @@ class Grid:
     @property
     def N(self):
         return int(np.prod(self.n))
+
+    def set_surface_correction(self, mode: int):
+        """PD_SC_VOLUME: scale the bonds of incomplete horizons (volume method); PD_SC_NONE: off."""
+        pd_set_surface_correction(self.handle, mode)
 
     def set_material(self, E=1.0, rho=1.0, thickness=1.0, s0=0.0, E_field=None):
         pd_set_material(self.handle, E, rho, thickness, s0, E_field)

@@ -8,7 +8,8 @@
 //     u^(n+1)   = u^n + v^(n+1/2)
 // The paper takes D and c from its reference [KM] (Kilic and Madenci):
 //   D_i = 1/4 sum_j |K_ij| (Gershgorin; the interior row, the largest, serves
-//   every node of a component), and c^n = 2 sqrt(u^T K1 u / u^T u) with the
+//   every node of a component; with the surface correction, the largest row
+//   over the whole grid), and c^n = 2 sqrt(u^T K1 u / u^T u) with the
 //   diagonal local stiffness K1_ii = -(f_i^n - f_i^(n-1)) / (D_i v_i^(n-1/2))
 //   (0 where v_i = 0), c^n = 0 when the quotient is not positive.
 // The iteration stops when |f^n + b| <= rtol |b| at u^n, before the update.
@@ -17,7 +18,11 @@
 // broken bonds), one reduction kernel (r.r, u^T K1 u, u^T u; its last block
 // forms c and the convergence flag) and one update kernel; chunks of 32
 // iterations replay as one CUDA graph and the host reads the flag between
-// chunks.  Everything is FP64, as in the oracle.
+// chunks.  The two force buffers swap roles every iteration (the product of
+// one iteration is the previous force of the next), so nothing is copied; a
+// chunk has an even number of iterations, so every replay starts on the same
+// buffer.  Everything is FP64, as in the oracle; the update multiplies by the
+// reciprocals of D and 2 + c instead of dividing element by element.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,7 +53,7 @@ struct AdrScal {
 struct AdrWs {
     size_t bytes = 0;
     void *base = nullptr;
-    double *q, *q_old, *v, *pb;   // P K P u^n, the previous one, velocity, P b
+    double *q[2], *v, *pb;        // P K P u at two consecutive iterates (alternating), velocity, P b
     AdrScal *sc;
     double *partial;              // [3][blocks]
     int blocks = 0;
@@ -102,10 +107,10 @@ k_adr_resid0(double *pb, const double *__restrict__ b, const double *__restrict_
     }
 }
 
-// First half step: v = (f^0 + b) / (2 D), u += v, q_old = q.
+// First half step: v = (f^0 + b) / (2 D), u += v.
 __global__ void __launch_bounds__(kBlk)
-k_adr_first(double *u, double *v, double *q_old, const double *__restrict__ q, const double *__restrict__ pb,
-            int64_t N, int dim, Dens D)
+k_adr_first(double *u, double *v, const double *__restrict__ q, const double *__restrict__ pb, int64_t N, int dim,
+            Dens D)
 {
     const int64_t L = (int64_t)dim * N;
     for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
@@ -113,7 +118,6 @@ k_adr_first(double *u, double *v, double *q_old, const double *__restrict__ q, c
         const double vi = (pb[i] - q[i]) / D.d[c] / 2.0;
         v[i] = vi;
         u[i] += vi;
-        q_old[i] = q[i];
     }
 }
 
@@ -166,10 +170,10 @@ k_adr_reduce(const double *__restrict__ u, const double *__restrict__ v, const d
     }
 }
 
-// v = ((2 - c) v + 2 (f + b) / D) / (2 + c), u += v, q_old = q.
+// v = ((2 - c) v + 2 (f + b) / D) / (2 + c), u += v.  invD: 1 / D per component.
 __global__ void __launch_bounds__(kBlk)
-k_adr_update(double *u, double *v, double *q_old, const double *__restrict__ q, const double *__restrict__ pb,
-             int64_t N, int dim, Dens D, AdrScal *sc)
+k_adr_update(double *u, double *v, const double *__restrict__ q, const double *__restrict__ pb, int64_t N, int dim,
+             Dens invD, AdrScal *sc)
 {
     __shared__ int s_done;
     __shared__ double s_c;
@@ -180,15 +184,13 @@ k_adr_update(double *u, double *v, double *q_old, const double *__restrict__ q, 
     }
     __syncthreads();
     if (s_done) return;
-    const double c = s_c;
+    const double c = s_c, a = 2.0 - c, e = 1.0 / (2.0 + c);
     const int64_t L = (int64_t)dim * N;
     for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
         const int cc = (int)(i / N);
-        const double qi = q[i];
-        const double vi = ((2.0 - c) * v[i] + 2.0 * (pb[i] - qi) / D.d[cc]) / (2.0 + c);
+        const double vi = (a * v[i] + 2.0 * (pb[i] - q[i]) * invD.d[cc]) * e;
         v[i] = vi;
         u[i] += vi;
-        q_old[i] = qi;
     }
 }
 
@@ -214,7 +216,7 @@ int ensure_ws(pd_grid *g, AdrWs *&w)
         PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         w->blocks = std::max(1, sms) * 4;
     }
-    const size_t need = sizeof(double) * (4 * (size_t)L + 3 * (size_t)w->blocks) + sizeof(AdrScal) + 1024;
+    const size_t need = sizeof(double) * (4 * (size_t)L + 3 * (size_t)w->blocks) + sizeof(AdrScal) + 2048;
     if (w->bytes >= need) return PD_OK;
     if (w->graph) {
         cudaGraphExecDestroy(w->graph);
@@ -227,8 +229,8 @@ int ensure_ws(pd_grid *g, AdrWs *&w)
     w->bytes = need;
     char *c = (char *)w->base;
     auto take = [&](size_t n) { char *p = c; c += (n + 255) & ~(size_t)255; return p; };
-    w->q = (double *)take(sizeof(double) * L);
-    w->q_old = (double *)take(sizeof(double) * L);
+    w->q[0] = (double *)take(sizeof(double) * L);
+    w->q[1] = (double *)take(sizeof(double) * L);
     w->v = (double *)take(sizeof(double) * L);
     w->pb = (double *)take(sizeof(double) * L);
     w->partial = (double *)take(sizeof(double) * 3 * w->blocks);
@@ -267,12 +269,21 @@ Dens density(const pd_grid *g)
     return D;
 }
 
-int adr_iteration(pd_grid *g, AdrWs *w, double *u, const Dens &D, cudaStream_t s)
+Dens recip(const Dens &D)
 {
-    int rc = matvec(g, 1, u, w->q, PD_F64 | PD_PROJECT | kInputProjected, s);
+    Dens r{};
+    for (int c = 0; c < 3; ++c) r.d[c] = D.d[c] != 0.0 ? 1.0 / D.d[c] : 0.0;
+    return r;
+}
+
+// One iteration on the force buffer `cur` (the other holds the previous force).
+int adr_iteration(pd_grid *g, AdrWs *w, double *u, const Dens &D, int cur, cudaStream_t s)
+{
+    double *q = w->q[cur], *q_old = w->q[cur ^ 1];
+    int rc = matvec(g, 1, u, q, PD_F64 | PD_PROJECT | kInputProjected, s);
     if (rc) return rc;
-    k_adr_reduce<<<w->blocks, kBlk, 0, s>>>(u, w->v, w->q, w->q_old, w->pb, g->N, g->dim, D, w->sc, w->partial);
-    k_adr_update<<<w->blocks, kBlk, 0, s>>>(u, w->v, w->q_old, w->q, w->pb, g->N, g->dim, D, w->sc);
+    k_adr_reduce<<<w->blocks, kBlk, 0, s>>>(u, w->v, q, q_old, w->pb, g->N, g->dim, D, w->sc, w->partial);
+    k_adr_update<<<w->blocks, kBlk, 0, s>>>(u, w->v, q, w->pb, g->N, g->dim, recip(D), w->sc);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -306,22 +317,29 @@ extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol,
     AdrWs *w = nullptr;
     int rc = ensure_ws(g, w);
     if (rc) return rc;
-    const Dens D = density(g);
+    Dens D = density(g);
+    if (g->sc) {   // corrected edge rows can outweigh the interior row: take the maximum over all rows
+        double rm[3];
+        rc = surface_row_abs_max(g, rm, s);
+        if (rc) return rc;
+        const bool interior = g->band_n < g->N;   // some row with a full, uncorrected horizon
+        for (int c = 0; c < g->dim; ++c) D.d[c] = std::max(0.25 * rm[c], interior ? D.d[c] : 0.0);
+    }
     const int blocks = w->blocks;
     if (g->has_cons) k_adr_zero_constrained<<<blocks, kBlk, 0, s>>>(u, g->d_cons, g->N, g->dim);
     // |P b|^2, and the residual at u^0
     volatile AdrScal *hs = (volatile AdrScal *)g->h_pinned;
-    PD_CUDA(cudaMemsetAsync(w->q, 0, sizeof(double) * (size_t)g->dim * g->N, s));
+    PD_CUDA(cudaMemsetAsync(w->q[0], 0, sizeof(double) * (size_t)g->dim * g->N, s));
     PD_CUDA(cudaMemsetAsync(w->sc, 0, sizeof(AdrScal), s));
-    k_adr_resid0<<<blocks, kBlk, 0, s>>>(w->pb, b, w->q, g->has_cons ? g->d_cons : nullptr, g->N, g->dim, w->sc,
+    k_adr_resid0<<<blocks, kBlk, 0, s>>>(w->pb, b, w->q[0], g->has_cons ? g->d_cons : nullptr, g->N, g->dim, w->sc,
                                          w->partial);
     PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(AdrScal), cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     const double bb = hs->rr;
     const double bn = bb > 0 ? std::sqrt(bb) : 1.0;
-    rc = matvec(g, 1, u, w->q, PD_F64 | PD_PROJECT | kInputProjected, s);
+    rc = matvec(g, 1, u, w->q[0], PD_F64 | PD_PROJECT | kInputProjected, s);
     if (rc) return rc;
-    k_adr_resid0<<<blocks, kBlk, 0, s>>>(w->pb, b, w->q, g->has_cons ? g->d_cons : nullptr, g->N, g->dim, w->sc,
+    k_adr_resid0<<<blocks, kBlk, 0, s>>>(w->pb, b, w->q[0], g->has_cons ? g->d_cons : nullptr, g->N, g->dim, w->sc,
                                          w->partial);
     PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(AdrScal), cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
@@ -331,16 +349,17 @@ extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol,
     if (rel <= rtol) {
         status = PD_OK;
     } else {
-        k_adr_first<<<blocks, kBlk, 0, s>>>(u, w->v, w->q_old, w->q, w->pb, g->N, g->dim, D);
+        k_adr_first<<<blocks, kBlk, 0, s>>>(u, w->v, w->q[0], w->pb, g->N, g->dim, D);
         AdrScal init{};
         init.tol2 = rtol * rtol * bb;
         init.iters = 1;
         *(AdrScal *)g->h_pinned = init;
         PD_CUDA(cudaMemcpyAsync(w->sc, g->h_pinned, sizeof(AdrScal), cudaMemcpyHostToDevice, s));
         // one plain iteration (kernel attributes outside any capture), then graph chunks
+        // the force of u^0 sits in q[0]; iteration k writes q[k & 1]
         int issued = 0;
         if (max_iter > 1) {
-            rc = adr_iteration(g, w, u, D, s);
+            rc = adr_iteration(g, w, u, D, 1, s);
             if (rc) return rc;
             ++issued;
         }
@@ -352,7 +371,7 @@ extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol,
             cudaGraph_t graph = nullptr;
             bool ok = cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                for (int i = 0; i < kChunk && ok; ++i) ok = (adr_iteration(g, w, u, D, w->cap) == PD_OK);
+                for (int i = 0; i < kChunk && ok; ++i) ok = (adr_iteration(g, w, u, D, i & 1, w->cap) == PD_OK);
                 ok = (cudaStreamEndCapture(w->cap, &graph) == cudaSuccess) && ok;
             }
             if (ok && cudaGraphInstantiate(&w->graph, graph, 0) != cudaSuccess) w->graph = nullptr;
@@ -369,7 +388,7 @@ extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol,
                 PD_CUDA(cudaGraphLaunch(w->graph, s));
             } else {
                 for (int i = 0; i < n; ++i) {
-                    rc = adr_iteration(g, w, u, D, s);
+                    rc = adr_iteration(g, w, u, D, i & 1, s);
                     if (rc) return rc;
                 }
             }

@@ -33,7 +33,7 @@ int fail(int code, const std::string &msg)
 // lambda of Eq. fac:e1 for an offset with |o|^2 = d2 (grid units, delta = M):
 // 1 when |o| <= M - 1/2 (tested exactly as 4 d2 <= (2M - 1)^2), M + 1/2 - |o| on
 // the shell M - 1/2 < |o| <= M.
-static double lambda_of(int d2, int M)
+double lambda_of(int d2, int M)
 {
     if (4 * d2 <= (2 * M - 1) * (2 * M - 1)) return 1.0;
     return (double)M + 0.5 - std::sqrt((double)d2);
@@ -130,6 +130,8 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_brk_thr);
     cudaFree(g->d_coef);
     cudaFree(g->d_coef1);
+    cudaFree(g->d_nu_tab);
+    cudaFree(g->d_band);
     cudaFree(g->ws);
     cg_release(g);
     adr_release(g);
@@ -187,6 +189,7 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
     a.no_tma = (flags & PD_NO_TMA) != 0;
     a.scale = scale;
 
+    if (dot_partial && g->sc) return fail(PD_ERR_INVALID, "internal: fused dot with the surface correction");
     if (g->has_E) {
         if (g->dim != 2) return fail(PD_ERR_INVALID, "a per-node modulus field is supported in 2D");
         if (method == PD_METHOD_FFT)
@@ -196,7 +199,9 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
         a.dot_partial = dot_partial;
         a.dot_out = dot_out;
         a.retire = retire;
-        return launch_stencil(g, f64, a, s);
+        int rc = launch_stencil(g, f64, a, s);
+        if (rc != PD_OK) return rc;
+        return launch_sc_gather(g, f64, u, out, batch, a.project, need_mu, scale, s);
     }
     bool use_fft = (method == PD_METHOD_FFT);
     if (method == 0) use_fft = (g->auto_choice[f64 ? 1 : 0] == 2);
@@ -206,8 +211,11 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
     a.retire = retire;
     int rc = use_fft ? launch_fft_tile(g, f64, a, s) : launch_stencil(g, f64, a, s);
     if (rc != PD_OK) return rc;
-    if (need_mu) return launch_df_gather(g, f64, u, out, batch, a.project, scale, s);
-    return PD_OK;
+    if (need_mu) {
+        rc = launch_df_gather(g, f64, u, out, batch, a.project, scale, s);
+        if (rc != PD_OK) return rc;
+    }
+    return launch_sc_gather(g, f64, u, out, batch, a.project, need_mu, scale, s);
 }
 
 }  // namespace pd

@@ -452,9 +452,9 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
     int64_t off = 0;
     for (int i = 0; i < count; ++i) {
         pd_grid *g = grids[bt->order[i]];
-        if (!g || g->dim != 2 || g->M > kMaxBM || g->has_E) {
+        if (!g || g->dim != 2 || g->M > kMaxBM || g->has_E || g->sc) {
             delete bt;
-            return fail(PD_ERR_INVALID, "batch plates must be 2D, horizon M <= 4, without a modulus field");
+            return fail(PD_ERR_INVALID, "batch plates must be 2D, horizon M <= 4, without a modulus field or surface correction");
         }
         bt->grids.push_back(g);
         PlateDesc d{};

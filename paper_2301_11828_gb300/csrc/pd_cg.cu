@@ -477,7 +477,7 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s, bool f
         PD_CUDA(cudaGetLastError());
         return PD_OK;
     }
-    const bool fuse = !(g->broken_total > 0 && !g->has_E);
+    const bool fuse = !(g->broken_total > 0 && !g->has_E) && !g->sc;
     const uint32_t fl = (f64 ? PD_F64 : PD_F32) | PD_PROJECT | kInputProjected;
     void *p = f64 ? (void *)w->p64 : (void *)w->p32;
     void *q = f64 ? (void *)w->q64 : (void *)w->q32;

@@ -484,7 +484,7 @@ int cg_persist_ctas(const pd_grid *g)
 
 bool cg_persist_eligible(const pd_grid *g)
 {
-    if (g->dim != 2 || g->has_E || g->broken_total > 0 || g->no_tma) return false;
+    if (g->dim != 2 || g->has_E || g->broken_total > 0 || g->no_tma || g->sc) return false;
     if (g->auto_choice[0] == 2) return false;   // the FFT method was chosen for FP32
     if (g->M < 1 || g->M > 8 || g->n[0] % 4 != 0) return false;
     if (encode_fn() == nullptr) return false;
@@ -497,7 +497,7 @@ bool cg_persist_eligible(const pd_grid *g)
 
 bool cg_dirmv_eligible(const pd_grid *g)
 {
-    if (g->dim != 2 || g->has_E || g->broken_total > 0 || g->no_tma) return false;
+    if (g->dim != 2 || g->has_E || g->broken_total > 0 || g->no_tma || g->sc) return false;
     if (g->auto_choice[0] == 2) return false;   // the FFT method was chosen for FP32
     if (g->M < 1 || g->M > 8 || g->n[0] % 4 != 0) return false;
     return encode_fn() != nullptr && resident_ctas(g->M) > 0;

@@ -276,11 +276,13 @@ template <int DIM>
 __global__ void __launch_bounds__(kBlk)
 k_grad_modulus(const double *__restrict__ u, const double *__restrict__ lam, int64_t N, int nx, int ny, int nz,
                int nnb, const int32_t *__restrict__ off, const double *__restrict__ coef1,
-               const uint32_t *__restrict__ mask, double scale, double *grad)
+               const uint32_t *__restrict__ mask, const double *__restrict__ nu_tab, int M, double scale,
+               double *grad)
 {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
         node_coords(p, nx, ny, i, j, k);
+        const double nu_p = nu_tab ? nu_tab[nu_class(i, j, k, nx, ny, nz, M, DIM)] : 1.0;
         double acc = 0.0;
         for (int kk = 0; kk < nnb; ++kk) {
             const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1], qk = k + off[3 * kk + 2];
@@ -293,15 +295,18 @@ k_grad_modulus(const double *__restrict__ u, const double *__restrict__ lam, int
                 du[c] = u[c * N + q] - u[c * N + p];
                 dl[c] = lam[c * N + q] - lam[c * N + p];
             }
+            double t;
             if (DIM == 2) {
                 const double *cf = coef1 + 3 * kk;
-                acc += dl[0] * (cf[0] * du[0] + cf[1] * du[1]) + dl[1] * (cf[1] * du[0] + cf[2] * du[DIM - 1]);
+                t = dl[0] * (cf[0] * du[0] + cf[1] * du[1]) + dl[1] * (cf[1] * du[0] + cf[2] * du[DIM - 1]);
             } else {
                 const double *cf = coef1 + 6 * kk;
-                acc += dl[0] * (cf[0] * du[0] + cf[1] * du[1] + cf[2] * du[DIM - 1]) +
-                       dl[1] * (cf[1] * du[0] + cf[3] * du[1] + cf[4] * du[DIM - 1]) +
-                       dl[DIM - 1] * (cf[2] * du[0] + cf[4] * du[1] + cf[5] * du[DIM - 1]);
+                t = dl[0] * (cf[0] * du[0] + cf[1] * du[1] + cf[2] * du[DIM - 1]) +
+                    dl[1] * (cf[1] * du[0] + cf[3] * du[1] + cf[4] * du[DIM - 1]) +
+                    dl[DIM - 1] * (cf[2] * du[0] + cf[4] * du[1] + cf[5] * du[DIM - 1]);
             }
+            // surface correction: the bond carries (nu_p + nu_q) / 2
+            acc += nu_tab ? 0.5 * (nu_p + nu_tab[nu_class(qi, qj, qk, nx, ny, nz, M, DIM)]) * t : t;
         }
         grad[p] += scale * acc;
     }
@@ -425,10 +430,12 @@ int launch_grad_modulus(pd_grid *g, const double *u, const double *lam, double s
     const int nx = (int)g->n[0], ny = (int)g->n[1], nz = (int)g->n[2];
     if (g->dim == 2)
         k_grad_modulus<2><<<grid_blocks(g->N), kBlk, 0, s>>>(u, lam, g->N, nx, ny, nz, g->nnb, g->d_off, g->d_coef1,
-                                                              g->d_mask, scale, grad);
+                                                              g->d_mask, g->sc ? g->d_nu_tab : nullptr, g->M,
+                                                              scale, grad);
     else
         k_grad_modulus<3><<<grid_blocks(g->N), kBlk, 0, s>>>(u, lam, g->N, nx, ny, nz, g->nnb, g->d_off, g->d_coef1,
-                                                              g->d_mask, scale, grad);
+                                                              g->d_mask, g->sc ? g->d_nu_tab : nullptr, g->M,
+                                                              scale, grad);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }

@@ -121,6 +121,13 @@ struct pd_grid {
     void *cg = nullptr;        // CG workspace and captured graphs (pd_cg.cu)
     void *adr = nullptr;       // ADR workspace and captured graph (pd_adr.cu)
     bool no_tma = false;       // use the plain FP32 stencil instead of the TMA-fed one
+    // surface correction (pd_surface.cu): mode, nu per class of clipped face distances,
+    // the band of nodes within 2M of a face, three words of scratch
+    int sc = 0;
+    double *d_nu_tab = nullptr;
+    int32_t *d_band = nullptr;
+    int64_t band_n = 0;
+    unsigned long long *d_sc_rowmax = nullptr;
     int64_t op_stamp = 0;      // bumped whenever the operator changes (material, bond state)
 };
 
@@ -170,6 +177,27 @@ constexpr uint32_t kForceMu = 0x80000000u;
 // Internal flag: the input already satisfies P u = u (the CG keeps its vectors projected).
 constexpr uint32_t kInputProjected = 0x40000000u;
 int upload_coefs(pd_grid *g);
+double lambda_of(int d2, int M);   // Eq. fac:e1 in grid units
+
+// ------------------------------------------------------------------ surface correction (pd_surface.cu)
+// Class of a node for the surface-correction table: its distances to the low and
+// high face along each axis, clipped at M (mixed radix M + 1).
+__device__ __forceinline__ int nu_class(int i, int j, int k, int nx, int ny, int nz, int M, int dim)
+{
+    int c = min(i, M);
+    c = c * (M + 1) + min(nx - 1 - i, M);
+    c = c * (M + 1) + min(j, M);
+    c = c * (M + 1) + min(ny - 1 - j, M);
+    if (dim == 3) {
+        c = c * (M + 1) + min(k, M);
+        c = c * (M + 1) + min(nz - 1 - k, M);
+    }
+    return c;
+}
+int surface_set(pd_grid *g, int mode);
+int launch_sc_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t batch, bool project, bool use_mu,
+                     double scale, cudaStream_t s);
+int surface_row_abs_max(pd_grid *g, double out[3], cudaStream_t s);   // band rows only; synchronises s
 void cg_release(pd_grid *g);
 void adr_release(pd_grid *g);
 int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, cudaStream_t s,
