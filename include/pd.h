@@ -234,7 +234,10 @@ int pd_break_bonds(pd_grid *g, const void *u, uint32_t flags, int64_t *n_newly_b
 
 /* Breaks every bond whose segment x_p -> x_q meets the closed segment
  * (seg[0], seg[1]) - (seg[2], seg[3]) / den, in units of h from the grid
- * corner (2D only; the pre-notch of Sec. 5.2).  Exact integer geometry. */
+ * corner (the pre-notch of Sec. 5.2).  In 3D the segment is extruded through
+ * the whole thickness (the through-thickness notches of Sec. 5.4): a bond is
+ * cut when its projection onto the x-y plane meets the segment.  Exact integer
+ * geometry. */
 int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_broken,
                      void *stream);
 

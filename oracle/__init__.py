@@ -73,7 +73,7 @@ def lib():
             L.or_cg.restype = ctypes.c_int
             L.or_break.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
             L.or_break.restype = ctypes.c_int64
-            L.or_prenotch.argtypes = [i64p, ctypes.c_int, i64p, ctypes.c_int64, dp]
+            L.or_prenotch.argtypes = [ctypes.c_int, i64p, ctypes.c_int, i64p, ctypes.c_int64, dp]
             L.or_prenotch.restype = ctypes.c_int64
             L.or_vv.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp,
                                 dp, dp, ctypes.c_double, dp, dp, dp, ctypes.c_double, ctypes.c_double,
@@ -264,11 +264,12 @@ def break_bonds(dim, n, h, M, s0, u, mu) -> int:
     return int(lib().or_break(dim, _n64(n), h, M, s0, _ptr(_f64(u)), _ptr(mu)))
 
 
-def prenotch(n, M, seg, den, mu) -> int:
-    """Break the bonds meeting the closed segment seg/den (units of h from the corner)."""
+def prenotch(n, M, seg, den, mu, dim=2) -> int:
+    """Break the bonds meeting the closed segment seg/den (units of h from the corner);
+    in 3D the segment is extruded through z and bonds are tested by their x-y projection."""
     assert mu.dtype == np.uint8 and mu.flags.c_contiguous
     s = (ctypes.c_int64 * 4)(*[int(v) for v in seg])
-    return int(lib().or_prenotch(_n64(n), M, s, int(den), _ptr(mu)))
+    return int(lib().or_prenotch(dim, _n64(n), M, s, int(den), _ptr(mu)))
 
 
 def vv(dim, n, h, M, alpha_, u, v, nsteps, dt, rho=1.0, b=None, E=None, mu=None, s0=0.0,

@@ -298,22 +298,26 @@ static int seg_meet(const int64_t *p1, const int64_t *p2, const int64_t *q1, con
     return 0;
 }
 
-/* 2D only.  seg = (x0, y0, x1, y1) numerators over den, in units of h from the
- * grid corner (node i, j sits at (i + 1/2, j + 1/2)).  Breaks every bond that
- * meets the segment; returns the number of bonds broken. */
-int64_t or_prenotch(const int64_t *n, int M, const int64_t *seg, int64_t den, uint8_t *mu)
+/* seg = (x0, y0, x1, y1) numerators over den, in units of h from the grid
+ * corner (node i, j sits at (i + 1/2, j + 1/2)).  Breaks every bond that
+ * meets the closed segment; returns the number of bonds broken.  In 3D the
+ * segment is extruded through the whole thickness (a planar notch normal to
+ * the x-y plane): a bond is cut when its projection onto the x-y plane meets
+ * the segment, whatever its z extent (a bond along z alone projects to a
+ * point, cut only if that point lies on the segment). */
+int64_t or_prenotch(int dim, const int64_t *n, int M, const int64_t *seg, int64_t den, uint8_t *mu)
 {
     int32_t off[3 * 16384];
-    int nnb = or_offsets(2, M, off, 16384);
-    const int64_t nx = n[0], ny = n[1], N = nx * ny;
+    int nnb = or_offsets(dim, M, off, 16384);
+    const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1, N = nx * ny * nz;
     int64_t A[2] = {2 * seg[0], 2 * seg[1]}, B[2] = {2 * seg[2], 2 * seg[3]};
     int64_t broken = 0;
     for (int64_t p = 0; p < N; ++p) {
-        int64_t i = p % nx, j = p / nx;
+        int64_t i = p % nx, j = (p / nx) % ny, kz = p / (nx * ny);
         for (int k = 0; k < nnb; ++k) {
-            int64_t qi = i + off[3 * k], qj = j + off[3 * k + 1];
-            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny) continue;
-            int64_t q = qi + nx * qj;
+            int64_t qi = i + off[3 * k], qj = j + off[3 * k + 1], qk = kz + off[3 * k + 2];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
+            int64_t q = qi + nx * (qj + ny * qk);
             if (q <= p) continue;
             int64_t P1[2] = {den * (2 * i + 1), den * (2 * j + 1)};
             int64_t P2[2] = {den * (2 * qi + 1), den * (2 * qj + 1)};

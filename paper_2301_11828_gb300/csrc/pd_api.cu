@@ -520,7 +520,6 @@ int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_b
 {
     int rc = check_grid(g);
     if (rc) return rc;
-    if (g->dim != 2) return fail(PD_ERR_INVALID, "segments are supported in 2D");
     if (!seg || den < 1) return fail(PD_ERR_INVALID, "bad segment");
     const int64_t lim = (int64_t)1 << 28;
     for (int i = 0; i < 4; ++i)

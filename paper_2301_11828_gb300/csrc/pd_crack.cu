@@ -9,7 +9,8 @@
 //     with a larger index (offsets of the upper half of the canonical list), in
 //     FP64 with explicitly rounded operations (no contraction), and clears the
 //     bit at both ends.  Broken bonds never heal.
-//   * Pre-notch: bonds whose segment meets a given segment, exact integers.
+//   * Pre-notch: bonds whose segment meets a given segment, exact integers (in
+//     3D the segment is extruded through z: bonds are tested by their x-y projection).
 //   * Velocity-Verlet (Algorithm 2) with a = (f + b) / rho.
 //   * Modulus gradient: bond sum of (lam_q - lam_r)^T C1 (u_q - u_r).
 #include <cuda_runtime.h>
@@ -208,17 +209,18 @@ __device__ __forceinline__ bool within(int64_t ax, int64_t ay, int64_t bx, int64
 }
 
 __global__ void __launch_bounds__(kBlk)
-k_segment(int64_t N, int nx, int ny, int nnb, const int32_t *__restrict__ off, uint32_t *mask, int64_t ax,
+k_segment(int64_t N, int nx, int ny, int nz, int nnb, const int32_t *__restrict__ off, uint32_t *mask, int64_t ax,
           int64_t ay, int64_t bx, int64_t by, int64_t den, uint32_t *brflag, int32_t *brlist,
           unsigned long long *count)
 {
     unsigned long long newly = 0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(p % nx), j = (int)(p / nx);
+        int i, j, k;
+        node_coords(p, nx, ny, i, j, k);
         const int64_t px = den * (2 * i + 1), py = den * (2 * j + 1);
-        for (int kk = nnb / 2; kk < nnb; ++kk) {
-            const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1];
-            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny) continue;
+        for (int kk = nnb / 2; kk < nnb; ++kk) {   // upper half: q > p
+            const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1], qk = k + off[3 * kk + 2];
+            if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
             const int64_t qx = den * (2 * qi + 1), qy = den * (2 * qj + 1);
             const int d1 = orient(ax, ay, bx, by, px, py), d2 = orient(ax, ay, bx, by, qx, qy);
             const int d3 = orient(px, py, qx, qy, ax, ay), d4 = orient(px, py, qx, qy, bx, by);
@@ -226,7 +228,7 @@ k_segment(int64_t N, int nx, int ny, int nnb, const int32_t *__restrict__ off, u
                         (d2 == 0 && within(ax, ay, bx, by, qx, qy)) || (d3 == 0 && within(px, py, qx, qy, ax, ay)) ||
                         (d4 == 0 && within(px, py, qx, qy, bx, by));
             if (!meet) continue;
-            const int64_t q = (int64_t)qj * nx + qi;
+            const int64_t q = ((int64_t)qk * ny + qj) * nx + qi;
             uint32_t *wp = mask + (int64_t)(kk >> 5) * N + p;
             const uint32_t bit = 1u << (kk & 31);
             if (*wp & bit) {
@@ -404,7 +406,8 @@ int launch_break(pd_grid *g, const void *u, bool f64, int32_t *break_step, int32
 
 int launch_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, cudaStream_t s)
 {
-    k_segment<<<grid_blocks(g->N), kBlk, 0, s>>>(g->N, (int)g->n[0], (int)g->n[1], g->nnb, g->d_off, g->d_mask,
+    k_segment<<<grid_blocks(g->N), kBlk, 0, s>>>(g->N, (int)g->n[0], (int)g->n[1], (int)g->n[2], g->nnb, g->d_off,
+                                                  g->d_mask,
                                                   2 * seg[0], 2 * seg[1], 2 * seg[2], 2 * seg[3], den, g->d_brflag,
                                                   g->d_brlist, g->d_count);
     PD_CUDA(cudaGetLastError());

@@ -3,7 +3,7 @@
 This module holds no arithmetic of the peridynamic method: it only draws random
 fields (numpy PCG64, fixed seeds) and builds the problem geometry (which nodes
 are clamped, where the load acts, where the pre-notch lies) for the workloads
-modelled on the paper's examples (Sec. 5.1-5.3).
+modelled on the paper's examples (Sec. 5.1-5.4).
 
 Layout of every per-node array: ``[dim][Nz][Ny][Nx]`` (2D: ``[dim][Ny][Nx]``),
 x fastest, which is the node numbering p = i + Nx*(j + Ny*k) of Sec. 3 and
@@ -153,6 +153,45 @@ def crack_plate(nside: int = 512, M: int = 3, tag: int = 4) -> Workload:
         s0=1e-3, rho=1.0,
         extra=dict(E_field=lognormal_modulus(n, 0.1, tag), notch=notch, notch_den=den,
                    vel_layers=velocity_layers_2d(n, M), v0=1e-3))
+
+
+def kw_block(nx: int = 201, ny: int = 101, nz: int = 9, M: int = 3, v0: float = 0.00634) -> Workload:
+    """Kalthoff-Winkler-like block (the geometry of Sec. 5.4, without the impactor).
+
+    Length along x, width along y, thickness along z (the paper's 0.2 x 0.1 x
+    0.009 block is 201 x 101 x 9 nodes, and 402 x 202 x 18 at half the
+    spacing); h = 1/nx, E = rho = 1, critical stretch s0 = 0.01 as in the paper.
+    Two through-thickness notches at x = 3/8 and 5/8 of the length run from the
+    y = 0 face to half the width (length a0 = W/2, distance d = L/4, as in the
+    paper); they are given in ``extra['notches']`` as segments over
+    ``extra['notch_den']`` in units of h from the grid corner.  Instead of the
+    impactor, the first M node layers of the y = 0 face between the notches
+    (node centres strictly between them) move with the prescribed velocity
+    v_y = v0: ``constrained`` marks their y component and ``extra['v_prescribed']``
+    holds the velocity field.  Time step and impact speed are the paper's in
+    units of the spacing and of the bar wave speed c0 = sqrt(E / rho) (its
+    steel: E = 2e11 Pa, rho = 7850 kg/m^3, c0 = 5048 m/s, spacing 0.001 m):
+    dt = 1.3367e-8 s -> 0.06747 h / c0 and v0 = 32 m/s -> 0.00634 c0, so the
+    paper's 1350 steps cover the same 0.46 wave transits of the length.  That
+    step is far below the stable one, 2 h sqrt(rho / (E Lambda_1)) with
+    Lambda_1 <= 1.2185 the largest eigenvalue of the unit (h = 1) symbol
+    (``extra['dt_stable']``).
+    """
+    n = (nx, ny, nz)
+    den = 8
+    notches = [(3 * nx, 0, 3 * nx, 4 * ny), (5 * nx, 0, 5 * nx, 4 * ny)]
+    i = np.arange(nx)
+    zone = (den * (2 * i + 1) > 2 * 3 * nx) & (den * (2 * i + 1) < 2 * 5 * nx)   # 3nx/8 < i + 1/2 < 5nx/8
+    cons = np.zeros((3,) + node_shape(n), dtype=np.uint8)
+    vp = np.zeros((3,) + node_shape(n))
+    for j in range(min(M, ny)):
+        cons[1, :, j, zone] = 1
+        vp[1, :, j, zone] = v0
+    h = 1.0 / nx
+    return Workload(name=f"kw3d_{nx}x{ny}x{nz}_M{M}", dim=3, n=n, M=M, h=h, s0=0.01, rho=1.0,
+                    constrained=cons,
+                    extra=dict(notches=notches, notch_den=den, v_prescribed=vp, v0=v0, dt=0.06747 * h,
+                               dt_stable=2.0 * h / np.sqrt(1.2185)))
 
 
 def batched_plates(count: int = 64, tag: int = 5):

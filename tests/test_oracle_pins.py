@@ -612,3 +612,64 @@ def test_surface_corrected_adr_reaches_the_corrected_cg_solution():
     assert rel <= 1e-10
     assert np.linalg.norm(u - x) / np.linalg.norm(x) <= 1e-7
     assert np.linalg.norm(x - x0) / np.linalg.norm(x0) > 1e-3   # the correction changes the answer
+
+
+# --------------------------------------------------------------------------- 3D through-thickness notch
+
+def _vertical_notch_cuts(P1, P2, xn, y0, y1):
+    """Closed vertical segment x = xn, y0 <= y <= y1 against the closed segment P1-P2 (Fractions)."""
+    (x1, ya), (x2, yb) = P1, P2
+    if not (min(x1, x2) <= xn <= max(x1, x2)):
+        return False
+    if x1 == x2:   # the bond is vertical too (or a point): overlap of the y ranges on the line x = xn
+        return max(min(ya, yb), y0) <= min(max(ya, yb), y1)
+    y = ya + (xn - x1) * (yb - ya) / (x2 - x1)
+    return y0 <= y <= y1
+
+
+@pytest.mark.parametrize("n,M,seg", [((12, 10, 4), 2, (20, 0, 20, 20)), ((9, 8, 3), 3, (14, 6, 14, 30)),
+                                     ((10, 7, 1), 2, (18, 4, 18, 17))])
+def test_prenotch_3d_is_the_extruded_2d_notch(n, M, seg):
+    """Every bond whose x-y projection meets the vertical notch is cut, counted by
+    brute force over node pairs with a parametric intersection in exact
+    fractions (a route of its own).  With one layer the 3D set equals the 2D
+    set.  Catches a z coordinate leaking into the test, a missed z-bond family
+    and an asymmetric cut."""
+    den = 4
+    mu = oracle.intact_mu(3, n, M)
+    got = oracle.prenotch(n, M, seg, den, mu, dim=3)
+    xn, y0, y1 = Fraction(seg[0], den), Fraction(seg[1], den), Fraction(seg[3], den)
+    offs = oracle.offsets(3, M)
+    nx, ny, nz = n
+    expect = 0
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                p = i + nx * (j + ny * k)
+                for kk, (ox, oy, oz) in enumerate(offs):
+                    qi, qj, qk = i + ox, j + oy, k + oz
+                    if not (0 <= qi < nx and 0 <= qj < ny and 0 <= qk < nz):
+                        continue
+                    q = qi + nx * (qj + ny * qk)
+                    cut = _vertical_notch_cuts((Fraction(2 * i + 1, 2), Fraction(2 * j + 1, 2)),
+                                               (Fraction(2 * qi + 1, 2), Fraction(2 * qj + 1, 2)), xn, y0, y1)
+                    assert mu[p, kk] == (0 if cut else 1)
+                    if cut and q > p:
+                        expect += 1
+    assert got == expect and got > 0
+    if nz == 1:
+        mu2 = oracle.intact_mu(2, n[:2], M)
+        assert oracle.prenotch(n[:2], M, seg, den, mu2) == got
+
+
+def test_kw_block_step_is_below_the_stable_step():
+    """The stable step stored with the 3D block, 2 h / sqrt(Lambda_1) with
+    Lambda_1 = 1.2185, is a lower bound: Lambda_1 >= the largest eigenvalue of
+    the unit symbol on the block's doubled grid; the run's step is below it."""
+    w = syn.kw_block()
+    L = tuple(2 * v for v in w.n)
+    G = oracle.symbol(3, L, 1.0, w.M, oracle.alpha(3, 1.0, w.M * 1.0)).real
+    lam = np.linalg.eigvalsh(-np.moveaxis(G.reshape(3, 3, -1), 2, 0)).max()
+    assert 1.2 < lam <= 1.2185
+    assert w.extra["dt_stable"] <= 2.0 * w.h / np.sqrt(lam)
+    assert w.extra["dt"] < 0.1 * w.extra["dt_stable"]
