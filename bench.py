@@ -377,15 +377,20 @@ def _extras(torch, pd, syn, dev):
     if cg["mixed"]["seconds"] > 0:
         cg["speedup_mixed_vs_f64"] = round(cg["f64"]["seconds"] / cg["mixed"]["seconds"], 3)
     out["cg_1024_rtol1e-8"] = cg
-    # the paper's static solver (ADR/CDEI, Algorithm 1, FP64) on the same plate and rtol
-    u = torch.zeros_like(b)
-    pd.pd_adr_solve(g.handle, b, u, 1e-8, 64, allow_not_converged=True)   # warm: workspace, graph
-    u.zero_()
-    torch.cuda.synchronize()
-    st = pd.pd_adr_solve(g.handle, b, u, 1e-8, 1_000_000, allow_not_converged=True)
-    out["adr_1024_rtol1e-8"] = {"seconds": round(st.seconds, 4), "iterations": st.iterations,
-                                "rel_residual": st.rel_residual,
-                                "us_per_iteration": round(st.seconds / max(1, st.iterations) * 1e6, 2)}
+    # the paper's static solver (ADR/CDEI, Algorithm 1) on the same plate and rtol: FP64, and FP32
+    # operator with FP64 refresh
+    adr1024 = {}
+    for mode, name in ((pd.PD_ADR_F64, "f64"), (pd.PD_ADR_MIXED, "mixed")):
+        u = torch.zeros_like(b)
+        pd.pd_adr_solve(g.handle, b, u, 1e-8, 64, allow_not_converged=True, mode=mode)   # warm: workspace, graph
+        u.zero_()
+        torch.cuda.synchronize()
+        st = pd.pd_adr_solve(g.handle, b, u, 1e-8, 1_000_000, allow_not_converged=True, mode=mode)
+        adr1024[name] = {"seconds": round(st.seconds, 4), "iterations": st.iterations, "outer": st.outer,
+                         "rel_residual": st.rel_residual,
+                         "us_per_iteration": round(st.seconds / max(1, st.iterations) * 1e6, 2)}
+    adr1024["speedup_mixed_vs_f64"] = round(adr1024["f64"]["seconds"] / adr1024["mixed"]["seconds"], 3)
+    out["adr_1024_rtol1e-8"] = adr1024
     g.close()
     # ADR for the step counts of the paper's 2D static runs (plate meshes 400x200 .. 1600x800)
     adr = {}
@@ -399,8 +404,14 @@ def _extras(torch, pd, syn, dev):
         u.zero_()
         torch.cuda.synchronize()
         st = pd.pd_adr_solve(g.handle, bb, u, 1e-30, steps, allow_not_converged=True)
+        u.zero_()
+        pd.pd_adr_solve(g.handle, bb, u, 1e-30, 64, allow_not_converged=True, mode=pd.PD_ADR_MIXED)
+        u.zero_()
+        torch.cuda.synchronize()
+        stm = pd.pd_adr_solve(g.handle, bb, u, 1e-30, steps, allow_not_converged=True, mode=pd.PD_ADR_MIXED)
         adr[f"{nx}x{ny}"] = {"steps": st.iterations, "seconds": round(st.seconds, 4),
-                             "dof_steps_per_s": 2 * nx * ny * st.iterations / st.seconds}
+                             "dof_steps_per_s": 2 * nx * ny * st.iterations / st.seconds,
+                             "mixed_seconds": round(stm.seconds, 4)}
         g.close()
     out["adr_plate_fixed_steps"] = adr
     # surface correction (volume method): its cost on the timed FP32 product, and ADR with it

@@ -60,10 +60,18 @@ typedef enum {
 #define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
 #define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
+#define PD_ACCURATE       0x800u /* FP32 TMA-fed 2D stencil: sum c(o) ((u_p+o - u_p) + (u_p-o - u_p)) instead of
+                                    c(o) (u_p+o + u_p-o) against Kd u_p, so that the FP32 error is relative to
+                                    |K u| for smooth fields too (about 25% more arithmetic); the solvers' FP32
+                                    products use it.  Other kernels ignore the flag */
 
 /* ---- modes for pd_set_surface_correction ---- */
 #define PD_SC_NONE   0    /* the paper's operator A = A^ + D^e + D^f (default) */
 #define PD_SC_VOLUME 1    /* bonds scaled by v_pq = (nu_p + nu_q)/2, nu_p = V_full / V_p */
+
+/* ---- modes for pd_adr_solve ---- */
+#define PD_ADR_F64   0x1u  /* Algorithm 1 in FP64 throughout (the paper's solver) */
+#define PD_ADR_MIXED 0x2u  /* FP32 operator on the correction since an FP64 base, FP64 residual at each 10x drop */
 
 /* ---- modes for pd_cg_solve ---- */
 #define PD_CG_F64   0x1u  /* plain CG, FP64 vectors and FP64 matvec */
@@ -161,18 +169,23 @@ int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, int max_ite
  * central-difference explicit integration of Algorithm 1 (Sec. 2.3), dt = 1,
  * on P K P u = P b.  The paper leaves the fictitious density D and the damping
  * c to its reference (Kilic and Madenci): D_i = 1/4 sum_j |K_ij| (Gershgorin,
- * interior row; with the surface correction, the largest row), c^n = 2 sqrt(u^T K1 u / u^T u) with the diagonal local
- * stiffness K1_ii = -(f_i^n - f_i^(n-1)) / (D_i v_i^(n-1/2)), 0 when not
- * positive.  FP64 throughout; any operator method of pd_matvec, broken bonds
- * included; constant modulus only (PD_ERR_INVALID with a modulus field).
- * b, u: DEVICE double [dim][N]; u is the initial guess on entry and the
- * solution on exit (constrained components set to 0).  Stops when
- * ||P(b - K u)|| <= rtol ||P b|| at an iterate, before its update; at most
- * max_iter updates (stats->iterations counts them), PD_ERR_NOT_CONVERGED after
- * that with u holding the last iterate and stats filled (outer = 0,
- * persistent = 0). */
-int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter, pd_cg_stats *stats,
-                 void *stream);
+ * interior row; with the surface correction, the largest row), c^n =
+ * 2 sqrt(u^T K1 u / u^T u) with the diagonal local stiffness
+ * K1_ii = -(f_i^n - f_i^(n-1)) / (D_i v_i^(n-1/2)), 0 when not positive.
+ * mode PD_ADR_F64: FP64 throughout.  mode PD_ADR_MIXED: the same iteration with
+ * the operator applied in FP32 to the correction d = u - u_base (residual
+ * r_base - K d, velocity and damping in FP32); whenever that estimate has
+ * dropped tenfold, d is added to u_base in FP64 and the residual there is
+ * recomputed with the FP64 operator (stats->outer counts these).  Any operator
+ * method of pd_matvec, broken bonds included; constant modulus only
+ * (PD_ERR_INVALID with a modulus field).  b, u: DEVICE double [dim][N]; u is
+ * the initial guess on entry and the solution on exit (constrained components
+ * set to 0).  Stops when the FP64 ||P(b - K u)|| <= rtol ||P b|| (PD_ADR_F64:
+ * at an iterate, before its update); at most max_iter updates
+ * (stats->iterations counts them), PD_ERR_NOT_CONVERGED after that with u
+ * holding the last iterate and stats filled (persistent = 0). */
+int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter, uint32_t mode,
+                 pd_cg_stats *stats, void *stream);
 
 /* Velocity-Verlet (Algorithm 2) with acceleration a = (f + b)/rho, f = A(mu) u,
  * and bond breaking (Eqs. mu, fra:s1) after each drift.  u, v: DEVICE double

@@ -29,11 +29,14 @@ PD_METHOD_FFT = 0x20
 PD_PROJECT = 0x100
 PD_IGNORE_BROKEN = 0x200
 PD_NO_TMA = 0x400
+PD_ACCURATE = 0x800
 PD_CG_F64 = 0x1
 PD_CG_MIXED = 0x2
 PD_CG_GRAPH = 0x10
 PD_SC_NONE = 0
 PD_SC_VOLUME = 1
+PD_ADR_F64 = 0x1
+PD_ADR_MIXED = 0x2
 
 _STATUS = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM", 4: "PD_ERR_NOT_CONVERGED",
            5: "PD_ERR_TIMEOUT", 6: "PD_ERR_STATE"}
@@ -70,7 +73,7 @@ SIGNATURES = {
     "pd_matvec": (_I, [_VP, _VP, _VP, _U32, _VP]),
     "pd_matvec_batch": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
     "pd_cg_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
-    "pd_adr_solve": (_I, [_VP, _VP, _VP, _D, _I, ctypes.POINTER(pd_cg_stats), _VP]),
+    "pd_adr_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
     "pd_step": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats), _VP]),
     "pd_step_noalloc": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats),
                              _VP]),
@@ -172,11 +175,11 @@ def pd_matvec_batch(g, batch: int, u, out, flags: int, stream=None):
     _check(load_library().pd_matvec_batch(g, int(batch), _dptr(u), _dptr(out), int(flags), _stream(stream)))
 
 
-def pd_adr_solve(g, b, u, rtol: float, max_iter: int, stream=None, allow_not_converged=False):
+def pd_adr_solve(g, b, u, rtol: float, max_iter: int, stream=None, allow_not_converged=False, mode=PD_ADR_F64):
     import torch
     st = pd_cg_stats()
     rc = load_library().pd_adr_solve(g, _dptr(b, torch.float64), _dptr(u, torch.float64), float(rtol), int(max_iter),
-                                     ctypes.byref(st), _stream(stream))
+                                     int(mode), ctypes.byref(st), _stream(stream))
     if not (allow_not_converged and rc == PD_ERR_NOT_CONVERGED):
         _check(rc)
     return st
@@ -354,12 +357,12 @@ class Grid:
             pd_matvec_batch(self.handle, batch, u, out, flags | _dtype_flag(u), stream)
         return out
 
-    def adr_solve(self, b, u=None, rtol=1e-8, max_iter=1000000, stream=None):
-        """The paper's ADR/CDEI static solver (Algorithm 1), FP64."""
+    def adr_solve(self, b, u=None, rtol=1e-8, max_iter=1000000, mode=PD_ADR_F64, stream=None):
+        """The paper's ADR/CDEI static solver (Algorithm 1): FP64, or FP32 operator with FP64 refresh."""
         import torch
         if u is None:
             u = torch.zeros_like(b)
-        st = pd_adr_solve(self.handle, b, u, rtol, max_iter, stream)
+        st = pd_adr_solve(self.handle, b, u, rtol, max_iter, stream, mode=mode)
         return u, st
 
     def cg_solve(self, b, u=None, rtol=1e-8, max_iter=100000, mode=PD_CG_MIXED, stream=None):

@@ -61,6 +61,13 @@ struct AdrWs {
     cudaGraphExec_t graph = nullptr;
     const void *key = nullptr;
     int64_t stamp = -1;
+    // mixed mode: FP32 correction d = u - u_base, velocity, K d at two iterates, base residual,
+    // FP32 copy of the base (for the damping quotient only)
+    size_t mbytes = 0;
+    void *mbase = nullptr;
+    float *d32, *dlo32, *v32, *q32, *w32, *rb32, *ub32;
+    cudaGraphExec_t mgraph = nullptr;
+    int64_t mstamp = -1;
 };
 
 struct Dens {
@@ -85,15 +92,15 @@ k_adr_resid0(double *pb, const double *__restrict__ b, const double *__restrict_
 {
     __shared__ double red[kBlk / 32];
     double acc = 0.0;
-    const int64_t L = (int64_t)dim * N;
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
-        const int c = (int)(i / N);
-        const bool fixed = cons && ((cons[i - c * N] >> c) & 1);
-        const double bi = fixed ? 0.0 : b[i];
-        pb[i] = bi;
-        const double r = bi - q[i];
-        acc += r * r;
-    }
+    for (int c = 0; c < dim; ++c)
+        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
+            const int64_t i = c * N + p;
+            const bool fixed = cons && ((cons[p] >> c) & 1);
+            const double bi = fixed ? 0.0 : b[i];
+            pb[i] = bi;
+            const double r = bi - q[i];
+            acc += r * r;
+        }
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
     if (last_block(&sc->retire)) {
@@ -112,13 +119,13 @@ __global__ void __launch_bounds__(kBlk)
 k_adr_first(double *u, double *v, const double *__restrict__ q, const double *__restrict__ pb, int64_t N, int dim,
             Dens D)
 {
-    const int64_t L = (int64_t)dim * N;
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
-        const int c = (int)(i / N);
-        const double vi = (pb[i] - q[i]) / D.d[c] / 2.0;
-        v[i] = vi;
-        u[i] += vi;
-    }
+    for (int c = 0; c < dim; ++c)
+        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
+            const int64_t i = c * N + p;
+            const double vi = (pb[i] - q[i]) / D.d[c] / 2.0;
+            v[i] = vi;
+            u[i] += vi;
+        }
 }
 
 // r.r, u^T K1 u and u^T u at u^n; the last block forms c^n and the stop flag.
@@ -133,14 +140,17 @@ k_adr_reduce(const double *__restrict__ u, const double *__restrict__ v, const d
     __syncthreads();
     if (s_done) return;
     double a_rr = 0.0, a_num = 0.0, a_den = 0.0;
-    const int64_t L = (int64_t)dim * N;
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
-        const int c = (int)(i / N);
-        const double r = pb[i] - q[i];
-        a_rr += r * r;
-        const double ui = u[i], vi = v[i];
-        if (vi != 0.0) a_num += ui * ((q[i] - q_old[i]) / (D.d[c] * vi)) * ui;   // -(f - f_old) = q - q_old
-        a_den += ui * ui;
+    for (int c = 0; c < dim; ++c) {
+        const double Dc = D.d[c];
+        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
+            const int64_t i = c * N + p;
+            const double qi = q[i];
+            const double r = pb[i] - qi;
+            a_rr += r * r;
+            const double ui = u[i], vi = v[i];
+            if (vi != 0.0) a_num += ui * ((qi - q_old[i]) / (Dc * vi)) * ui;   // -(f - f_old) = q - q_old
+            a_den += ui * ui;
+        }
     }
     const int nb = gridDim.x;
     const double s0 = block_sum(a_rr, red), s1 = block_sum(a_num, red), s2 = block_sum(a_den, red);
@@ -185,21 +195,183 @@ k_adr_update(double *u, double *v, const double *__restrict__ q, const double *_
     __syncthreads();
     if (s_done) return;
     const double c = s_c, a = 2.0 - c, e = 1.0 / (2.0 + c);
-    const int64_t L = (int64_t)dim * N;
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
-        const int cc = (int)(i / N);
-        const double vi = (a * v[i] + 2.0 * (pb[i] - q[i]) * invD.d[cc]) * e;
-        v[i] = vi;
-        u[i] += vi;
+    for (int cc = 0; cc < dim; ++cc) {
+        const double g = 2.0 * invD.d[cc];
+        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
+            const int64_t i = cc * N + p;
+            const double vi = (a * v[i] + (pb[i] - q[i]) * g) * e;
+            v[i] = vi;
+            u[i] += vi;
+        }
     }
 }
 
 __global__ void __launch_bounds__(kBlk)
 k_adr_zero_constrained(double *u, const uint8_t *__restrict__ cons, int64_t N, int dim)
 {
-    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < (int64_t)dim * N; i += (int64_t)gridDim.x * kBlk) {
-        const int c = (int)(i / N);
-        if ((cons[i - c * N] >> c) & 1) u[i] = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk)
+        for (int c = 0; c < dim; ++c)
+            if ((cons[p] >> c) & 1) u[c * N + p] = 0.0;
+}
+
+// ------------------------------------------------------------------ mixed precision
+// The same iteration with the operator applied in FP32 to the correction
+// d = u - u_base only: the residual is r = r_base - K d, where r_base is the
+// FP64 residual at the base point (recomputed whenever the FP32 estimate has
+// dropped tenfold).  The product of each iteration is w = K v^(n-1/2), the
+// change of K d over the last step, accumulated into q = K d: the damping
+// quotient needs exactly that change, and taking it as the difference of two
+// FP32 products of d would leave only rounding noise where v is small.  d is
+// kept as an unevaluated FP32 sum d + d_lo (compensated summation of the
+// steps): otherwise the roundings of d, which K amplifies up to its condition
+// number, open a gap between q and K d that on a 1024^2 grid is as large as the
+// residual itself.  In exact arithmetic the iterates are those above.  The product is taken
+// without projection (the fast interior path of the FP32 stencil);
+// constrained components are masked here instead.
+
+// r.r (estimated), u^T K1 u, u^T u at iterate n with q^n = q^(n-1) + w, K1_ii = w_i / (D v_i),
+// u = u_base + d; the last block forms c and the flag.
+__global__ void __launch_bounds__(kBlk)
+k_adrm_reduce(const float *__restrict__ d, const float *__restrict__ ub, const float *__restrict__ v,
+              const float *__restrict__ q, const float *__restrict__ w, const float *__restrict__ rb,
+              const uint8_t *__restrict__ cons, int64_t N, int dim, Dens D, AdrScal *sc, double *partial)
+{
+    __shared__ double red[kBlk / 32];
+    __shared__ int s_done;
+    if (threadIdx.x == 0) s_done = sc->done;
+    __syncthreads();
+    if (s_done) return;
+    // u^T K1 u sums terms of both signs and of very different sizes (small velocities give
+    // large quotients) that largely cancel: that sum runs in FP64, the positive ones in FP32
+    float a_rr = 0.f, a_den = 0.f;
+    double a_num = 0.0;
+    for (int c = 0; c < dim; ++c) {
+        const float Dc = (float)D.d[c];
+        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
+            const int64_t i = c * N + p;
+            const bool fixed = cons && ((cons[p] >> c) & 1);
+            const float wi = w[i];
+            const float r = fixed ? 0.f : rb[i] - (q[i] + wi);
+            a_rr = __fmaf_rn(r, r, a_rr);
+            const float ui = ub[i] + d[i], vi = v[i];
+            // velocities below 1e-30 are taken as zero (keeps the quotient finite in FP32)
+            if (!fixed && fabsf(vi) > 1e-30f) a_num += (double)(ui * (wi / (Dc * vi)) * ui);
+            a_den = __fmaf_rn(ui, ui, a_den);
+        }
+    }
+    const int nb = gridDim.x;
+    const double s0 = block_sum(a_rr, red), s1 = block_sum(a_num, red), s2 = block_sum(a_den, red);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s0;
+        partial[nb + blockIdx.x] = s1;
+        partial[2 * nb + blockIdx.x] = s2;
+    }
+    if (last_block(&sc->retire)) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int i = threadIdx.x; i < nb; i += kBlk) {
+            t0 += __ldcg(partial + i);
+            t1 += __ldcg(partial + nb + i);
+            t2 += __ldcg(partial + 2 * nb + i);
+        }
+        t0 = block_sum(t0, red);
+        t1 = block_sum(t1, red);
+        t2 = block_sum(t2, red);
+        if (threadIdx.x == 0) {
+            sc->rr = t0;
+            sc->num = t1;
+            sc->den = t2;
+            sc->c = (t1 > 0.0 && t2 > 0.0 && isfinite(t1)) ? 2.0 * sqrt(t1 / t2) : 0.0;
+            if (!(t0 > sc->tol2)) sc->done = 1;
+            sc->retire = 0u;
+        }
+    }
+}
+
+// q += w; v = ((2 - c) v + 2 r / D) / (2 + c), d += v (compensated: the rounding
+// error of each add goes to d_lo) on free components (constrained ones stay 0).
+__global__ void __launch_bounds__(kBlk)
+k_adrm_update(float *d, float *dlo, float *v, float *q, const float *__restrict__ w, const float *__restrict__ rb,
+              const uint8_t *__restrict__ cons, int64_t N, int dim, Dens invD, AdrScal *sc)
+{
+    __shared__ int s_done;
+    __shared__ double s_c;
+    if (threadIdx.x == 0) {
+        s_done = sc->done;
+        s_c = sc->c;
+        if (blockIdx.x == 0 && !s_done) sc->iters += 1;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const float a = (float)(2.0 - s_c), e = (float)(1.0 / (2.0 + s_c));
+    for (int cc = 0; cc < dim; ++cc) {
+        const float g = (float)(2.0 * invD.d[cc]);
+        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
+            if (cons && ((cons[p] >> cc) & 1)) continue;
+            const int64_t i = cc * N + p;
+            const float qn = q[i] + w[i];
+            q[i] = qn;
+            const float vi = (a * v[i] + (rb[i] - qn) * g) * e;
+            v[i] = vi;
+            const float dh = d[i], sum = dh + vi, bp = sum - dh;   // two-sum of Knuth
+            d[i] = sum;
+            dlo[i] += (dh - (sum - bp)) + (vi - bp);
+        }
+    }
+}
+
+// First half step from the base: v = r_base / (2 D), d = v, and the FP32 copy of the base.
+__global__ void __launch_bounds__(kBlk)
+k_adrm_first(float *d, float *dlo, float *v, float *ub, const float *__restrict__ rb, const double *__restrict__ u,
+             int64_t N, int dim, Dens invD)
+{
+    for (int c = 0; c < dim; ++c) {
+        const float g = (float)(0.5 * invD.d[c]);
+        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
+            const int64_t i = c * N + p;
+            const float vi = rb[i] * g;
+            v[i] = vi;
+            d[i] = vi;
+            dlo[i] = 0.f;
+            ub[i] = (float)u[i];
+        }
+    }
+}
+
+// u_base += d + d_lo in FP64, d = 0, refresh the FP32 copy of the base.
+__global__ void __launch_bounds__(kBlk)
+k_adrm_fold(double *u, float *d, float *dlo, float *ub, int64_t L)
+{
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+        const double ui = u[i] + ((double)d[i] + (double)dlo[i]);
+        u[i] = ui;
+        d[i] = 0.f;
+        dlo[i] = 0.f;
+        ub[i] = (float)ui;
+    }
+}
+
+// r_base = P b - P K P u (FP64 product already in q); its FP32 copy and |r|^2 (FP64).
+__global__ void __launch_bounds__(kBlk)
+k_adrm_true(float *rb, const double *__restrict__ pb, const double *__restrict__ q, int64_t L, AdrScal *sc,
+            double *partial)
+{
+    __shared__ double red[kBlk / 32];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kBlk + threadIdx.x; i < L; i += (int64_t)gridDim.x * kBlk) {
+        const double r = pb[i] - q[i];
+        rb[i] = (float)r;
+        acc += r * r;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (last_block(&sc->retire)) {
+        double t = 0.0;
+        for (int i = threadIdx.x; i < gridDim.x; i += kBlk) t += __ldcg(partial + i);
+        t = block_sum(t, red);
+        if (threadIdx.x == 0) {
+            sc->rr = t;
+            sc->retire = 0u;
+        }
     }
 }
 
@@ -288,6 +460,45 @@ int adr_iteration(pd_grid *g, AdrWs *w, double *u, const Dens &D, int cur, cudaS
     return PD_OK;
 }
 
+int ensure_mixed(pd_grid *g, AdrWs *w)
+{
+    const size_t L = (size_t)g->dim * g->N;
+    const size_t need = sizeof(float) * 7 * ((L + 63) & ~(size_t)63) + 1024;
+    if (w->mbytes >= need) return PD_OK;
+    if (w->mgraph) {
+        cudaGraphExecDestroy(w->mgraph);
+        w->mgraph = nullptr;
+    }
+    if (w->mbase) cudaFree(w->mbase);
+    w->mbase = nullptr;
+    w->mbytes = 0;
+    if (cudaMalloc(&w->mbase, need) != cudaSuccess) return fail(PD_ERR_OOM, "ADR mixed workspace");
+    w->mbytes = need;
+    float *c = (float *)w->mbase;
+    const size_t st = (L + 63) & ~(size_t)63;   // 256-byte aligned vectors (TMA needs 16)
+    w->d32 = c;
+    w->v32 = c + st;
+    w->q32 = c + 2 * st;
+    w->w32 = c + 3 * st;
+    w->rb32 = c + 4 * st;
+    w->ub32 = c + 5 * st;
+    w->dlo32 = c + 6 * st;
+    return PD_OK;
+}
+
+int adrm_iteration(pd_grid *g, AdrWs *w, const Dens &D, const Dens &invD, cudaStream_t s)
+{
+    const uint8_t *cons = g->has_cons ? g->d_cons : nullptr;
+    int rc = matvec(g, 1, w->v32, w->w32, PD_F32 | PD_ACCURATE | kInputProjected, s);
+    if (rc) return rc;
+    k_adrm_reduce<<<w->blocks, kBlk, 0, s>>>(w->d32, w->ub32, w->v32, w->q32, w->w32, w->rb32, cons, g->N, g->dim,
+                                             D, w->sc, w->partial);
+    k_adrm_update<<<w->blocks, kBlk, 0, s>>>(w->d32, w->dlo32, w->v32, w->q32, w->w32, w->rb32, cons, g->N, g->dim,
+                                             invD, w->sc);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
 }  // namespace
 
 void adr_release(pd_grid *g)
@@ -295,6 +506,8 @@ void adr_release(pd_grid *g)
     AdrWs *w = (AdrWs *)g->adr;
     if (!w) return;
     if (w->graph) cudaGraphExecDestroy(w->graph);
+    if (w->mgraph) cudaGraphExecDestroy(w->mgraph);
+    if (w->mbase) cudaFree(w->mbase);
     if (w->base) cudaFree(w->base);
     if (w->cap) cudaStreamDestroy(w->cap);
     delete w;
@@ -305,12 +518,13 @@ void adr_release(pd_grid *g)
 
 using namespace pd;
 
-extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter, pd_cg_stats *stats,
-                            void *stream)
+extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter, uint32_t mode,
+                            pd_cg_stats *stats, void *stream)
 {
     if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
     if (!b || !u) return fail(PD_ERR_INVALID, "b and u must be device pointers");
     if (!(rtol > 0) || max_iter < 1) return fail(PD_ERR_INVALID, "rtol > 0 and max_iter >= 1 required");
+    if (mode != PD_ADR_F64 && mode != PD_ADR_MIXED) return fail(PD_ERR_INVALID, "mode must be PD_ADR_F64 or PD_ADR_MIXED");
     if (g->has_E) return fail(PD_ERR_INVALID, "ADR needs a constant modulus (no modulus field)");
     cudaStream_t s = (cudaStream_t)stream;
     const auto t0 = std::chrono::steady_clock::now();
@@ -344,10 +558,104 @@ extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol,
     PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(AdrScal), cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     double rel = std::sqrt(hs->rr) / bn;
-    int iters = 0;
+    int iters = 0, outer = 0, f64mv = 1;
     int status = PD_ERR_NOT_CONVERGED;
     if (rel <= rtol) {
         status = PD_OK;
+    } else if (mode == PD_ADR_MIXED) {
+        rc = ensure_mixed(g, w);
+        if (rc) return rc;
+        const Dens invD = recip(D);
+        const int64_t L = (int64_t)g->dim * g->N;
+        constexpr double kRU = 0.1;   // new FP64 base residual once the estimate has dropped tenfold
+        const double floor2 = (0.5 * rtol * bn) * (0.5 * rtol * bn);
+        k_adrm_true<<<blocks, kBlk, 0, s>>>(w->rb32, w->pb, w->q[0], L, w->sc, w->partial);
+        k_adrm_first<<<blocks, kBlk, 0, s>>>(w->d32, w->dlo32, w->v32, w->ub32, w->rb32, u, g->N, g->dim,
+                                                 invD);
+        // K d^0 = 0: the first product K v^(1/2) then gives K d^1
+        PD_CUDA(cudaMemsetAsync(w->q32, 0, sizeof(float) * (size_t)L, s));
+        PD_CUDA(cudaGetLastError());
+        double rr_b = hs->rr;
+        AdrScal init{};
+        init.iters = 1;
+        init.tol2 = std::max(kRU * kRU * rr_b, floor2);
+        *(AdrScal *)g->h_pinned = init;
+        PD_CUDA(cudaMemcpyAsync(w->sc, g->h_pinned, sizeof(AdrScal), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaStreamSynchronize(s));
+        if (!w->mgraph || w->mstamp != g->op_stamp) {   // chunks touch only the workspace
+            if (w->mgraph) {
+                cudaGraphExecDestroy(w->mgraph);
+                w->mgraph = nullptr;
+            }
+            rc = adrm_iteration(g, w, D, invD, s);   // first use outside any capture (kernel attributes)
+            if (rc) return rc;
+            PD_CUDA(cudaMemsetAsync(w->q32, 0, sizeof(float) * (size_t)L, s));
+            *(AdrScal *)g->h_pinned = init;
+            PD_CUDA(cudaMemcpyAsync(w->sc, g->h_pinned, sizeof(AdrScal), cudaMemcpyHostToDevice, s));
+            k_adrm_first<<<blocks, kBlk, 0, s>>>(w->d32, w->dlo32, w->v32, w->ub32, w->rb32, u, g->N, g->dim,
+                                                 invD);
+            PD_CUDA(cudaStreamSynchronize(s));
+            cudaGraph_t graph = nullptr;
+            bool ok = cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                for (int i = 0; i < kChunk && ok; ++i) ok = (adrm_iteration(g, w, D, invD, w->cap) == PD_OK);
+                ok = (cudaStreamEndCapture(w->cap, &graph) == cudaSuccess) && ok;
+            }
+            if (ok && cudaGraphInstantiate(&w->mgraph, graph, 0) != cudaSuccess) w->mgraph = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            w->mstamp = g->op_stamp;
+        }
+        int dev_iters = 1;
+        for (;;) {
+            // one phase: FP32 iterations until the estimate reaches its target or the cap
+            bool done = false;
+            while (!done && dev_iters < max_iter) {
+                const int n = std::min(kChunk, max_iter - dev_iters);   // at most one update per iteration
+                if (w->mgraph && n == kChunk) {
+                    PD_CUDA(cudaGraphLaunch(w->mgraph, s));
+                } else {
+                    for (int i = 0; i < n; ++i) {
+                        rc = adrm_iteration(g, w, D, invD, s);
+                        if (rc) return rc;
+                    }
+                }
+                PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(AdrScal), cudaMemcpyDeviceToHost, s));
+                PD_CUDA(cudaStreamSynchronize(s));
+                done = hs->done != 0;
+                dev_iters = hs->iters;
+            }
+            ++outer;
+            // fold the correction into the FP64 base and take the true residual there
+            k_adrm_fold<<<blocks, kBlk, 0, s>>>(u, w->d32, w->dlo32, w->ub32, L);
+            rc = matvec(g, 1, u, w->q[0], PD_F64 | PD_PROJECT | kInputProjected, s);
+            if (rc) return rc;
+            k_adrm_true<<<blocks, kBlk, 0, s>>>(w->rb32, w->pb, w->q[0], L, w->sc, w->partial);
+            PD_CUDA(cudaGetLastError());
+            PD_CUDA(cudaMemcpyAsync((void *)hs, w->sc, sizeof(AdrScal), cudaMemcpyDeviceToHost, s));
+            PD_CUDA(cudaStreamSynchronize(s));
+            ++f64mv;
+            rr_b = hs->rr;
+            rel = std::sqrt(rr_b) / bn;
+            if (rel <= rtol) {
+                status = PD_OK;
+                break;
+            }
+            if (dev_iters >= max_iter || !std::isfinite(rel)) break;
+            // in the new base the previous iterate sits at d = -v: q = K d there is -K v, so that the
+            // next product K v brings q to K d = 0 at the base
+            rc = matvec(g, 1, w->v32, w->q32, PD_F32 | PD_ACCURATE | kInputProjected, s, nullptr, nullptr, nullptr,
+                        -1.0);
+            if (rc) return rc;
+            AdrScal next{};
+            next.iters = dev_iters;
+            next.tol2 = std::max(kRU * kRU * rr_b, floor2);
+            next.rr = rr_b;
+            *(AdrScal *)g->h_pinned = next;
+            PD_CUDA(cudaMemcpyAsync(w->sc, g->h_pinned, sizeof(AdrScal), cudaMemcpyHostToDevice, s));
+            PD_CUDA(cudaStreamSynchronize(s));
+        }
+        iters = dev_iters;
     } else {
         k_adr_first<<<blocks, kBlk, 0, s>>>(u, w->v, w->q[0], w->pb, g->N, g->dim, D);
         AdrScal init{};
@@ -403,10 +711,11 @@ extern "C" int pd_adr_solve(pd_grid *g, const double *b, double *u, double rtol,
         rel = std::sqrt(hs->rr) / bn;
         if (hs->done) status = PD_OK;
     }
+    if (mode == PD_ADR_F64) f64mv = iters + 1;
     if (stats) {
         stats->iterations = iters;
-        stats->outer = 0;
-        stats->f64_matvecs = iters + 1;
+        stats->outer = outer;
+        stats->f64_matvecs = f64mv;
         stats->rel_residual = rel;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         stats->persistent = 0;

@@ -187,6 +187,7 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
     a.project = (flags & PD_PROJECT) && g->has_cons;
     a.input_projected = (flags & kInputProjected) != 0;
     a.no_tma = (flags & PD_NO_TMA) != 0;
+    a.accurate = (flags & PD_ACCURATE) != 0;
     a.scale = scale;
 
     if (dot_partial && g->sc) return fail(PD_ERR_INVALID, "internal: fused dot with the surface correction");

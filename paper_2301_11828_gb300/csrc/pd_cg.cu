@@ -89,9 +89,10 @@ __device__ __forceinline__ bool grid_last(double block_value, double *partial, d
 }
 
 // x += alpha p ; r -= alpha q ; rr_new = r.r ; last block: beta, rr, done, iters.
+// FP32: x + xlo is a compensated sum (two_sum_acc); FP64: xlo unused.
 template <typename T>
 __global__ void __launch_bounds__(kBlk, 4)
-k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_t L, int64_t nv, CgScal *sc,
+k_cg_update(T *x, T *xlo, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_t L, int64_t nv, CgScal *sc,
             double *partial)
 {
     __shared__ double red[kBlk / 32];
@@ -106,22 +107,35 @@ k_cg_update(T *x, T *r, const T *__restrict__ p, const T *__restrict__ q, int64_
     const T a = (T)s_alpha;
     T acc = T(0);
     const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    constexpr bool comp = sizeof(T) == 4;
     for (int64_t j = t0; j < nv; j += st) {
         Pk<T> xv = ldp(x, j), rv = ldp(r, j);
+        Pk<T> xl;
+        if constexpr (comp) xl = ldp(xlo, j);
         const Pk<T> pv = ldp(p, j), qv = ldp(q, j);
 #pragma unroll
         for (int e = 0; e < Pk<T>::n; ++e) {
-            xv.v[e] += a * pv.v[e];
+            if constexpr (comp)
+                two_sum_acc(xv.v[e], xl.v[e], a * pv.v[e]);
+            else
+                xv.v[e] += a * pv.v[e];
             rv.v[e] -= a * qv.v[e];
             acc += rv.v[e] * rv.v[e];
         }
         stp(x, j, xv);
+        if constexpr (comp) stp(xlo, j, xl);
         stp(r, j, rv);
     }
     for (int64_t i = nv * Pk<T>::n + t0; i < L; i += st) {
-        const T xi = x[i] + a * p[i];
+        if constexpr (comp) {
+            float xi = x[i], xli = xlo[i];
+            two_sum_acc(xi, xli, a * p[i]);
+            x[i] = xi;
+            xlo[i] = xli;
+        } else {
+            x[i] = x[i] + a * p[i];
+        }
         const T ri = r[i] - a * q[i];
-        x[i] = xi;
         r[i] = ri;
         acc += ri * ri;
     }
@@ -158,8 +172,8 @@ k_cg_p(T *p, const T *__restrict__ r, int64_t L, int64_t nv, const CgScal *sc)
 // r -= alpha q, r.r; the last block forms beta, tests convergence and makes
 // p_new the next p_old.  Every block reads pbuf before the last block flips it.
 __global__ void __launch_bounds__(kBlk, 4)
-k_cg_update2(float *x, float *r, const float *p0, const float *p1, const float *__restrict__ q, int64_t L, int64_t nv,
-             CgScal *sc, double *partial)
+k_cg_update2(float *x, float *xlo, float *r, const float *p0, const float *p1, const float *__restrict__ q, int64_t L,
+             int64_t nv, CgScal *sc, double *partial)
 {
     __shared__ double red[kBlk / 32];
     __shared__ int s_done, s_pbuf;
@@ -176,21 +190,24 @@ k_cg_update2(float *x, float *r, const float *p0, const float *p1, const float *
     float acc = 0.f;
     const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
     for (int64_t j = t0; j < nv; j += st) {
-        Pk<float> xv = ldp(x, j), rv = ldp(r, j);
+        Pk<float> xv = ldp(x, j), xl = ldp(xlo, j), rv = ldp(r, j);
         const Pk<float> pv = ldp(p, j), qv = ldp(q, j);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            xv.v[e] += a * pv.v[e];
+            two_sum_acc(xv.v[e], xl.v[e], a * pv.v[e]);
             rv.v[e] -= a * qv.v[e];
             acc += rv.v[e] * rv.v[e];
         }
         stp(x, j, xv);
+        stp(xlo, j, xl);
         stp(r, j, rv);
     }
     for (int64_t i = nv * 4 + t0; i < L; i += st) {
-        const float xi = x[i] + a * p[i];
+        float xi = x[i], xli = xlo[i];
+        two_sum_acc(xi, xli, a * p[i]);
         const float ri = r[i] - a * q[i];
         x[i] = xi;
+        xlo[i] = xli;
         r[i] = ri;
         acc += ri * ri;
     }
@@ -247,8 +264,8 @@ k_resid(double *r, const double *__restrict__ b, const double *__restrict__ Ku, 
 // Inner start (mixed): r32 = r64 * inv, p32 = r32, x32 = 0, sc->rr = r32.r32, done flag.
 // nv counts packs of four floats (two packs of doubles each).
 __global__ void __launch_bounds__(kBlk)
-k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64, int64_t L, int64_t nv, double inv,
-              double tau2, CgScal *sc, double *partial)
+k_inner_start(float *r32, float *p32, float *x32, float *xlo32, const double *__restrict__ r64, int64_t L, int64_t nv,
+              double inv, double tau2, CgScal *sc, double *partial)
 {
     __shared__ double red[kBlk / 32];
     float acc = 0.f;
@@ -263,6 +280,7 @@ k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64
         stp(r32, j, v);
         stp(p32, j, v);
         stp(x32, j, Pk<float>{});
+        stp(xlo32, j, Pk<float>{});
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc += v.v[e] * v.v[e];
     }
@@ -271,6 +289,7 @@ k_inner_start(float *r32, float *p32, float *x32, const double *__restrict__ r64
         r32[i] = v;
         p32[i] = v;
         x32[i] = 0.f;
+        xlo32[i] = 0.f;
         acc += v * v;
     }
     const double bs = block_sum(acc, red);
@@ -296,25 +315,27 @@ k_plain_start(double *p, const double *__restrict__ r, int64_t L, double tol2, C
     }
 }
 
-// u += s * x32, then x32 = 0 (a reliable update folds the FP32 increment into u).
+// u += s * (x32 + xlo32), then both = 0 (a reliable update folds the FP32 increment into u).
 __global__ void __launch_bounds__(kBlk)
-k_correct_zero(double *u, float *x32, double s, int64_t L, int64_t nv)
+k_correct_zero(double *u, float *x32, float *xlo32, double s, int64_t L, int64_t nv)
 {
     const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
     for (int64_t j = t0; j < nv; j += st) {
-        const Pk<float> x = ldp(x32, j);
+        const Pk<float> x = ldp(x32, j), xl = ldp(xlo32, j);
         Pk<double> a = ldp(u, 2 * j), b = ldp(u, 2 * j + 1);
-        a.v[0] += s * (double)x.v[0];
-        a.v[1] += s * (double)x.v[1];
-        b.v[0] += s * (double)x.v[2];
-        b.v[1] += s * (double)x.v[3];
+        a.v[0] += s * ((double)x.v[0] + (double)xl.v[0]);
+        a.v[1] += s * ((double)x.v[1] + (double)xl.v[1]);
+        b.v[0] += s * ((double)x.v[2] + (double)xl.v[2]);
+        b.v[1] += s * ((double)x.v[3] + (double)xl.v[3]);
         stp(u, 2 * j, a);
         stp(u, 2 * j + 1, b);
         stp(x32, j, Pk<float>{});
+        stp(xlo32, j, Pk<float>{});
     }
     for (int64_t i = nv * 4 + t0; i < L; i += st) {
-        u[i] += s * (double)x32[i];
+        u[i] += s * ((double)x32[i] + (double)xlo32[i]);
         x32[i] = 0.f;
+        xlo32[i] = 0.f;
     }
 }
 
@@ -375,7 +396,7 @@ struct CgWs {
     size_t bytes = 0;
     void *base = nullptr;
     double *r64, *q64, *p64;    // FP64 residual, operator output, direction
-    float *r32, *p32, *q32, *x32;
+    float *r32, *p32, *q32, *x32, *xlo32;
     float *p32b;                // persistent loop: second direction buffer
     uint8_t *tile_flags;        // persistent loop: tiles holding a constrained node
     CgBar *gbar;                // persistent loop: grid barrier
@@ -398,8 +419,8 @@ int ensure_ws(pd_grid *g, CgWs *&w)
                               stencil_blocks(g, false, g->has_E || g->broken_total > 0));
     const size_t nparts = (size_t)std::max(nblk, kRedMax) + 64;
     const size_t ntile = (size_t)((g->n[0] + 63) / 64) * (size_t)((g->n[1] + 31) / 32) * (size_t)g->n[2];
-    const size_t need = sizeof(double) * 3 * L + sizeof(float) * 5 * L + sizeof(CgScal) + 2 * sizeof(double) * nparts +
-                        ntile + sizeof(CgBar) + 2304;
+    const size_t need = sizeof(double) * 3 * L + sizeof(float) * 6 * L + sizeof(CgScal) + 2 * sizeof(double) * nparts +
+                        ntile + sizeof(CgBar) + 2560;
     w = (CgWs *)g->cg;
     if (w && w->bytes >= need) return PD_OK;
     if (!w) {
@@ -433,6 +454,7 @@ int ensure_ws(pd_grid *g, CgWs *&w)
     w->p32 = (float *)take(sizeof(float) * L);
     w->q32 = (float *)take(sizeof(float) * L);
     w->x32 = (float *)take(sizeof(float) * L);
+    w->xlo32 = (float *)take(sizeof(float) * L);
     w->p32b = (float *)take(sizeof(float) * L);
     w->tile_flags = (uint8_t *)take(ntile);
     w->gbar = (CgBar *)take(sizeof(CgBar));
@@ -449,6 +471,7 @@ CgVecs cg_vecs(CgWs *w)
 {
     CgVecs v;
     v.x = w->x32;
+    v.xlo = w->xlo32;
     v.r = w->r32;
     v.q = w->q32;
     v.p[0] = w->p32;
@@ -473,12 +496,13 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s, bool f
     if (fused && !f64) {
         int rc = cg_dirmv_run(g, cg_vecs(w), w->sc, w->partial, w->tile_flags, s);
         if (rc) return rc;
-        k_cg_update2<<<w->red, kBlk, 0, s>>>(w->x32, w->r32, w->p32, w->p32b, w->q32, L, L / 4, w->sc, w->partial2);
+        k_cg_update2<<<w->red, kBlk, 0, s>>>(w->x32, w->xlo32, w->r32, w->p32, w->p32b, w->q32, L, L / 4, w->sc,
+                                             w->partial2);
         PD_CUDA(cudaGetLastError());
         return PD_OK;
     }
     const bool fuse = !(g->broken_total > 0 && !g->has_E) && !g->sc;
-    const uint32_t fl = (f64 ? PD_F64 : PD_F32) | PD_PROJECT | kInputProjected;
+    const uint32_t fl = (f64 ? PD_F64 : PD_F32 | PD_ACCURATE) | PD_PROJECT | kInputProjected;
     void *p = f64 ? (void *)w->p64 : (void *)w->p32;
     void *q = f64 ? (void *)w->q64 : (void *)w->q32;
     int rc;
@@ -498,10 +522,12 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s, bool f
     if (rc) return rc;
     if (f64) {
         const int64_t nv = aligned16(x64) ? L / 2 : 0;
-        k_cg_update<double><<<w->red64, kBlk, 0, s>>>(x64, w->r64, w->p64, w->q64, L, nv, w->sc, w->partial2);
+        k_cg_update<double><<<w->red64, kBlk, 0, s>>>(x64, nullptr, w->r64, w->p64, w->q64, L, nv, w->sc,
+                                                      w->partial2);
         k_cg_p<double><<<w->red64, kBlk, 0, s>>>(w->p64, w->r64, L, L / 2, w->sc);
     } else {
-        k_cg_update<float><<<w->red, kBlk, 0, s>>>(w->x32, w->r32, w->p32, w->q32, L, L / 4, w->sc, w->partial2);
+        k_cg_update<float><<<w->red, kBlk, 0, s>>>(w->x32, w->xlo32, w->r32, w->p32, w->q32, L, L / 4, w->sc,
+                                                   w->partial2);
         k_cg_p<float><<<w->red, kBlk, 0, s>>>(w->p32, w->r32, L, L / 4, w->sc);
     }
     PD_CUDA(cudaGetLastError());
@@ -713,7 +739,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
             status = PD_OK;
         } else {
             double rr_ref = rr / (s0 * s0);
-            k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->r64, L, L / 4, 1.0 / s0,
+            k_inner_start<<<blocks, kBlk, 0, s>>>(w->r32, w->p32, w->x32, w->xlo32, w->r64, L, L / 4, 1.0 / s0,
                                                   std::max(kRU * kRU, tgt2 / rr_ref), w->sc, w->partial2);
 
             for (int phase = 0; phase < 1000; ++phase) {
@@ -723,7 +749,7 @@ extern "C" int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, 
                              : inner_loop(g, w, false, nullptr, max_iter - total_iters, s, &it, fused);
                 total_iters += it;
                 if (rc != PD_OK && rc != PD_ERR_NOT_CONVERGED) return rc;
-                k_correct_zero<<<blocks, kBlk, 0, s>>>(u, w->x32, s0, L, aligned16(u) ? L / 4 : 0);
+                k_correct_zero<<<blocks, kBlk, 0, s>>>(u, w->x32, w->xlo32, s0, L, aligned16(u) ? L / 4 : 0);
                 PD_CUDA(cudaGetLastError());
                 rc = true_residual(g, w, b, u, s, &rr);
                 if (rc) return rc;

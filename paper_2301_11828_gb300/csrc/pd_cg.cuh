@@ -48,8 +48,20 @@ bool cg_persist_eligible(const pd_grid *g);
 int cg_persist_ctas(const pd_grid *g);
 
 // Vectors of the persistent loop (FP32, [2][N] each, 16-byte aligned).
+// hi + lo += v with the rounding error of the add kept in lo (two-sum of Knuth).
+// The FP32 solution increment is accumulated this way: each rounding of a
+// plain FP32 sum would be amplified by K up to its condition number and open a
+// gap between the recursive residual and b - K x as large as the residual on
+// fine grids.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v)
+{
+    const float s = hi + v, bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
+}
+
 struct CgVecs {
-    float *x, *r, *q;
+    float *x, *xlo, *r, *q;   // x + xlo: the FP32 increment as an unevaluated sum
     float *p[2];   // direction, double-buffered: tiles read p_old from one while CTAs write p to the other
 };
 

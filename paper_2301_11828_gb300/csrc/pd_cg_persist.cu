@@ -179,20 +179,21 @@ __device__ __forceinline__ bool cg_dir_tiles(const CUtensorMap *map_r, const CUt
         __syncthreads();
 
         u64 a1[kRt], a2[kRt], w0[WL];
-        tile_pairs<M>(sp + (ty * kRt) * BX + tx + XL, sp + PLANE + (ty * kRt) * BX + tx + XL, tab, a1, a2, w0);
+        // difference form: FP32 error relative to |K p| for smooth directions too
+        tile_pairs<M, true>(sp + (ty * kRt) * BX + tx + XL, sp + PLANE + (ty * kRt) * BX + tx + XL, tab, a1, a2,
+                            w0);
 
         const int gx = x0 + tx, gy0 = y0 + ty * kRt;
         const int64_t o0 = (int64_t)gy0 * nx + gx;
         float dot = 0.f;
         const bool interior = (x0 >= M) && (x0 + kTXt <= nx - M) && (y0 >= M) && (y0 + kTYt <= ny - M);
         if (interior && !tile_flags[t]) {
-            const float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
 #pragma unroll
             for (int r = 0; r < kRt; ++r) {
                 const float2 up = upk(w0[r + M]);
                 const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
-                const float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
-                const float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
+                const float fx = -(x1.x + x2.y);
+                const float fy = -(x1.y + x2.x);
                 const int64_t p = o0 + (int64_t)r * nx;
                 q[p] = fx;
                 q[N + p] = fy;
@@ -220,6 +221,9 @@ __device__ __forceinline__ bool cg_dir_tiles(const CUtensorMap *map_r, const CUt
                     kxy = __ldg(kd + 3 * cls + 1);
                     kyy = __ldg(kd + 3 * cls + 2);
                 }
+                kxx -= tab.v[4 * NP];   // the difference-form sums already hold -Kd_int u_p
+                kxy -= tab.v[4 * NP + 1];
+                kyy -= tab.v[4 * NP + 2];
                 float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
                 float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
                 const int64_t p = o0 + (int64_t)r * nx;
@@ -242,7 +246,7 @@ __device__ __forceinline__ bool cg_dir_tiles(const CUtensorMap *map_r, const CUt
 }
 
 template <int M>
-__global__ void __launch_bounds__(kThreads, (M <= 4 ? 3 : 2))
+__global__ void __launch_bounds__(kThreads, (M <= 3 ? 3 : 2))
 k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_p0,
              const __grid_constant__ CUtensorMap map_p1, const __grid_constant__ CgVecs v, int nx, int ny, int64_t N,
              int tiles_x, int ntiles, const uint8_t *__restrict__ cons, const uint8_t *__restrict__ tile_flags,
@@ -299,12 +303,13 @@ k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ 
         float acc = 0.f;
         for (int64_t j = t0; j < nv; j += stride) {
             float4 xv = reinterpret_cast<float4 *>(v.x)[j], rv = reinterpret_cast<float4 *>(v.r)[j];
+            float4 xl = reinterpret_cast<float4 *>(v.xlo)[j];
             const float4 pv = __ldcg(reinterpret_cast<const float4 *>(pn) + j);
             const float4 qv = __ldcg(reinterpret_cast<const float4 *>(v.q) + j);
-            xv.x += a32 * pv.x;
-            xv.y += a32 * pv.y;
-            xv.z += a32 * pv.z;
-            xv.w += a32 * pv.w;
+            two_sum_acc(xv.x, xl.x, a32 * pv.x);
+            two_sum_acc(xv.y, xl.y, a32 * pv.y);
+            two_sum_acc(xv.z, xl.z, a32 * pv.z);
+            two_sum_acc(xv.w, xl.w, a32 * pv.w);
             rv.x -= a32 * qv.x;
             rv.y -= a32 * qv.y;
             rv.z -= a32 * qv.z;
@@ -314,6 +319,7 @@ k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ 
             acc += rv.z * rv.z;
             acc += rv.w * rv.w;
             reinterpret_cast<float4 *>(v.x)[j] = xv;
+            reinterpret_cast<float4 *>(v.xlo)[j] = xl;
             reinterpret_cast<float4 *>(v.r)[j] = rv;
         }
         double rn;
@@ -338,7 +344,7 @@ k_cg_persist(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ 
 // p_old from sc, forms p and q = P K P p for every tile and reduces p.q into
 // sc->pq (last block, fixed order).
 template <int M>
-__global__ void __launch_bounds__(kThreads, (M <= 4 ? 3 : 2))
+__global__ void __launch_bounds__(kThreads, (M <= 3 ? 3 : 2))
 k_cg_dirmv(const __grid_constant__ CUtensorMap map_r, const __grid_constant__ CUtensorMap map_p0,
            const __grid_constant__ CUtensorMap map_p1, const __grid_constant__ CgVecs v, int nx, int ny, int64_t N,
            int tiles_x, int ntiles, const uint8_t *__restrict__ cons, const uint8_t *__restrict__ tile_flags,

@@ -143,6 +143,7 @@ struct MatvecArgs {
     bool use_E;           // per-node modulus (direct form)
     bool input_projected; // the caller guarantees P u = u (skip the input projection)
     bool no_tma;          // force the plain FP32 2D stencil
+    bool accurate;        // FP32 TMA stencil: difference form (PD_ACCURATE)
     double scale;         // multiplies the whole operator (1 = K u)
     // optional fused reduction: dot_out[b] = sum_p in . out (FP64), needs scratch
     double *dot_partial;  // [gridDim.x * gridDim.y] per batch

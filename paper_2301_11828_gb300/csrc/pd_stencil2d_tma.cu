@@ -19,6 +19,9 @@
 //     a2 += (cxy, cxy) * s give (K u) after the final swap
 //     a_x = a1.x + a2.y, a_y = a1.y + a2.x -- one packed add and two packed
 //     fused multiply-adds per pair instead of six scalar instructions.
+//   * DIFF (PD_ACCURATE) sums the differences (u~_{p+o} - u_p) + (u~_{p-o} - u_p)
+//     instead, so that the FP32 error is relative to |K u| even for smooth
+//     fields (see tile_pairs); the solvers use it, the plain product does not.
 // Used for FP32 grids whose row length is a multiple of 4 floats (TMA stride
 // rule); other grids use the plain kernel.
 #include <cuda.h>
@@ -37,10 +40,10 @@ using namespace tma2d;
 
 constexpr int kStages = 3;               // halo tiles in flight or in use per CTA
 
-// Three CTAs per SM (three halo tiles in flight each) up to M = 4; register
-// growth beyond that leaves two.
-template <int M>
-__global__ void __launch_bounds__(kThreads, (M <= 4 ? 3 : 2))
+// Three CTAs per SM (three halo tiles in flight each) up to M = 4 (M = 3 in
+// the difference form); register growth beyond that leaves two.
+template <int M, bool DIFF>
+__global__ void __launch_bounds__(kThreads, (M <= 3 || (M == 4 && !DIFF) ? 3 : 2))
 k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u, float *__restrict__ out, int nx,
             int ny, int64_t N, int tiles_x, int tiles_y, int ntiles, const uint8_t *__restrict__ cons,
             int project_in, int project_out, const float *__restrict__ kd, float scale, PackTab<M> tab,
@@ -136,20 +139,27 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         auto tile_body = [&](auto EDGE) {
             constexpr bool edge = decltype(EDGE)::value;
             u64 a1[kRt], a2[kRt], w0[WL];
-            tile_pairs<M>(sx + (ty * kRt) * BX + tx + XL, sy + (ty * kRt) * BX + tx + XL, tab, a1, a2, w0);
+            tile_pairs<M, DIFF>(sx + (ty * kRt) * BX + tx + XL, sy + (ty * kRt) * BX + tx + XL, tab, a1, a2, w0);
 
             float *ob = out + (int64_t)b * 2 * N;
             const int gx = x0 + tx;
-            // outputs whose horizon stays inside the grid: interior Kd, no tests
+            // outputs whose horizon stays inside the grid: interior Kd (none in the
+            // difference form), no tests
             auto interior_epilogue = [&]() {
                 const float kxx = tab.v[4 * NP], kxy = tab.v[4 * NP + 1], kyy = tab.v[4 * NP + 2];
                 float *o0 = ob + (int64_t)(y0 + ty * kRt) * nx + gx;
 #pragma unroll
                 for (int r = 0; r < kRt; ++r) {
-                    const float2 up = upk(w0[r + M]);
                     const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
-                    const float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
-                    const float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
+                    float fx, fy;
+                    if constexpr (DIFF) {
+                        fx = -(x1.x + x2.y);
+                        fy = -(x1.y + x2.x);
+                    } else {
+                        const float2 up = upk(w0[r + M]);
+                        fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -(x1.x + x2.y)));
+                        fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -(x1.y + x2.x)));
+                    }
                     o0[(int64_t)r * nx] = fx * scale;
                     o0[(int64_t)r * nx + N] = fy * scale;
                 }
@@ -193,6 +203,11 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
                         kxy = __ldg(kd + 3 * cls + 1);
                         kyy = __ldg(kd + 3 * cls + 2);
                     }
+                    if constexpr (DIFF) {   // the sums already hold -Kd_int u_p
+                        kxx -= tab.v[4 * NP];
+                        kxy -= tab.v[4 * NP + 1];
+                        kyy -= tab.v[4 * NP + 2];
+                    }
                     float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
                     float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
                     if (project_out) {
@@ -231,7 +246,7 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
 }
 
 // ------------------------------------------------------------------ host side
-template <int M>
+template <int M, bool DIFF>
 int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
     constexpr int BX = box_x<M>(), BY = box_y<M>();
@@ -239,7 +254,7 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     CUtensorMap map;
     if (!make_map<M>(&map, a.u, nx, ny, a.batch)) return fail(PD_ERR_CUDA, "tensor map encode failed");
     const size_t smem = (size_t)kStages * 2 * BX * BY * sizeof(float);
-    auto kern = k_tbt2d_tma<M>;
+    auto kern = k_tbt2d_tma<M, DIFF>;
     static int attr_done[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -293,16 +308,19 @@ bool tma_stencil_eligible(const pd_grid *g, const MatvecArgs &a, bool f64)
 
 int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
+#define PD_TMA_CASE(m) \
+    case m: return a.accurate ? run<m, true>(g, a, s) : run<m, false>(g, a, s);
     switch (g->M) {
-        case 1: return run<1>(g, a, s);
-        case 2: return run<2>(g, a, s);
-        case 3: return run<3>(g, a, s);
-        case 4: return run<4>(g, a, s);
-        case 5: return run<5>(g, a, s);
-        case 6: return run<6>(g, a, s);
-        case 7: return run<7>(g, a, s);
-        case 8: return run<8>(g, a, s);
+        PD_TMA_CASE(1)
+        PD_TMA_CASE(2)
+        PD_TMA_CASE(3)
+        PD_TMA_CASE(4)
+        PD_TMA_CASE(5)
+        PD_TMA_CASE(6)
+        PD_TMA_CASE(7)
+        PD_TMA_CASE(8)
     }
+#undef PD_TMA_CASE
     return fail(PD_ERR_INVALID, "horizon M not compiled for 2D");
 }
 

@@ -41,17 +41,16 @@ k_sc_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int
             const int32_t *__restrict__ band, int64_t nband, const int32_t *__restrict__ off,
             const double *__restrict__ coef, const double *__restrict__ E, const double *__restrict__ nu_tab,
             const uint32_t *__restrict__ mask, int use_mu, const uint8_t *__restrict__ cons, int project,
-            double scale, int64_t batch)
+            double scale)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = warp; w < nband * batch; w += nwarps) {
-        const int64_t b = w / nband;
-        const int64_t p = band[w - b * nband];
-        const T *ub = u + b * DIM * N;
-        T *ob = out + b * DIM * N;
-        const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((int64_t)nx * ny));
+    const T *ub = u + (int64_t)blockIdx.y * DIM * N;   // one field per grid row
+    T *ob = out + (int64_t)blockIdx.y * DIM * N;
+    for (int64_t w = warp; w < nband; w += nwarps) {
+        const int p = band[w];   // fewer than 2^31 nodes: 32-bit index arithmetic
+        const int i = p % nx, j = (p / nx) % ny, k = p / (nx * ny);
         const double nu_p = nu_tab[nu_class(i, j, k, nx, ny, nz, M, DIM)];
         const double E_p = E ? E[p] : 1.0;
         const uint8_t cm = project ? cons[p] : 0;
@@ -68,7 +67,7 @@ k_sc_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int
             const double nu_q = nu_tab[nu_class(qi, qj, qk, nx, ny, nz, M, DIM)];
             double wgt = 0.5 * (nu_p + nu_q) - 1.0;
             if (wgt == 0.0) continue;
-            const int64_t q = ((int64_t)qk * ny + qj) * nx + qi;
+            const int q = (qk * ny + qj) * nx + qi;
             if (E) wgt *= 0.5 * (E_p + E[q]);
             const uint8_t qm = project ? cons[q] : 0;
             double d[DIM];
@@ -112,8 +111,8 @@ k_sc_rowmax(int64_t N, int nx, int ny, int nz, int M, int nnb, const int32_t *__
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int NC = DIM == 2 ? 3 : 6;
     for (int64_t w = warp; w < nband; w += nwarps) {
-        const int64_t p = band[w];
-        const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((int64_t)nx * ny));
+        const int p = band[w];
+        const int i = p % nx, j = (p / nx) % ny, k = p / (nx * ny);
         const double nu_p = nu_tab[nu_class(i, j, k, nx, ny, nz, M, DIM)];
         double diag[NC], offs[DIM];
 #pragma unroll
@@ -236,15 +235,16 @@ int launch_sc_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t bat
                      double scale, cudaStream_t s)
 {
     if (!g->sc || g->band_n == 0) return PD_OK;
-    const int64_t work = g->band_n * batch;   // warps
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 7) / 8, 152 * 8));
+    if (batch > 65535) return fail(PD_ERR_INVALID, "batch must be at most 65535");
+    const int64_t per_field = std::max<int64_t>(1, std::min<int64_t>((g->band_n + 7) / 8, 152 * 8 / batch + 1));
+    const dim3 blocks((unsigned)per_field, (unsigned)batch);   // 8 warps per block, one node per warp
     const int nx = (int)g->n[0], ny = (int)g->n[1], nz = (int)g->n[2];
     const double *coef = g->has_E ? g->d_coef1 : g->d_coef;
     const double *E = g->has_E ? g->d_E : nullptr;
 #define PD_SC(T, D)                                                                                              \
     k_sc_gather<T, D><<<blocks, kBlk, 0, s>>>((const T *)u, (T *)out, g->N, nx, ny, nz, g->M, g->nnb, g->d_band,  \
                                                g->band_n, g->d_off, coef, E, g->d_nu_tab, g->d_mask,              \
-                                               use_mu ? 1 : 0, g->d_cons, project ? 1 : 0, scale, batch)
+                                               use_mu ? 1 : 0, g->d_cons, project ? 1 : 0, scale)
     if (g->dim == 2) {
         if (f64) PD_SC(double, 2); else PD_SC(float, 2);
     } else {

@@ -32,6 +32,12 @@ __device__ __forceinline__ u64 fadd2(u64 a, u64 b)
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b)
+{
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
 {
     u64 d;
@@ -99,18 +105,30 @@ struct __align__(16) PackTab {
     float v[4 * kPairs + 4];
 };
 
-// Pair sums of the TBT form for the kRt outputs of one thread.  colx / coly point
-// at the thread's column (first halo row) in the x / y planes of a staged box of
-// row length BX.  On return a1, a2 hold the packed accumulators of
-// sum_{o in half} c(o) (u~_{p+o} + u~_{p-o}) (f_x = a1.x + a2.y, f_y = a1.y + a2.x)
-// and w0 the thread's own column (w0[r + M] = u_p of output r).
-template <int M>
+// Per-tile pair sums.  colx / coly point at the thread's column (first halo
+// row) in the x / y planes of a staged box of row length BX.  On return a1, a2
+// hold the packed accumulators of sum_{o in half} c(o) s_o with
+//   s_o = u~_{p+o} + u~_{p-o}                     (DIFF = false, pair form), or
+//   s_o = (u~_{p+o} - u_p) + (u~_{p-o} - u_p)     (DIFF = true, difference form),
+// (f_x = a1.x + a2.y, f_y = a1.y + a2.x), and w0 the thread's own column
+// (w0[r + M] = u_p of output r).  The pair form leaves K u = Kd_p u_p - a: for a
+// smooth field its terms nearly cancel, so its FP32 error is relative to
+// sum |c||u| rather than to |K u|.  The difference form rounds the small
+// differences instead and gives K u = (Kd_p - Kd_int) u_p - a, where Kd_int =
+// 2 sum c(o) is the interior diagonal; it costs two packed subtractions more
+// per general pair and two scalar ones per axis pair.
+template <int M, bool DIFF = false>
 __device__ __forceinline__ void tile_pairs(const float *colx, const float *coly, const PackTab<M> &tab,
                                            u64 (&a1)[kRt], u64 (&a2)[kRt], u64 (&w0)[kRt + 2 * M])
 {
     constexpr int BX = box_x<M>(), WL = kRt + 2 * M;
 #pragma unroll
     for (int r = 0; r < kRt; ++r) { a1[r] = 0ull; a2[r] = 0ull; }
+    u64 ctr[DIFF ? kRt : 1];   // difference form: u_p of each output
+    if constexpr (DIFF) {
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) ctr[r] = pk(colx[(r + M) * BX], coly[(r + M) * BX]);
+    }
     static_for<1, M + 1>([&](auto OX) {
         constexpr int ox = decltype(OX)::value;
         constexpr int My = isqrt_c(M * M - ox * ox);
@@ -128,7 +146,11 @@ __device__ __forceinline__ void tile_pairs(const float *colx, const float *coly,
                 const u64 c2 = *reinterpret_cast<const u64 *>(&tab.v[4 * pi + 2]);
 #pragma unroll
                 for (int r = 0; r < kRt; ++r) {
-                    const u64 s = fadd2(wp[r + M + oy], wm[r + M - oy]);
+                    u64 s;
+                    if constexpr (DIFF)
+                        s = fadd2(fsub2(wp[r + M + oy], ctr[r]), fsub2(wm[r + M - oy], ctr[r]));
+                    else
+                        s = fadd2(wp[r + M + oy], wm[r + M - oy]);
                     a1[r] = ffma2(c1, s, a1[r]);
                     a2[r] = ffma2(c2, s, a2[r]);
                 }
@@ -143,7 +165,14 @@ __device__ __forceinline__ void tile_pairs(const float *colx, const float *coly,
             for (int r = 0; r < kRt; ++r) {
                 const float2 p2 = upk(wp[r + M]), m2 = upk(wm[r + M]);
                 float2 acc = upk(a1[r]);
-                acc.x = __fmaf_rn(cxx, p2.x + m2.x, acc.x);
+                float sx;
+                if constexpr (DIFF) {
+                    const float cx = upk(ctr[r]).x;
+                    sx = (p2.x - cx) + (m2.x - cx);
+                } else {
+                    sx = p2.x + m2.x;
+                }
+                acc.x = __fmaf_rn(cxx, sx, acc.x);
                 a1[r] = pk(acc.x, acc.y);
             }
         }
@@ -159,7 +188,14 @@ __device__ __forceinline__ void tile_pairs(const float *colx, const float *coly,
         for (int r = 0; r < kRt; ++r) {
             const float2 p2 = upk(w0[r + M + oy]), m2 = upk(w0[r + M - oy]);
             float2 acc = upk(a1[r]);
-            acc.y = __fmaf_rn(cyy, p2.y + m2.y, acc.y);
+            float sy;
+            if constexpr (DIFF) {
+                const float cy = upk(w0[r + M]).y;
+                sy = (p2.y - cy) + (m2.y - cy);
+            } else {
+                sy = p2.y + m2.y;
+            }
+            acc.y = __fmaf_rn(cyy, sy, acc.y);
             a1[r] = pk(acc.x, acc.y);
         }
     });

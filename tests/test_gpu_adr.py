@@ -106,3 +106,62 @@ def test_adr_rejects_modulus_field(pd):
     with pytest.raises(pd.PDError) as e:
         pd.pd_adr_solve(g.handle, b, torch.zeros_like(b), 1e-8, 10)
     assert e.value.code == pd.PD_ERR_INVALID
+
+
+# --------------------------------------------------------------------------- mixed precision
+
+@pytest.mark.parametrize("method", ["stencil", "fft"])
+def test_adr_mixed_converges_like_fp64(pd, method):
+    """FP32 operator on the correction, FP64 base residual at each tenfold drop:
+    the true FP64 residual reaches rtol, in about as many updates as the FP64 iteration."""
+    n, M = (64, 64), 3
+    w = _plate(n, M, tag=5)
+    al = oracle.alpha(2, 1.0, w.delta)
+    g = pd.Grid(2, n, w.h, M, constrained=w.constrained)
+    if method == "fft":
+        g.prefer_method(pd.PD_METHOD_FFT)
+    b = torch.tensor(w.b, device="cuda")
+    u64, st64 = g.adr_solve(b, rtol=1e-8)
+    um, stm = g.adr_solve(b, rtol=1e-8, mode=pd.PD_ADR_MIXED)
+    assert stm.rel_residual <= 1e-8 and stm.outer >= 8
+    assert abs(stm.iterations - st64.iterations) <= 0.1 * st64.iterations + 20
+    P = 1 - w.constrained
+    r = w.b * P - oracle.stiffness(2, n, w.h, M, al, um.cpu().numpy(), cons=w.constrained)
+    assert np.linalg.norm(r) / np.linalg.norm(w.b * P) <= 1.05e-8
+    assert np.all(um.cpu().numpy()[w.constrained.astype(bool)] == 0)
+    assert rel_l2(um.cpu().numpy(), u64.cpu().numpy()) <= 1e-5
+
+
+def test_adr_mixed_cap_broken_bonds_surface_and_3d(pd):
+    # cap: stops with the iterate reached and the true residual of it
+    n, M = (48, 40), 3
+    w = _plate(n, M, tag=6)
+    al = oracle.alpha(2, 1.0, w.delta)
+    g = pd.Grid(2, n, w.h, M, constrained=w.constrained, surface_correction=pd.PD_SC_VOLUME)
+    seg = (10 * n[0] // 4, 10 * n[1] // 2, 10 * 3 * n[0] // 4, 10 * n[1] // 2)
+    g.break_segment(seg, 10)
+    mu = oracle.intact_mu(2, n, M)
+    oracle.prenotch(n, M, seg, 10, mu)
+    nu = oracle.surface_nu(2, n, w.h, M)
+    b = torch.tensor(w.b, device="cuda")
+    u = torch.zeros_like(b)
+    st = pd.pd_adr_solve(g.handle, b, u, 1e-12, 100, allow_not_converged=True, mode=pd.PD_ADR_MIXED)
+    assert st.iterations == 100
+    P = 1 - w.constrained
+    r = w.b * P - oracle.stiffness(2, n, w.h, M, al, u.cpu().numpy(), cons=w.constrained, mu=mu, nu=nu)
+    assert abs(np.linalg.norm(r) / np.linalg.norm(w.b * P) - st.rel_residual) <= 1e-6 * st.rel_residual
+    # converged, with the D^f and surface corrections in the operator
+    u, st = g.adr_solve(b, rtol=1e-8, mode=pd.PD_ADR_MIXED)
+    r = w.b * P - oracle.stiffness(2, n, w.h, M, al, u.cpu().numpy(), cons=w.constrained, mu=mu, nu=nu)
+    assert np.linalg.norm(r) / np.linalg.norm(w.b * P) <= 1.05e-8
+    # 3D cube under its random body force
+    c = syn.cube(12, 2)
+    al3 = oracle.alpha(3, 1.0, c.delta)
+    g3 = pd.Grid(3, c.n, c.h, c.M, constrained=c.constrained)
+    u3, st3 = g3.adr_solve(torch.tensor(c.b, device="cuda"), rtol=1e-8, mode=pd.PD_ADR_MIXED)
+    P3 = 1 - c.constrained
+    r3 = c.b * P3 - oracle.stiffness(3, c.n, c.h, c.M, al3, u3.cpu().numpy(), cons=c.constrained)
+    assert np.linalg.norm(r3) / np.linalg.norm(c.b * P3) <= 1.05e-8
+    with pytest.raises(pd.PDError) as e:
+        pd.pd_adr_solve(g3.handle, torch.tensor(c.b, device="cuda"), u3, 1e-8, 10, mode=7)
+    assert e.value.code == pd.PD_ERR_INVALID

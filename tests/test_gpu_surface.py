@@ -131,11 +131,14 @@ def test_sc_adr_iterates_match_oracle(pd):
     g = pd.Grid(2, n, h, M, constrained=cons, surface_correction=pd.PD_SC_VOLUME)
     bt = torch.tensor(b, device="cuda")
     u = torch.zeros_like(bt)
-    st = pd.pd_adr_solve(g.handle, bt, u, 1e-30, 300, allow_not_converged=True)
+    # 100 updates: with the correction the damping quotient amplifies rounding faster
+    # than without (the oracle itself moves by 1.4e-13 at 100 updates and by 2.6e-10
+    # at 300 under a 1e-16 relative change of its operator)
+    st = pd.pd_adr_solve(g.handle, bt, u, 1e-30, 100, allow_not_converged=True)
     nu = oracle.surface_nu(2, n, h, M)
     al = oracle.alpha(2, 1.0, M * h)
-    ref, it, _ = oracle.adr_solve(2, n, h, M, al, b, cons=cons, rtol=1e-30, maxit=300, nu=nu)
-    assert st.iterations == it == 300
+    ref, it, _ = oracle.adr_solve(2, n, h, M, al, b, cons=cons, rtol=1e-30, maxit=100, nu=nu)
+    assert st.iterations == it == 100
     assert rel_l2(u.cpu().numpy(), ref) <= 1e-9
     u, st = g.adr_solve(bt, rtol=1e-8)
     r = b * (1 - cons) - oracle.stiffness(2, n, h, M, al, u.cpu().numpy(), cons=cons, nu=nu)
