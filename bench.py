@@ -16,7 +16,7 @@ surface correction), the 128^3 cube, the 2D crack loop and the notched 3D
 block, and the CPU oracle timed on this host's cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
-  python bench.py --case fft2d|stencil2d_f64|stencil3d|fft3d|crack|cg|adr [--steps K] [--warmup W]
+  python bench.py --case fft2d|stencil2d_f64|stencil3d|fft3d|crack|cg|adr|adr_mixed|sc|kw3d [--steps K] [--warmup W]
 """
 from __future__ import annotations
 
@@ -41,13 +41,13 @@ BATCH = 32          # 32 fields x 2 comps x 1M nodes x 4 B = 268 MB of inputs (>
 # DRAM traffic of the dominant kernel per launch (ncu, dram__bytes_read.sum + dram__bytes_write.sum),
 # recorded with the hash of the kernel sources it was taken on; reported only while they match.
 TRAFFIC = {
-    "kernel": "k_tbt2d_tma<3>",
+    "kernel": "k_tbt2d_tma<3, pair form>",
     "sources": ["paper_2301_11828_gb300/csrc/pd_stencil2d_tma.cu", "paper_2301_11828_gb300/csrc/pd_tma2d.cuh",
                 "paper_2301_11828_gb300/csrc/pd_stencil.cuh", "paper_2301_11828_gb300/csrc/pd_reduce.cuh"],
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch on 32 fields (the ncu --set full
     # capture summarised under profiles/) divided by 32; valid while the sources hash to sha256
-    "sha256": "3c4d278d0bd56b01202dc0c635aad9eb2ccd4899eded5d8b2164136a74138784",
-    "bytes_per_field": 15484124,
+    "sha256": "9f126fb4de9e652bf5ede6dc3dfabb94c5f5c7e283eb5de0f12751babcf13aaa",
+    "bytes_per_field": 15496440,
 }
 
 
@@ -556,7 +556,7 @@ def _extras(torch, pd, syn, dev):
     return out
 
 
-CASES = ("fft2d", "stencil2d_f64", "stencil3d", "fft3d", "crack", "cg", "adr")
+CASES = ("fft2d", "stencil2d_f64", "stencil3d", "fft3d", "crack", "cg", "adr", "adr_mixed", "sc", "kw3d")
 
 
 def run_case(args):
@@ -565,7 +565,9 @@ def run_case(args):
     fft2d: K u, 1024^2 plate, M=3, FP32 FFT tiles, 8 fields.  stencil2d_f64: the same with the FP64
     stencil, 4 fields.  stencil3d / fft3d: K u on the 128^3 cube, M=3, FP32.  crack: one Verlet step
     with bond breaking on the pre-notched 512^2 plate.  cg: 64 iterations of the mixed CG on the
-    1024^2 plate (graph-replayed inner loop).  adr: 64 ADR iterations (Algorithm 1, FP64) on that plate."""
+    1024^2 plate (graph-replayed inner loop).  adr / adr_mixed: 64 ADR iterations (Algorithm 1, FP64 /
+    mixed) on that plate.  sc: K u with the surface correction, 1024^2, FP32, 8 fields.  kw3d: one Verlet
+    step on the notched 201x101x9 block."""
     import numpy as np
     import torch
     import paper_2301_11828_gb300 as pd
@@ -601,16 +603,32 @@ def run_case(args):
         u = torch.zeros((2,) + lay.shape, dtype=torch.float64, device=dev)
         v = vpt.clone()
         step, units = (lambda: g.step(u, v, None, nsteps=1, dt=2.99e-3, v_prescribed=vpt)), 2 * w.N
-    elif case == "adr":
+    elif case in ("adr", "adr_mixed"):
         w = syn.large_plate(3)
         g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
         b = torch.tensor(w.b, device=dev)
         u = torch.zeros_like(b)
+        mode = pd.PD_ADR_F64 if case == "adr" else pd.PD_ADR_MIXED
 
         def step():
             u.zero_()
-            pd.pd_adr_solve(g.handle, b, u, 1e-30, 64, allow_not_converged=True)
+            pd.pd_adr_solve(g.handle, b, u, 1e-30, 64, allow_not_converged=True, mode=mode)
         units = 64
+    elif case == "sc":
+        w = syn.large_plate(3)
+        g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained, surface_correction=pd.PD_SC_VOLUME)
+        U = torch.rand((8, 2, NSIDE, NSIDE), dtype=torch.float32, device=dev) * 2 - 1
+        O = torch.empty_like(U)
+        step, units = (lambda: g.matvec(U, O, flags=pd.PD_METHOD_STENCIL)), 8 * 2 * w.N
+    elif case == "kw3d":
+        w = syn.kw_block(201, 101, 9, 3)
+        g = pd.Grid(3, w.n, w.h, w.M, constrained=w.constrained, s0=w.s0)
+        for seg in w.extra["notches"]:
+            g.break_segment(seg, w.extra["notch_den"])
+        vpt = torch.tensor(w.extra["v_prescribed"], device=dev)
+        u = torch.zeros_like(vpt)
+        v = vpt.clone()
+        step, units = (lambda: g.step(u, v, None, nsteps=1, dt=w.extra["dt"], v_prescribed=vpt)), 3 * w.N
     elif case == "cg":
         w = syn.large_plate(3)
         g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)

@@ -72,6 +72,8 @@ struct AdrWs {
 
 struct Dens {
     double d[3];
+    // component c without a dynamically indexed copy of the kernel parameter in local memory
+    __host__ __device__ double at(int c) const { return c == 0 ? d[0] : (c == 1 ? d[1] : d[2]); }
 };
 
 __device__ __forceinline__ bool last_block(unsigned int *retire)
@@ -122,7 +124,7 @@ k_adr_first(double *u, double *v, const double *__restrict__ q, const double *__
     for (int c = 0; c < dim; ++c)
         for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
             const int64_t i = c * N + p;
-            const double vi = (pb[i] - q[i]) / D.d[c] / 2.0;
+            const double vi = (pb[i] - q[i]) / D.at(c) / 2.0;
             v[i] = vi;
             u[i] += vi;
         }
@@ -141,7 +143,7 @@ k_adr_reduce(const double *__restrict__ u, const double *__restrict__ v, const d
     if (s_done) return;
     double a_rr = 0.0, a_num = 0.0, a_den = 0.0;
     for (int c = 0; c < dim; ++c) {
-        const double Dc = D.d[c];
+        const double Dc = D.at(c);
         for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
             const int64_t i = c * N + p;
             const double qi = q[i];
@@ -196,7 +198,7 @@ k_adr_update(double *u, double *v, const double *__restrict__ q, const double *_
     if (s_done) return;
     const double c = s_c, a = 2.0 - c, e = 1.0 / (2.0 + c);
     for (int cc = 0; cc < dim; ++cc) {
-        const double g = 2.0 * invD.d[cc];
+        const double g = 2.0 * invD.at(cc);
         for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
             const int64_t i = cc * N + p;
             const double vi = (a * v[i] + (pb[i] - q[i]) * g) * e;
@@ -229,6 +231,27 @@ k_adr_zero_constrained(double *u, const uint8_t *__restrict__ cons, int64_t N, i
 // without projection (the fast interior path of the FP32 stencil);
 // constrained components are masked here instead.
 
+// Vector access for the mixed kernels: when N is a multiple of 4 every component
+// plane starts on a 16-byte boundary (the workspace vectors are 256-byte
+// aligned), so nodes are taken four at a time (float4, and uchar4 of the
+// constraint bytes); otherwise one at a time.
+template <typename F>
+__device__ __forceinline__ void adrm_for_each(int64_t N, int dim, F &&f)
+{
+    const int64_t t0 = (int64_t)blockIdx.x * kBlk + threadIdx.x, st = (int64_t)gridDim.x * kBlk;
+    if ((N & 3) == 0) {
+        const int64_t nq = N >> 2;
+        for (int c = 0; c < dim; ++c)
+            for (int64_t j = t0; j < nq; j += st) f(c, j, true);
+    } else {
+        for (int c = 0; c < dim; ++c)
+            for (int64_t p = t0; p < N; p += st) f(c, p, false);
+    }
+}
+
+__device__ __forceinline__ float4 ld4(const float *a, int64_t i4) { return reinterpret_cast<const float4 *>(a)[i4]; }
+__device__ __forceinline__ void st4(float *a, int64_t i4, float4 v) { reinterpret_cast<float4 *>(a)[i4] = v; }
+
 // r.r (estimated), u^T K1 u, u^T u at iterate n with q^n = q^(n-1) + w, K1_ii = w_i / (D v_i),
 // u = u_base + d; the last block forms c and the flag.
 __global__ void __launch_bounds__(kBlk)
@@ -242,25 +265,42 @@ k_adrm_reduce(const float *__restrict__ d, const float *__restrict__ ub, const f
     __syncthreads();
     if (s_done) return;
     // u^T K1 u sums terms of both signs and of very different sizes (small velocities give
-    // large quotients) that largely cancel: that sum runs in FP64, the positive ones in FP32
-    float a_rr = 0.f, a_den = 0.f;
-    double a_num = 0.0;
-    for (int c = 0; c < dim; ++c) {
-        const float Dc = (float)D.d[c];
-        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
-            const int64_t i = c * N + p;
-            const bool fixed = cons && ((cons[p] >> c) & 1);
-            const float wi = w[i];
-            const float r = fixed ? 0.f : rb[i] - (q[i] + wi);
-            a_rr = __fmaf_rn(r, r, a_rr);
-            const float ui = ub[i] + d[i], vi = v[i];
-            // velocities below 1e-30 are taken as zero (keeps the quotient finite in FP32)
-            if (!fixed && fabsf(vi) > 1e-30f) a_num += (double)(ui * (wi / (Dc * vi)) * ui);
-            a_den = __fmaf_rn(ui, ui, a_den);
+    // large quotients) that largely cancel: that sum is compensated (Neumaier: the rounding
+    // error of every add is kept in n_lo), the positive ones are plain FP32.  The quotient
+    // only steers the damping, so the fast FP32 divide serves.
+    float a_rr = 0.f, a_den = 0.f, n_hi = 0.f, n_lo = 0.f;
+    auto one = [&](bool fixed, float wi, float qi, float rbi, float ubi, float di, float vi, float Dc) {
+        const float r = fixed ? 0.f : rbi - (qi + wi);
+        a_rr = __fmaf_rn(r, r, a_rr);
+        const float ui = ubi + di;
+        // velocities below 1e-30 are taken as zero (keeps the quotient finite in FP32)
+        if (!fixed && fabsf(vi) > 1e-30f) {
+            const float x = ui * __fdividef(wi, Dc * vi) * ui;
+            const float t = n_hi + x;
+            n_lo += (fabsf(n_hi) >= fabsf(x)) ? (n_hi - t) + x : (x - t) + n_hi;
+            n_hi = t;
         }
-    }
+        a_den = __fmaf_rn(ui, ui, a_den);
+    };
+    adrm_for_each(N, dim, [&](int c, int64_t k, bool vec) {
+        const float Dc = (float)D.at(c);
+        if (vec) {
+            const int64_t i4 = c * (N >> 2) + k;
+            const float4 w4 = ld4(w, i4), q4 = ld4(q, i4), r4 = ld4(rb, i4), u4 = ld4(ub, i4), d4 = ld4(d, i4),
+                         v4 = ld4(v, i4);
+            const uchar4 m4 = cons ? reinterpret_cast<const uchar4 *>(cons)[k] : make_uchar4(0, 0, 0, 0);
+            one((m4.x >> c) & 1, w4.x, q4.x, r4.x, u4.x, d4.x, v4.x, Dc);
+            one((m4.y >> c) & 1, w4.y, q4.y, r4.y, u4.y, d4.y, v4.y, Dc);
+            one((m4.z >> c) & 1, w4.z, q4.z, r4.z, u4.z, d4.z, v4.z, Dc);
+            one((m4.w >> c) & 1, w4.w, q4.w, r4.w, u4.w, d4.w, v4.w, Dc);
+        } else {
+            const int64_t i = c * N + k;
+            one(cons && ((cons[k] >> c) & 1), w[i], q[i], rb[i], ub[i], d[i], v[i], Dc);
+        }
+    });
     const int nb = gridDim.x;
-    const double s0 = block_sum(a_rr, red), s1 = block_sum(a_num, red), s2 = block_sum(a_den, red);
+    const double s0 = block_sum(a_rr, red), s1 = block_sum((double)n_hi + (double)n_lo, red),
+                 s2 = block_sum(a_den, red);
     if (threadIdx.x == 0) {
         partial[blockIdx.x] = s0;
         partial[nb + blockIdx.x] = s1;
@@ -303,20 +343,35 @@ k_adrm_update(float *d, float *dlo, float *v, float *q, const float *__restrict_
     __syncthreads();
     if (s_done) return;
     const float a = (float)(2.0 - s_c), e = (float)(1.0 / (2.0 + s_c));
-    for (int cc = 0; cc < dim; ++cc) {
-        const float g = (float)(2.0 * invD.d[cc]);
-        for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
-            if (cons && ((cons[p] >> cc) & 1)) continue;
-            const int64_t i = cc * N + p;
-            const float qn = q[i] + w[i];
-            q[i] = qn;
-            const float vi = (a * v[i] + (rb[i] - qn) * g) * e;
-            v[i] = vi;
-            const float dh = d[i], sum = dh + vi, bp = sum - dh;   // two-sum of Knuth
-            d[i] = sum;
-            dlo[i] += (dh - (sum - bp)) + (vi - bp);
+    // one node: returns false for a constrained component (left untouched: v = d = 0 there)
+    auto one = [&](bool fixed, float &qi, float wi, float rbi, float &vi, float &di, float &dli, float g) {
+        if (fixed) return;
+        qi += wi;
+        vi = (a * vi + (rbi - qi) * g) * e;
+        const float dh = di, sum = dh + vi, bp = sum - dh;   // two-sum of Knuth
+        di = sum;
+        dli += (dh - (sum - bp)) + (vi - bp);
+    };
+    adrm_for_each(N, dim, [&](int cc, int64_t k, bool vec) {
+        const float g = (float)(2.0 * invD.at(cc));
+        if (vec) {
+            const int64_t i4 = cc * (N >> 2) + k;
+            const uchar4 m4 = cons ? reinterpret_cast<const uchar4 *>(cons)[k] : make_uchar4(0, 0, 0, 0);
+            float4 q4 = ld4(q, i4), v4 = ld4(v, i4), d4 = ld4(d, i4), l4 = ld4(dlo, i4);
+            const float4 w4 = ld4(w, i4), r4 = ld4(rb, i4);
+            one((m4.x >> cc) & 1, q4.x, w4.x, r4.x, v4.x, d4.x, l4.x, g);
+            one((m4.y >> cc) & 1, q4.y, w4.y, r4.y, v4.y, d4.y, l4.y, g);
+            one((m4.z >> cc) & 1, q4.z, w4.z, r4.z, v4.z, d4.z, l4.z, g);
+            one((m4.w >> cc) & 1, q4.w, w4.w, r4.w, v4.w, d4.w, l4.w, g);
+            st4(q, i4, q4);
+            st4(v, i4, v4);
+            st4(d, i4, d4);
+            st4(dlo, i4, l4);
+        } else {
+            const int64_t i = cc * N + k;
+            one(cons && ((cons[k] >> cc) & 1), q[i], w[i], rb[i], v[i], d[i], dlo[i], g);
         }
-    }
+    });
 }
 
 // First half step from the base: v = r_base / (2 D), d = v, and the FP32 copy of the base.
@@ -325,7 +380,7 @@ k_adrm_first(float *d, float *dlo, float *v, float *ub, const float *__restrict_
              int64_t N, int dim, Dens invD)
 {
     for (int c = 0; c < dim; ++c) {
-        const float g = (float)(0.5 * invD.d[c]);
+        const float g = (float)(0.5 * invD.at(c));
         for (int64_t p = (int64_t)blockIdx.x * kBlk + threadIdx.x; p < N; p += (int64_t)gridDim.x * kBlk) {
             const int64_t i = c * N + p;
             const float vi = rb[i] * g;

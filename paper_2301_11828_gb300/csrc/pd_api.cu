@@ -351,6 +351,10 @@ int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s
     if (rc) return rc;
     g->auto_choice[0] = g->auto_choice[1] = 0;
     ++g->op_stamp;
+    if (g->sc) {   // its FP32 copy of the unit-modulus blocks follows the thickness
+        rc = surface_set(g, g->sc);
+        if (rc) return rc;
+    }
     if (g->d_sym3_32) {
         rc = fft3_prepare(g);
         if (rc) return rc;

@@ -79,7 +79,10 @@ __device__ __forceinline__ int plate_of_tile(const PlateDesc *d, int np, int t)
     return lo;
 }
 
-// One tile of K p for plate desc (TBT pair form, horizon M, R rows per thread).
+// One tile of K p for plate desc (TBT form, horizon M, R rows per thread).  FP32
+// sums the differences (u~_{p+o} - u_p) + (u~_{p-o} - u_p) (error relative to
+// |K p| for smooth directions, then K p = (Kd_p - Kd_int) p_p - sum), FP64 the
+// pairs u~_{p+o} + u~_{p-o} (K p = Kd_p p_p - sum).
 template <typename T, int M, int R>
 __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const T *__restrict__ in, T *__restrict__ out,
                                        int x0, int y0, T *s_x, T *s_y)
@@ -106,9 +109,15 @@ __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const 
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const T *colx = s_x + (ty * R) * SX + tx + M;
     const T *coly = s_y + (ty * R) * SX + tx + M;
-    T ax[R], ay[R];
+    constexpr bool DIFF = sizeof(T) == 4;
+    T ax[R], ay[R], ctx[R], cty[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) { ax[r] = T(0); ay[r] = T(0); }
+    for (int r = 0; r < R; ++r) {
+        ax[r] = T(0);
+        ay[r] = T(0);
+        ctx[r] = DIFF ? colx[(r + M) * SX] : T(0);   // the outputs' own values
+        cty[r] = DIFF ? coly[(r + M) * SX] : T(0);
+    }
     static_for<1, M + 1>([&](auto OX) {
         constexpr int ox = decltype(OX)::value;
         constexpr int My = isqrt_c(M * M - ox * ox);
@@ -126,11 +135,13 @@ __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const 
             const T cxx = coef[3 * pi], cxy = coef[3 * pi + 1], cyy = coef[3 * pi + 2];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const T sx = px[r + M + oy] + mx[r + M - oy];
+                const T sx = DIFF ? (px[r + M + oy] - ctx[r]) + (mx[r + M - oy] - ctx[r])
+                                  : px[r + M + oy] + mx[r + M - oy];
                 if constexpr (oy == 0) {
                     ax[r] = dfma(cxx, sx, ax[r]);   // axis pair: c_xy = c_yy = 0 exactly
                 } else {
-                    const T sy = py[r + M + oy] + my[r + M - oy];
+                    const T sy = DIFF ? (py[r + M + oy] - cty[r]) + (my[r + M - oy] - cty[r])
+                                      : py[r + M + oy] + my[r + M - oy];
                     ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
                     ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
                 }
@@ -148,7 +159,11 @@ __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const 
         constexpr int pi = pair_index2(M, 0, oy);
         const T cyy = coef[3 * pi + 2];   // axis pair: c_xx = c_xy = 0 exactly
 #pragma unroll
-        for (int r = 0; r < R; ++r) ay[r] = dfma(cyy, cy[r + M + oy] + cy[r + M - oy], ay[r]);
+        for (int r = 0; r < R; ++r) {
+            const T sy = DIFF ? (cy[r + M + oy] - cy[r + M]) + (cy[r + M - oy] - cy[r + M])
+                              : cy[r + M + oy] + cy[r + M - oy];
+            ay[r] = dfma(cyy, sy, ay[r]);
+        }
     });
     const T *kd = (sizeof(T) == 4) ? (const T *)d.kd32 : (const T *)d.kd64;
     T dot = T(0);
@@ -163,9 +178,11 @@ __device__ __forceinline__ T tile_body(const PlateDesc &d, const T *coef, const 
             const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
             if (a0 != M || a1 != M || b0 != M || b1 != M) {
                 const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
-                kxx = kd[3 * cls];
-                kxy = kd[3 * cls + 1];
-                kyy = kd[3 * cls + 2];
+                kxx = kd[3 * cls] - (DIFF ? kxx : T(0));
+                kxy = kd[3 * cls + 1] - (DIFF ? kxy : T(0));
+                kyy = kd[3 * cls + 2] - (DIFF ? kyy : T(0));
+            } else if (DIFF) {   // full horizon: the difference sums are the whole product
+                kxx = kxy = kyy = T(0);
             }
             T fx = dfma(kxx, upx, dfma(kxy, upy, -ax[r]));
             T fy = dfma(kxy, upx, dfma(kyy, upy, -ay[r]));
@@ -233,7 +250,7 @@ __device__ __forceinline__ double warp_sum(const double *__restrict__ a, int n)
 
 // x += alpha p, r -= alpha q over the chunk; alpha = rr / pq re-summed per plate.
 __global__ void __launch_bounds__(kBT)
-k_batch_update(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, float *x, float *r,
+k_batch_update(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, float *x, float *xlo, float *r,
                const float *__restrict__ p, const float *__restrict__ q, const double *__restrict__ tile_part,
                const double *__restrict__ rr_prev, double *rr_cur, const BatchScal *__restrict__ scal)
 {
@@ -256,7 +273,11 @@ k_batch_update(const PlateDesc *__restrict__ desc, const int *__restrict__ cplat
         const int64_t hi = min(lo + (int64_t)kChunk, d.off + L);
         float acc = 0.f;
         for (int64_t i = lo + threadIdx.x; i < hi; i += kBT) {
-            x[i] += a * p[i];
+            // the increment as a compensated sum x + xlo (two-sum of Knuth): rounding of a
+            // plain FP32 sum, amplified by K, would open a gap to the recursive residual
+            const float dx = a * p[i], xh = x[i], sum = xh + dx, bp = sum - xh;
+            x[i] = sum;
+            xlo[i] += (xh - (sum - bp)) + (dx - bp);
             const float ri = r[i] - a * q[i];
             r[i] = ri;
             acc += ri * ri;
@@ -342,7 +363,7 @@ k_batch_resid(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate
 // previous pass's |r|), which is CG with reliable updates; 0 starts a new direction.
 __global__ void __launch_bounds__(kBT)
 k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, float *r32, float *p32,
-              float *x32, const double *__restrict__ r64, double *rr, const BatchScal *__restrict__ scal)
+              float *x32, float *xlo32, const double *__restrict__ r64, double *rr, const BatchScal *__restrict__ scal)
 {
     __shared__ double red[kBT / 32];
     const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
@@ -360,6 +381,7 @@ k_batch_start(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate
             r32[i] = v;
             p32[i] = (ps != 0.f) ? v + ps * p32[i] : v;
             x32[i] = 0.f;
+            xlo32[i] = 0.f;
             acc += v * v;
         }
         const double s = block_sum(acc, red);
@@ -390,7 +412,8 @@ k_batch_project(const PlateDesc *__restrict__ desc, const int *__restrict__ cpla
 // u += |r| x on plates that ran an inner solve this pass
 __global__ void __launch_bounds__(kBT)
 k_batch_correct(const PlateDesc *__restrict__ desc, const int *__restrict__ cplate, int nch, const BatchRange *__restrict__ range, double *u,
-                const float *__restrict__ x32, const BatchScal *__restrict__ scal, const int *__restrict__ active)
+                const float *__restrict__ x32, const float *__restrict__ xlo32, const BatchScal *__restrict__ scal,
+                const int *__restrict__ active)
 {
     const int c0 = range ? range->chunk_begin : 0, c1 = range ? range->chunk_end : nch;
     for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
@@ -400,7 +423,7 @@ k_batch_correct(const PlateDesc *__restrict__ desc, const int *__restrict__ cpla
         const double rn = scal[pl].rn;
         const int64_t lo = d.off + (int64_t)(c - d.chunk_base) * kChunk;
         const int64_t hi = min(lo + (int64_t)kChunk, d.off + 2 * d.N);
-        for (int64_t i = lo + threadIdx.x; i < hi; i += kBT) u[i] += rn * (double)x32[i];
+        for (int64_t i = lo + threadIdx.x; i < hi; i += kBT) u[i] += rn * ((double)x32[i] + (double)xlo32[i]);
     }
 }
 
@@ -423,7 +446,7 @@ struct pd_batch {
     std::vector<BatchRange> ranges;     // per group
     void *ws = nullptr;
     double *u64, *b64, *r64, *q64, *part_t, *rrA, *rrB, *part_c;
-    float *r32, *p32, *q32, *x32;
+    float *r32, *p32, *q32, *x32, *xlo32;
     cudaStream_t cap = nullptr;
     std::vector<cudaStream_t> gstream;  // per group: its passes run concurrently with the others
     std::vector<cudaEvent_t> gevent;    // per group: completion of the last work the host waits for
@@ -564,7 +587,7 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
     const int64_t L = bt->total;
     const int64_t nt = std::max(bt->ntiles32, bt->ntiles64);
     const size_t need = sizeof(double) * (4 * (size_t)L + (size_t)nt + 3 * (size_t)bt->nch) +
-                        sizeof(float) * 4 * (size_t)L + 16 * 256;
+                        sizeof(float) * 5 * (size_t)L + 17 * 256;
     if (cudaMalloc(&bt->ws, need) != cudaSuccess) return bail(PD_ERR_OOM, "batch workspace");
     char *c = (char *)bt->ws;
     auto take = [&](size_t n) { char *q = c; c += (n + 255) & ~(size_t)255; return q; };
@@ -580,6 +603,7 @@ int pd_batch_create(pd_grid *const *grids, int count, pd_batch **out)
     bt->p32 = (float *)take(sizeof(float) * L);
     bt->q32 = (float *)take(sizeof(float) * L);
     bt->x32 = (float *)take(sizeof(float) * L);
+    bt->xlo32 = (float *)take(sizeof(float) * L);
     if (cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking) != cudaSuccess)
         return bail(PD_ERR_CUDA, "capture stream");
     int dev = 0, sms = 0;
@@ -622,8 +646,8 @@ int batch_two_iterations(pd_batch *bt, const BatchRange *rg, cudaStream_t s)
         double *cur = (k == 0) ? bt->rrA : bt->rrB;
         k_batch_matvec<float><<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->np, bt->ntiles32, bt->p32, bt->q32,
                                                          bt->part_t, bt->d_scal, rg);
-        k_batch_update<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, rg, bt->x32, bt->r32, bt->p32,
-                                                  bt->q32, bt->part_t, prev, cur, bt->d_scal);
+        k_batch_update<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, rg, bt->x32, bt->xlo32, bt->r32,
+                                                  bt->p32, bt->q32, bt->part_t, prev, cur, bt->d_scal);
         k_batch_pupdate<<<bt->blocks, kBT, 0, s>>>(bt->d_desc32, bt->d_cplate, bt->nch, rg, bt->p32, bt->r32, prev, cur,
                                                    bt->d_scal);
     }
@@ -794,7 +818,8 @@ extern "C" int pd_batch_cg_solve(pd_batch *bt, const double *const *b, double *c
                 PD_CUDA(cudaMemcpyAsync(bt->d_active + R.first, h_active + R.first, sizeof(int) * (R.last - R.first),
                                         cudaMemcpyHostToDevice, st));
                 k_batch_start<<<bt->blocks, kBT, 0, st>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range + gi,
-                                                          bt->r32, bt->p32, bt->x32, bt->r64, bt->rrB, bt->d_scal);
+                                                          bt->r32, bt->p32, bt->x32, bt->xlo32, bt->r64, bt->rrB,
+                                                          bt->d_scal);
                 PD_CUDA(cudaGetLastError());
                 R.issued = 0;
                 int rc = issue_inner(gi);
@@ -816,7 +841,7 @@ extern "C" int pd_batch_cg_solve(pd_batch *bt, const double *const *b, double *c
                 R.group_iters += mx;
                 ++R.pass;
                 k_batch_correct<<<bt->blocks, kBT, 0, st>>>(bt->d_desc32, bt->d_cplate, bt->nch, bt->d_range + gi,
-                                                            bt->u64, bt->x32, bt->d_scal, bt->d_active);
+                                                            bt->u64, bt->x32, bt->xlo32, bt->d_scal, bt->d_active);
                 PD_CUDA(cudaGetLastError());
                 int rc = issue_resid(gi);
                 if (rc) return rc;

@@ -128,6 +128,8 @@ struct pd_grid {
     int32_t *d_band = nullptr;
     int64_t band_n = 0;
     unsigned long long *d_sc_rowmax = nullptr;
+    float *d_sc_f32 = nullptr;     // FP32 nu table [sc_ncls], then unit-modulus bond blocks [nnb][ncoef]
+    int sc_ncls = 0;
     int64_t op_stamp = 0;      // bumped whenever the operator changes (material, bond state)
 };
 

@@ -33,13 +33,15 @@ namespace {
 
 constexpr int kBlk = 256;
 
-// out -= scale * sum_q mu (v - 1) C (u_q - u_p) on every band node, every field.
-// coef: bond blocks at the grid modulus, or at E = 1 when E (per node) is given.
-template <typename T, int DIM>
+// out -= scale * sum_q mu (v - 1) C (u_q - u_p) on every band node; one field
+// per grid row.  Arithmetic in C (the field's precision: FP64 is a slow pipe
+// on this GPU and FP32 outputs need no more); coef: unit-modulus bond blocks
+// in C, times Econst, or times (E_p + E_q) / 2 when E (per node) is given.
+template <typename T, typename C, int DIM>
 __global__ void __launch_bounds__(kBlk)
 k_sc_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int ny, int nz, int M, int nnb,
             const int32_t *__restrict__ band, int64_t nband, const int32_t *__restrict__ off,
-            const double *__restrict__ coef, const double *__restrict__ E, const double *__restrict__ nu_tab,
+            const C *__restrict__ coef, C Econst, const double *__restrict__ E, const C *__restrict__ nu_tab,
             const uint32_t *__restrict__ mask, int use_mu, const uint8_t *__restrict__ cons, int project,
             double scale)
 {
@@ -51,34 +53,34 @@ k_sc_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int
     for (int64_t w = warp; w < nband; w += nwarps) {
         const int p = band[w];   // fewer than 2^31 nodes: 32-bit index arithmetic
         const int i = p % nx, j = (p / nx) % ny, k = p / (nx * ny);
-        const double nu_p = nu_tab[nu_class(i, j, k, nx, ny, nz, M, DIM)];
-        const double E_p = E ? E[p] : 1.0;
+        const C nu_p = nu_tab[nu_class(i, j, k, nx, ny, nz, M, DIM)];
+        const C E_p = E ? (C)E[p] : C(0);
         const uint8_t cm = project ? cons[p] : 0;
-        double up[DIM], acc[DIM];
+        C up[DIM], acc[DIM];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
-            up[c] = ((cm >> c) & 1) ? 0.0 : (double)ub[c * N + p];
-            acc[c] = 0.0;
+            up[c] = ((cm >> c) & 1) ? C(0) : (C)ub[c * N + p];
+            acc[c] = C(0);
         }
         for (int kk = lane; kk < nnb; kk += 32) {
             const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1], qk = k + off[3 * kk + 2];
             if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
             if (use_mu && !((mask[(int64_t)(kk >> 5) * N + p] >> (kk & 31)) & 1u)) continue;
-            const double nu_q = nu_tab[nu_class(qi, qj, qk, nx, ny, nz, M, DIM)];
-            double wgt = 0.5 * (nu_p + nu_q) - 1.0;
-            if (wgt == 0.0) continue;
+            const C nu_q = nu_tab[nu_class(qi, qj, qk, nx, ny, nz, M, DIM)];
+            C wgt = C(0.5) * (nu_p + nu_q) - C(1);
+            if (wgt == C(0)) continue;
             const int q = (qk * ny + qj) * nx + qi;
-            if (E) wgt *= 0.5 * (E_p + E[q]);
+            wgt *= E ? C(0.5) * (E_p + (C)E[q]) : Econst;
             const uint8_t qm = project ? cons[q] : 0;
-            double d[DIM];
+            C d[DIM];
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) d[c] = (((qm >> c) & 1) ? 0.0 : (double)ub[c * N + q]) - up[c];
+            for (int c = 0; c < DIM; ++c) d[c] = (((qm >> c) & 1) ? C(0) : (C)ub[c * N + q]) - up[c];
             if (DIM == 2) {
-                const double *cf = coef + 3 * kk;
+                const C *cf = coef + 3 * kk;
                 acc[0] += wgt * (cf[0] * d[0] + cf[1] * d[1]);
                 acc[1] += wgt * (cf[1] * d[0] + cf[2] * d[DIM - 1]);
             } else {
-                const double *cf = coef + 6 * kk;
+                const C *cf = coef + 6 * kk;
                 acc[0] += wgt * (cf[0] * d[0] + cf[1] * d[1] + cf[2] * d[DIM - 1]);
                 acc[1] += wgt * (cf[1] * d[0] + cf[3] * d[1] + cf[4] * d[DIM - 1]);
                 acc[DIM - 1] += wgt * (cf[2] * d[0] + cf[4] * d[1] + cf[5] * d[DIM - 1]);
@@ -91,7 +93,7 @@ k_sc_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int
         if (lane == 0) {
 #pragma unroll
             for (int c = 0; c < DIM; ++c)
-                if (!((cm >> c) & 1)) ob[c * N + p] = (T)((double)ob[c * N + p] - scale * acc[c]);
+                if (!((cm >> c) & 1)) ob[c * N + p] = (T)((C)ob[c * N + p] - (C)scale * acc[c]);
         }
     }
 }
@@ -168,6 +170,7 @@ int surface_set(pd_grid *g, int mode)
     g->d_nu_tab = nullptr;
     g->d_band = nullptr;
     g->d_sc_rowmax = nullptr;
+    g->d_sc_f32 = nullptr;
     g->band_n = 0;
     g->sc = 0;
     ++g->op_stamp;
@@ -218,10 +221,19 @@ int surface_set(pd_grid *g, int mode)
                 for (int64_t i = hi_start; i < nx; ++i) band.push_back((int32_t)(base + i));
             }
         }
-    // the table, then three words of scratch for the row maximum
-    PD_CUDA(cudaMalloc(&g->d_nu_tab, sizeof(double) * (tab.size() + 3)));
+    // the table, three words of scratch for the row maximum, then FP32 copies of the
+    // table and of the unit-modulus bond blocks for the FP32 gather
+    const int nc = ncoef(dim);
+    const size_t nf = tab.size() + (size_t)g->nnb * nc;
+    PD_CUDA(cudaMalloc(&g->d_nu_tab, sizeof(double) * (tab.size() + 3) + sizeof(float) * nf));
     PD_CUDA(cudaMemcpy(g->d_nu_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
     g->d_sc_rowmax = (unsigned long long *)(g->d_nu_tab + tab.size());
+    std::vector<float> f32(nf);
+    for (size_t t = 0; t < tab.size(); ++t) f32[t] = (float)tab[t];
+    for (size_t t = 0; t < (size_t)g->nnb * nc; ++t) f32[tab.size() + t] = (float)g->coef1[t];
+    g->d_sc_f32 = (float *)(g->d_nu_tab + tab.size() + 3);
+    g->sc_ncls = (int)tab.size();
+    PD_CUDA(cudaMemcpy(g->d_sc_f32, f32.data(), sizeof(float) * nf, cudaMemcpyHostToDevice));
     if (!band.empty()) {
         PD_CUDA(cudaMalloc(&g->d_band, sizeof(int32_t) * band.size()));
         PD_CUDA(cudaMemcpy(g->d_band, band.data(), sizeof(int32_t) * band.size(), cudaMemcpyHostToDevice));
@@ -239,16 +251,16 @@ int launch_sc_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t bat
     const int64_t per_field = std::max<int64_t>(1, std::min<int64_t>((g->band_n + 7) / 8, 152 * 8 / batch + 1));
     const dim3 blocks((unsigned)per_field, (unsigned)batch);   // 8 warps per block, one node per warp
     const int nx = (int)g->n[0], ny = (int)g->n[1], nz = (int)g->n[2];
-    const double *coef = g->has_E ? g->d_coef1 : g->d_coef;
     const double *E = g->has_E ? g->d_E : nullptr;
-#define PD_SC(T, D)                                                                                              \
-    k_sc_gather<T, D><<<blocks, kBlk, 0, s>>>((const T *)u, (T *)out, g->N, nx, ny, nz, g->M, g->nnb, g->d_band,  \
-                                               g->band_n, g->d_off, coef, E, g->d_nu_tab, g->d_mask,              \
-                                               use_mu ? 1 : 0, g->d_cons, project ? 1 : 0, scale)
+    const float *nu32 = g->d_sc_f32, *coef32 = g->d_sc_f32 + g->sc_ncls;
+#define PD_SC(T, C, D, COEF, NU)                                                                                    \
+    k_sc_gather<T, C, D><<<blocks, kBlk, 0, s>>>((const T *)u, (T *)out, g->N, nx, ny, nz, g->M, g->nnb, g->d_band,   \
+                                                  g->band_n, g->d_off, COEF, (C)g->E, E, NU, g->d_mask,               \
+                                                  use_mu ? 1 : 0, g->d_cons, project ? 1 : 0, scale)
     if (g->dim == 2) {
-        if (f64) PD_SC(double, 2); else PD_SC(float, 2);
+        if (f64) PD_SC(double, double, 2, g->d_coef1, g->d_nu_tab); else PD_SC(float, float, 2, coef32, nu32);
     } else {
-        if (f64) PD_SC(double, 3); else PD_SC(float, 3);
+        if (f64) PD_SC(double, double, 3, g->d_coef1, g->d_nu_tab); else PD_SC(float, float, 3, coef32, nu32);
     }
 #undef PD_SC
     PD_CUDA(cudaGetLastError());
