@@ -54,37 +54,37 @@ def lib():
             L = ctypes.CDLL(build())
             i64p = ctypes.POINTER(ctypes.c_int64)
             dp = ctypes.c_void_p
-            L.or_offsets.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int]
+            L.or_offsets.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int]
             L.or_offsets.restype = ctypes.c_int
             L.or_lambda.argtypes = [ctypes.c_double] * 3
             L.or_lambda.restype = ctypes.c_double
             L.or_alpha.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.or_alpha.restype = ctypes.c_double
-            L.or_bond_block.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp]
-            L.or_force.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+            L.or_bond_block.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            L.or_force.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    dp, dp, dp, dp, dp]
             L.or_force.restype = ctypes.c_int
-            L.or_stiffness.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+            L.or_stiffness.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        dp, dp, dp, dp, dp, dp]
             L.or_stiffness.restype = ctypes.c_int
-            L.or_cg.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+            L.or_cg.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 dp, dp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_double)]
             L.or_cg.restype = ctypes.c_int
-            L.or_break.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp]
+            L.or_break.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
             L.or_break.restype = ctypes.c_int64
-            L.or_prenotch.argtypes = [ctypes.c_int, i64p, ctypes.c_int, i64p, ctypes.c_int64, dp]
+            L.or_prenotch.argtypes = [ctypes.c_int, i64p, ctypes.c_double, i64p, ctypes.c_int64, dp]
             L.or_prenotch.restype = ctypes.c_int64
-            L.or_vv.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double, dp,
+            L.or_vv.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
                                 dp, dp, ctypes.c_double, dp, dp, dp, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_int, dp, dp]
             L.or_vv.restype = ctypes.c_int64
-            L.or_grad_modulus.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+            L.or_grad_modulus.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           dp, dp, dp, dp, dp]
             L.or_grad_modulus.restype = ctypes.c_int
-            L.or_surface_nu.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, dp]
+            L.or_surface_nu.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, dp]
             L.or_surface_nu.restype = ctypes.c_int
-            L.or_row_abs_max.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+            L.or_row_abs_max.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          dp, dp]
             L.or_row_abs_max.restype = ctypes.c_int
             L.or_threads.argtypes = []
@@ -117,8 +117,14 @@ def _u8(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
 
 
-def offsets(dim: int, M: int) -> np.ndarray:
-    """Neighbour offsets o != 0 with |o|^2 <= M^2 (Eq. band), int32 [nnb][3]."""
+def radius(M) -> int:
+    """Integer radius of the offset disk for m = delta / h (= m when m is an integer)."""
+    return int(math.ceil(float(M) - 1e-9))
+
+
+def offsets(dim: int, M) -> np.ndarray:
+    """Neighbour offsets o != 0 with |o| <= m = M (Eq. band; M = delta / h, any real >= 1),
+    int32 [nnb][3]."""
     buf = np.zeros((16384, 3), dtype=np.int32)
     cnt = lib().or_offsets(dim, M, _ptr(buf), 16384)
     assert cnt > 0
@@ -253,6 +259,13 @@ def row_abs_max(dim, n, h, M, alpha_, nu=None) -> np.ndarray:
     return out[:dim]
 
 
+def critical_stretch(G0: float, E: float, delta: float, plane: str = "stress") -> float:
+    """Critical bond stretch of Eq. fra:s1 from the energy release rate G0."""
+    if plane == "stress":
+        return math.sqrt(4.0 * math.pi * G0 / (9.0 * E * delta))
+    return math.sqrt(5.0 * math.pi * G0 / (12.0 * E * delta))
+
+
 def intact_mu(dim, n, M) -> np.ndarray:
     """All-intact bond state, uint8 [N][nnb]."""
     return np.ones((int(np.prod(n)), len(offsets(dim, M))), dtype=np.uint8)
@@ -326,11 +339,12 @@ def dense_matrix(dim: int, n, h: float, M: int, alpha_: float, E=None) -> np.nda
 def kernel_table(dim: int, h: float, M: int, alpha_: float) -> np.ndarray:
     """Kernel matrix / tensor of Eqs. frb:e1, frb:e4 (2D) and thm:e2, thm:e3 (3D).
 
-    Returns T[a][b][oz+M][oy+M][ox+M] (2D: T[a][b][oy+M][ox+M]) holding
-    alpha lambda h^(dim-1) o_a o_b / |o|^3 off the centre and minus the sum of
-    all others at the centre.
+    Returns T[a][b][oz+R][oy+R][ox+R] (2D: T[a][b][oy+R][ox+R]), R = radius(M), holding
+    alpha lambda h^(dim-1) o_a o_b / |o|^3 off the centre (lambda = 0 beyond
+    |o| = M = delta / h) and minus the sum of all others at the centre.
     """
-    rng_ = np.arange(-M, M + 1)
+    R = radius(M)
+    rng_ = np.arange(-R, R + 1)
     if dim == 2:
         oy, ox = np.meshgrid(rng_, rng_, indexing="ij")
         comps = [ox, oy]
@@ -344,7 +358,7 @@ def kernel_table(dim: int, h: float, M: int, alpha_: float) -> np.ndarray:
     with np.errstate(divide="ignore", invalid="ignore"):
         w = np.where(d2 > 0, alpha_ * lamv * h ** (dim - 1) / np.where(d2 > 0, r ** 3, 1.0), 0.0)
     T = np.zeros((dim, dim) + d2.shape)
-    centre = (M,) * dim
+    centre = (R,) * dim
     for a in range(dim):
         for b in range(dim):
             T[a, b] = w * comps[a] * comps[b]
@@ -367,7 +381,8 @@ def fmvm(dim: int, n, h: float, M: int, alpha_: float, u, mu=None) -> np.ndarray
     u = np.asarray(u, dtype=np.float64).reshape((dim,) + shp)
     # G: first column of the embedded circulant, K(o) at index o mod 2N (zero elsewhere)
     G = np.zeros((dim, dim) + big)
-    rng_ = np.arange(-M, M + 1)
+    R = radius(M)
+    rng_ = np.arange(-R, R + 1)
     grids = np.meshgrid(*([rng_] * dim), indexing="ij")   # axes order (z,) y, x
     idx = tuple(g % s for g, s in zip(grids, big))
     for a in range(dim):
@@ -391,7 +406,7 @@ def fmvm(dim: int, n, h: float, M: int, alpha_: float, u, mu=None) -> np.ndarray
             out |= (q[c] < 0) | (q[c] >= n[c])
         if not out.any():
             continue
-        tidx = tuple(int(o[c]) + M for c in reversed(range(dim)))
+        tidx = tuple(int(o[c]) + R for c in reversed(range(dim)))
         for a in range(dim):
             for b in range(dim):
                 f[a].reshape(-1)[out] += T[(a, b) + tidx] * u[b].reshape(-1)[out]
@@ -404,7 +419,7 @@ def fmvm(dim: int, n, h: float, M: int, alpha_: float, u, mu=None) -> np.ndarray
             if any(c[i] < 0 or c[i] >= n[i] for i in range(dim)):
                 continue
             q = int(sum(int(c[i]) * int(np.prod(n[:i])) for i in range(dim)))
-            tidx = tuple(int(o[cc]) + M for cc in reversed(range(dim)))
+            tidx = tuple(int(o[cc]) + R for cc in reversed(range(dim)))
             for a in range(dim):
                 for b in range(dim):
                     f[a].reshape(-1)[p] += T[(a, b) + tidx] * (u[b].reshape(-1)[p] - u[b].reshape(-1)[q])
@@ -418,7 +433,8 @@ def symbol(dim: int, L, h: float, M: int, alpha_: float) -> np.ndarray:
     L = [int(v) for v in L]
     big = tuple(reversed(L))
     G = np.zeros((dim, dim) + big)
-    rng_ = np.arange(-M, M + 1)
+    R = radius(M)
+    rng_ = np.arange(-R, R + 1)
     grids = np.meshgrid(*([rng_] * dim), indexing="ij")
     idx = tuple(g % s for g, s in zip(grids, big))
     for a in range(dim):

@@ -18,7 +18,8 @@
  *    p = i + Nx (j + Ny k) (Sec. 3 and Sec. 4 node numbering, 0-based);
  *  - per-node arrays are stored component-major: u[c * N + p];
  *  - the offset of a bond is o = (q - p) in grid units; the neighbour test
- *    |x_q - x_p| <= delta with delta = M h is |o|^2 <= M^2 in integers
+ *    |x_q - x_p| <= delta with delta = m h is |o|^2 <= m^2 (m = delta / h, an
+ *    integer in the paper's examples but any real >= 1 here)
  *    (Eq. band, Sec. 3.1), and the bond vector is xi = h o (Eq. frb:e1);
  *  - f = A u is the paper's internal force; the stiffness product used by the
  *    solver is K u = -A u (Eq. mat:e2 reads -A u = b on the free nodes);
@@ -37,19 +38,22 @@
 /* Neighbour set (Eq. band) and partial-volume factor (Eq. fac:e1)           */
 /* ------------------------------------------------------------------------- */
 
-/* Offsets o != 0 with |o|^2 <= M^2, in lexicographic (oz, oy, ox) order.
+/* Offsets o != 0 with |o| <= m (m = delta / h, any real >= 1: the bonds of
+ * Eq. band), in lexicographic (oz, oy, ox) order; the test is |o|^2 <= m^2 on
+ * the integer |o|^2 (a tie at |o| = m counts, as Eq. fac:e1 includes r = delta).
  * Because the set is centrally symmetric, the offset at index k and the one at
  * index (count - 1 - k) are negatives of each other.  Returns the count, or -1
  * when cap is too small. */
-int or_offsets(int dim, int M, int32_t *off, int cap)
+int or_offsets(int dim, double m, int32_t *off, int cap)
 {
     int cnt = 0;
-    int zlo = (dim == 3) ? -M : 0, zhi = (dim == 3) ? M : 0;
+    const int R = (int)ceil(m - 1e-9);
+    int zlo = (dim == 3) ? -R : 0, zhi = (dim == 3) ? R : 0;
     for (int oz = zlo; oz <= zhi; ++oz)
-        for (int oy = -M; oy <= M; ++oy)
-            for (int ox = -M; ox <= M; ++ox) {
+        for (int oy = -R; oy <= R; ++oy)
+            for (int ox = -R; ox <= R; ++ox) {
                 int d2 = ox * ox + oy * oy + oz * oz;
-                if (d2 == 0 || d2 > M * M) continue;
+                if (d2 == 0 || (double)d2 > m * m + 1e-9) continue;
                 if (cnt >= cap) return -1;
                 off[3 * cnt + 0] = ox;
                 off[3 * cnt + 1] = oy;
@@ -78,14 +82,14 @@ double or_alpha(int dim, double E, double delta, double thickness)
 
 /* Bond block lambda_q V_q C(xi) of Eqs. ker:e1 and mat:f1 for offset o:
  * c[a][b] = alpha xi_a xi_b / |xi|^3 * lambda * h^dim with xi = h o. */
-static void bond_block(int dim, const int32_t *o, double h, int M, double alpha,
+static void bond_block(int dim, const int32_t *o, double h, double m, double alpha,
                        double c[3][3])
 {
     double xi[3] = {h * o[0], h * o[1], h * o[2]};
     double r2 = 0.0;
     for (int a = 0; a < dim; ++a) r2 += xi[a] * xi[a];
     double r = sqrt(r2);
-    double lam = or_lambda(r, M * h, h);
+    double lam = or_lambda(r, m * h, h);
     double V = (dim == 2) ? h * h : h * h * h;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b)
@@ -93,10 +97,10 @@ static void bond_block(int dim, const int32_t *o, double h, int M, double alpha,
 }
 
 /* Public copy of the bond block for the tests (row-major 3x3). */
-void or_bond_block(int dim, const int32_t *o, double h, int M, double alpha, double *c9)
+void or_bond_block(int dim, const int32_t *o, double h, double m, double alpha, double *c9)
 {
     double c[3][3];
-    bond_block(dim, o, h, M, alpha, c);
+    bond_block(dim, o, h, m, alpha, c);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) c9[3 * a + b] = c[a][b];
 }
@@ -115,15 +119,15 @@ void or_bond_block(int dim, const int32_t *o, double h, int M, double alpha, dou
  * nu:    NULL, or the per-node surface-correction factors of or_surface_nu:
  *        the bond (p, q) is then scaled by v_pq = (nu_p + nu_q) / 2.
  */
-int or_force(int dim, const int64_t *n, double h, int M, double alpha,
+int or_force(int dim, const int64_t *n, double h, double m, double alpha,
              const double *E, const uint8_t *mu, const double *nu, const double *u, double *f)
 {
     int32_t off[3 * 16384];
-    int nnb = or_offsets(dim, M, off, 16384);
+    int nnb = or_offsets(dim, m, off, 16384);
     if (nnb < 0) return -1;
     double (*blk)[3][3] = malloc(sizeof(double[3][3]) * (size_t)nnb);
     if (!blk) return -2;
-    for (int k = 0; k < nnb; ++k) bond_block(dim, off + 3 * k, h, M, alpha, blk[k]);
+    for (int k = 0; k < nnb; ++k) bond_block(dim, off + 3 * k, h, m, alpha, blk[k]);
     const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
     const int64_t N = nx * ny * nz;
 
@@ -153,7 +157,7 @@ int or_force(int dim, const int64_t *n, double h, int M, double alpha,
 
 /* Stiffness product with the volume constraint: out = P K P u, K = -A, where
  * P zeroes the constrained components (cons[c * N + p] != 0). */
-int or_stiffness(int dim, const int64_t *n, double h, int M, double alpha,
+int or_stiffness(int dim, const int64_t *n, double h, double m, double alpha,
                  const double *E, const uint8_t *mu, const double *nu, const uint8_t *cons,
                  const double *u, double *out)
 {
@@ -161,7 +165,7 @@ int or_stiffness(int dim, const int64_t *n, double h, int M, double alpha,
     double *up = malloc(sizeof(double) * (size_t)(dim * N));
     if (!up) return -2;
     for (int64_t t = 0; t < dim * N; ++t) up[t] = (cons && cons[t]) ? 0.0 : u[t];
-    int rc = or_force(dim, n, h, M, alpha, E, mu, nu, up, out);
+    int rc = or_force(dim, n, h, m, alpha, E, mu, nu, up, out);
     for (int64_t t = 0; t < dim * N; ++t) out[t] = (cons && cons[t]) ? 0.0 : -out[t];
     free(up);
     return rc;
@@ -183,7 +187,7 @@ static double dot(const double *a, const double *b, int64_t len)
 /* x: in = initial guess, out = solution.  Returns the iteration count (or a
  * negative error); *relres receives ||P(b - K x)|| / ||P b|| recomputed from
  * scratch at the end. */
-int or_cg(int dim, const int64_t *n, double h, int M, double alpha, const double *E,
+int or_cg(int dim, const int64_t *n, double h, double m, double alpha, const double *E,
           const uint8_t *mu, const double *nu, const uint8_t *cons, const double *b, double *x,
           double rtol, int maxit, double *relres)
 {
@@ -199,12 +203,12 @@ int or_cg(int dim, const int64_t *n, double h, int M, double alpha, const double
     if (bnorm == 0.0) bnorm = 1.0;
     int it = 0;
     for (int restart = 0; restart < 8 && it < maxit; ++restart) {
-        or_stiffness(dim, n, h, M, alpha, E, mu, nu, cons, x, q);
+        or_stiffness(dim, n, h, m, alpha, E, mu, nu, cons, x, q);
         for (int64_t t = 0; t < L; ++t) { r[t] = pb[t] - q[t]; p[t] = r[t]; }
         double rr = dot(r, r, L);
         if (sqrt(rr) / bnorm <= rtol) break;
         for (; it < maxit; ++it) {
-            or_stiffness(dim, n, h, M, alpha, E, mu, nu, cons, p, q);
+            or_stiffness(dim, n, h, m, alpha, E, mu, nu, cons, p, q);
             double a = rr / dot(p, q, L);
             for (int64_t t = 0; t < L; ++t) { x[t] += a * p[t]; r[t] -= a * q[t]; }
             double rr_new = dot(r, r, L);
@@ -214,7 +218,7 @@ int or_cg(int dim, const int64_t *n, double h, int M, double alpha, const double
             for (int64_t t = 0; t < L; ++t) p[t] = r[t] + beta * p[t];
         }
     }
-    or_stiffness(dim, n, h, M, alpha, E, mu, nu, cons, x, q);
+    or_stiffness(dim, n, h, m, alpha, E, mu, nu, cons, x, q);
     for (int64_t t = 0; t < L; ++t) r[t] = pb[t] - q[t];
     *relres = sqrt(dot(r, r, L)) / bnorm;
     free(r); free(p); free(q); free(pb);
@@ -234,11 +238,11 @@ int or_cg(int dim, const int64_t *n, double h, int M, double alpha, const double
  * The bond breaks when s >= s0 (Eq. mu), in both directions, for good.
  * Returns the number of bonds newly broken.
  */
-int64_t or_break(int dim, const int64_t *n, double h, int M, double s0,
+int64_t or_break(int dim, const int64_t *n, double h, double m, double s0,
                  const double *u, uint8_t *mu)
 {
     int32_t off[3 * 16384];
-    int nnb = or_offsets(dim, M, off, 16384);
+    int nnb = or_offsets(dim, m, off, 16384);
     const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
     const int64_t N = nx * ny * nz;
     int64_t broken = 0;
@@ -305,10 +309,10 @@ static int seg_meet(const int64_t *p1, const int64_t *p2, const int64_t *q1, con
  * the x-y plane): a bond is cut when its projection onto the x-y plane meets
  * the segment, whatever its z extent (a bond along z alone projects to a
  * point, cut only if that point lies on the segment). */
-int64_t or_prenotch(int dim, const int64_t *n, int M, const int64_t *seg, int64_t den, uint8_t *mu)
+int64_t or_prenotch(int dim, const int64_t *n, double m, const int64_t *seg, int64_t den, uint8_t *mu)
 {
     int32_t off[3 * 16384];
-    int nnb = or_offsets(dim, M, off, 16384);
+    int nnb = or_offsets(dim, m, off, 16384);
     const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1, N = nx * ny * nz;
     int64_t A[2] = {2 * seg[0], 2 * seg[1]}, B[2] = {2 * seg[2], 2 * seg[3]};
     int64_t broken = 0;
@@ -346,14 +350,14 @@ int64_t or_prenotch(int dim, const int64_t *n, int M, const int64_t *seg, int64_
  * cons may be NULL (nothing constrained); vpres may be NULL (zero velocity).
  * Returns the number of bonds broken during the call.
  */
-int64_t or_vv(int dim, const int64_t *n, double h, int M, double alpha, const double *E,
+int64_t or_vv(int dim, const int64_t *n, double h, double m, double alpha, const double *E,
               uint8_t *mu, const double *nu, double s0, const uint8_t *cons, const double *vpres,
               const double *b, double rho, double dt, int nsteps, double *u, double *v)
 {
     const int64_t N = n[0] * n[1] * ((dim == 3) ? n[2] : 1), L = dim * N;
     double *a = malloc(sizeof(double) * L), *an = malloc(sizeof(double) * L);
     if (!a || !an) { free(a); free(an); return -2; }
-    or_force(dim, n, h, M, alpha, E, mu, nu, u, a);
+    or_force(dim, n, h, m, alpha, E, mu, nu, u, a);
     for (int64_t t = 0; t < L; ++t) a[t] = (a[t] + (b ? b[t] : 0.0)) / rho;
     int64_t broken = 0;
     for (int s = 0; s < nsteps; ++s) {
@@ -361,8 +365,8 @@ int64_t or_vv(int dim, const int64_t *n, double h, int M, double alpha, const do
             if (cons && cons[t]) u[t] += dt * (vpres ? vpres[t] : 0.0);
             else u[t] += dt * v[t] + 0.5 * dt * dt * a[t];
         }
-        if (mu && s0 > 0.0) broken += or_break(dim, n, h, M, s0, u, mu);
-        or_force(dim, n, h, M, alpha, E, mu, nu, u, an);
+        if (mu && s0 > 0.0) broken += or_break(dim, n, h, m, s0, u, mu);
+        or_force(dim, n, h, m, alpha, E, mu, nu, u, an);
         for (int64_t t = 0; t < L; ++t) {
             an[t] = (an[t] + (b ? b[t] : 0.0)) / rho;
             if (cons && cons[t]) v[t] = vpres ? vpres[t] : 0.0;
@@ -386,14 +390,14 @@ int64_t or_vv(int dim, const int64_t *n, double h, int M, double alpha, const do
  * vectors.  With surface-correction factors nu (nullable) each bond term also
  * carries v_rq = (nu_r + nu_q) / 2.  Writes g[N].
  */
-int or_grad_modulus(int dim, const int64_t *n, double h, int M, double alpha1,
+int or_grad_modulus(int dim, const int64_t *n, double h, double m, double alpha1,
                     const uint8_t *mu, const double *nu, const double *u, const double *lam, double *g)
 {
     int32_t off[3 * 16384];
-    int nnb = or_offsets(dim, M, off, 16384);
+    int nnb = or_offsets(dim, m, off, 16384);
     double (*blk)[3][3] = malloc(sizeof(double[3][3]) * (size_t)nnb);
     if (!blk) return -2;
-    for (int k = 0; k < nnb; ++k) bond_block(dim, off + 3 * k, h, M, alpha1, blk[k]);
+    for (int k = 0; k < nnb; ++k) bond_block(dim, off + 3 * k, h, m, alpha1, blk[k]);
     const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
     const int64_t N = nx * ny * nz;
 #pragma omp parallel for schedule(static)
@@ -434,10 +438,10 @@ int or_grad_modulus(int dim, const int64_t *n, double h, int M, double alpha1,
  * that A stays symmetric.  The common factor h^dim cancels in the ratio.
  * Writes nu[N]; returns the offset count.
  */
-int or_surface_nu(int dim, const int64_t *n, double h, int M, double *nu)
+int or_surface_nu(int dim, const int64_t *n, double h, double m, double *nu)
 {
     int32_t off[3 * 16384];
-    int nnb = or_offsets(dim, M, off, 16384);
+    int nnb = or_offsets(dim, m, off, 16384);
     if (nnb < 0) return -1;
     double *lam = malloc(sizeof(double) * (size_t)nnb);
     if (!lam) return -2;
@@ -445,7 +449,7 @@ int or_surface_nu(int dim, const int64_t *n, double h, int M, double *nu)
     for (int k = 0; k < nnb; ++k) {
         double r2 = 0.0;
         for (int a = 0; a < dim; ++a) r2 += (h * off[3 * k + a]) * (h * off[3 * k + a]);
-        lam[k] = or_lambda(sqrt(r2), M * h, h);
+        lam[k] = or_lambda(sqrt(r2), m * h, h);
         full += lam[k];
     }
     const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
@@ -472,14 +476,14 @@ int or_surface_nu(int dim, const int64_t *n, double h, int M, double *nu)
  * are -v_pq C_pq (nu NULL: v = 1).  This is the Gershgorin bound behind the
  * fictitious density of the ADR method.
  */
-int or_row_abs_max(int dim, const int64_t *n, double h, int M, double alpha, const double *nu, double *out)
+int or_row_abs_max(int dim, const int64_t *n, double h, double m, double alpha, const double *nu, double *out)
 {
     int32_t off[3 * 16384];
-    int nnb = or_offsets(dim, M, off, 16384);
+    int nnb = or_offsets(dim, m, off, 16384);
     if (nnb < 0) return -1;
     double (*blk)[3][3] = malloc(sizeof(double[3][3]) * (size_t)nnb);
     if (!blk) return -2;
-    for (int k = 0; k < nnb; ++k) bond_block(dim, off + 3 * k, h, M, alpha, blk[k]);
+    for (int k = 0; k < nnb; ++k) bond_block(dim, off + 3 * k, h, m, alpha, blk[k]);
     const int64_t nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
     const int64_t N = nx * ny * nz;
     for (int a = 0; a < 3; ++a) out[a] = 0.0;

@@ -60,7 +60,8 @@ def _field_coords(n, h):
     return (idx + 0.5) * h
 
 
-@pytest.mark.parametrize("dim,n,M", [(2, (13, 9), 3), (2, (9, 17), 4), (3, (7, 6, 8), 2)])
+@pytest.mark.parametrize("dim,n,M", [(2, (13, 9), 3), (2, (9, 17), 4), (3, (7, 6, 8), 2), (2, (12, 10), 2.5),
+                                     (3, (7, 8, 6), 1.5)])
 def test_translation_rotation_give_zero_force(dim, n, M):
     """P1/P2: a rigid translation and an infinitesimal rigid rotation produce no
     bond force on ANY row, edges and broken bonds included (each bond term
@@ -95,7 +96,7 @@ def test_translation_rotation_give_zero_force(dim, n, M):
                 assert np.abs(f).max() < 1e-12 * scale
 
 
-@pytest.mark.parametrize("dim,n,M", [(2, (15, 15), 3), (3, (9, 9, 9), 2)])
+@pytest.mark.parametrize("dim,n,M", [(2, (15, 15), 3), (3, (9, 9, 9), 2), (2, (16, 15), 3.7)])
 def test_linear_field_zero_on_full_horizon(dim, n, M):
     """P3: u = G x gives f = 0 at every node whose horizon lies inside the grid
     (odd symmetry of the kernel); at edge nodes it does not vanish."""
@@ -105,7 +106,8 @@ def test_linear_field_zero_on_full_horizon(dim, n, M):
     G = np.random.default_rng(2).normal(size=(dim, dim))
     u = np.einsum("ab,b...->a...", G, X)
     f = oracle.force(dim, n, h, M, al, u)
-    inner = (slice(None),) + (slice(M, -M),) * dim
+    R = oracle.radius(M)
+    inner = (slice(None),) + (slice(R, -R),) * dim
     scale = al * h ** dim * np.abs(u).max()
     assert np.abs(f[inner]).max() < 1e-12 * scale
     assert np.abs(f).max() > 1e-3 * scale
@@ -136,7 +138,8 @@ def test_quadratic_field_continuum_limit(dim, Ms, target):
 
 
 @pytest.mark.parametrize("dim,n,M", [(2, (11, 7), 1), (2, (11, 7), 2), (2, (8, 8), 3), (2, (9, 10), 4),
-                                     (3, (5, 6, 4), 1), (3, (5, 4, 6), 2)])
+                                     (3, (5, 6, 4), 1), (3, (5, 4, 6), 2), (2, (10, 9), 2.5), (2, (9, 9), 3.7),
+                                     (3, (5, 6, 5), 1.5)])
 def test_direct_sum_equals_dense_assembly(dim, n, M):
     """P5/P7: the C direct sum equals the brute-force dense matrix assembled from
     node positions (Eq. matrix / mae:e1); the dense matrix is symmetric and
@@ -154,7 +157,8 @@ def test_direct_sum_equals_dense_assembly(dim, n, M):
 
 
 @pytest.mark.parametrize("dim,n,M,frac", [(2, (11, 7), 2, 0.0), (2, (13, 10), 3, 0.1), (2, (9, 12), 4, 0.05),
-                                          (3, (5, 6, 7), 2, 0.0), (3, (6, 5, 7), 3, 0.05)])
+                                          (3, (5, 6, 7), 2, 0.0), (3, (6, 5, 7), 3, 0.05), (2, (12, 11), 2.5, 0.1),
+                                          (2, (10, 13), 3.7, 0.0), (3, (6, 6, 7), 2.5, 0.05)])
 def test_direct_sum_equals_fmvm(dim, n, M, frac):
     """P7: the direct sum equals the paper's fast form: TBT/TBTBT part by 2N
     circulant embedding and FFT (Algorithms 3/4), plus D^e (Eq. tea:sc) and the
@@ -673,3 +677,39 @@ def test_kw_block_step_is_below_the_stable_step():
     assert 1.2 < lam <= 1.2185
     assert w.extra["dt_stable"] <= 2.0 * w.h / np.sqrt(lam)
     assert w.extra["dt"] < 0.1 * w.extra["dt_stable"]
+
+
+def test_critical_stretch_hand_values():
+    """Eq. fra:s1: G0 = 9/(4 pi) (plane stress) or 12/(5 pi) (plane strain) with
+    E = delta = 1 gives s0 = 1; s0 grows as sqrt(G0 / (E delta)); the two
+    cases differ by sqrt(15/16) for the same G0."""
+    assert abs(oracle.critical_stretch(9 / (4 * math.pi), 1.0, 1.0, "stress") - 1.0) <= 1e-15
+    assert abs(oracle.critical_stretch(12 / (5 * math.pi), 1.0, 1.0, "strain") - 1.0) <= 1e-15
+    a = oracle.critical_stretch(3.0, 2.0, 0.5, "stress")
+    assert abs(oracle.critical_stretch(12.0, 2.0, 0.5, "stress") / a - 2.0) <= 1e-15
+    assert abs(oracle.critical_stretch(3.0, 2.0, 0.5, "strain") / a - math.sqrt(15 / 16)) <= 1e-15
+
+
+
+# --------------------------------------------------------------------------- horizons that are not a whole number of spacings
+
+@pytest.mark.parametrize("dim,m,count,shell", [(2, 1.5, 8, 4), (2, 2.5, 20, 8), (2, 3.7, 44, 8), (3, 2.5, 80, None)])
+def test_offsets_and_lambda_for_real_m(dim, m, count, shell):
+    """|o| <= m for m = delta / h not an integer, counted by hand: 2D m = 1.5 keeps
+    |o|^2 in {1, 2} (4 + 4), m = 2.5 adds {4, 5} (4 + 8), m = 3.7 adds {8, 9, 10, 13}
+    (4 + 4 + 8 + 8); 3D m = 2.5: |o|^2 in {1..6} (6 + 12 + 8 + 6 + 24 + 24).  The
+    partial-volume shell m - 1/2 < |o| <= m holds |o|^2 = 2 (m = 1.5), 5 (m = 2.5)
+    and 13 (m = 3.7; |o| = sqrt(10) = 3.16 is inside 3.2).  Catches rounding m to
+    an integer and a shell taken from the integer radius."""
+    offs = oracle.offsets(dim, m)
+    assert len(offs) == count
+    assert np.array_equal(offs, -offs[::-1])
+    d2 = (offs.astype(float) ** 2).sum(1)
+    assert d2.max() <= m * m
+    if shell is not None:
+        lam = np.array([oracle.lam(math.sqrt(v), m, 1.0) for v in d2])
+        assert int((lam < 1.0).sum()) == shell
+        assert np.all(lam > 0)
+    # hand values at m = 2.5: |o| = 2 is inside (lambda 1), |o| = sqrt(5) on the shell
+    assert oracle.lam(2.0, 2.5, 1.0) == 1.0
+    assert abs(oracle.lam(math.sqrt(5), 2.5, 1.0) - (3.0 - math.sqrt(5))) <= 1e-15
