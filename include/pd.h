@@ -69,6 +69,10 @@ typedef enum {
 #define PD_SC_NONE   0    /* the paper's operator A = A^ + D^e + D^f (default) */
 #define PD_SC_VOLUME 1    /* bonds scaled by v_pq = (nu_p + nu_q)/2, nu_p = V_full / V_p */
 
+/* ---- modes for pd_critical_stretch ---- */
+#define PD_PLANE_STRESS 0
+#define PD_PLANE_STRAIN 1
+
 /* ---- modes for pd_adr_solve ---- */
 #define PD_ADR_F64   0x1u  /* Algorithm 1 in FP64 throughout (the paper's solver) */
 #define PD_ADR_MIXED 0x2u  /* FP32 operator on the correction since an FP64 base, FP64 residual at each 10x drop */
@@ -315,6 +319,13 @@ int pd_set_bond_mask(pd_grid *g, const uint32_t *mask, void *stream);
  * [dim][N]; grad: DEVICE double [N].  scale = -1/2 gives dL/dE. */
 int pd_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale,
                     double *grad, void *stream);
+
+/* Critical bond stretch from the energy release rate G0 (Eq. fra:s1):
+ * s0 = sqrt(4 pi G0 / (9 E delta)) in plane stress (mode PD_PLANE_STRESS) and
+ * sqrt(5 pi G0 / (12 E delta)) in plane strain (PD_PLANE_STRAIN), for the 2D
+ * model; pass the result to pd_set_material.  Host only, no GPU needed.
+ * Errors: PD_ERR_INVALID (non-positive or non-finite input, unknown mode, s0 NULL). */
+int pd_critical_stretch(double G0, double E, double delta, int mode, double *s0);
 
 /* Destroys the grid and frees its device memory.  NULL is accepted. */
 int pd_destroy(pd_grid *g);

@@ -37,6 +37,8 @@ PD_SC_NONE = 0
 PD_SC_VOLUME = 1
 PD_ADR_F64 = 0x1
 PD_ADR_MIXED = 0x2
+PD_PLANE_STRESS = 0
+PD_PLANE_STRAIN = 1
 
 _STATUS = {0: "PD_OK", 1: "PD_ERR_INVALID", 2: "PD_ERR_CUDA", 3: "PD_ERR_OOM", 4: "PD_ERR_NOT_CONVERGED",
            5: "PD_ERR_TIMEOUT", 6: "PD_ERR_STATE"}
@@ -91,6 +93,7 @@ SIGNATURES = {
     "pd_set_bond_mask": (_I, [_VP, _VP, _VP]),
     "pd_grad_modulus": (_I, [_VP, _VP, _VP, _D, _VP, _VP]),
     "pd_destroy": (_I, [_VP]),
+    "pd_critical_stretch": (_I, [_D, _D, _D, _I, ctypes.POINTER(_D)]),
     "pd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -161,6 +164,13 @@ def pd_set_material(g, E=1.0, rho=1.0, thickness=1.0, s0=0.0, E_field=None):
     import torch
     _check(load_library().pd_set_material(g, float(E), float(rho), float(thickness), float(s0),
                                           _dptr(E_field, torch.float64)))
+
+
+def pd_critical_stretch(G0: float, E: float, delta: float, mode: int = PD_PLANE_STRESS) -> float:
+    """Critical bond stretch from the energy release rate (host only)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().pd_critical_stretch(float(G0), float(E), float(delta), int(mode), ctypes.byref(out)))
+    return out.value
 
 
 def pd_set_surface_correction(g, mode: int):

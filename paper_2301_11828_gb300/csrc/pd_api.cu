@@ -30,13 +30,15 @@ int fail(int code, const std::string &msg)
     return code;
 }
 
-// lambda of Eq. fac:e1 for an offset with |o|^2 = d2 (grid units, delta = M):
-// 1 when |o| <= M - 1/2 (tested exactly as 4 d2 <= (2M - 1)^2), M + 1/2 - |o| on
-// the shell M - 1/2 < |o| <= M.
-double lambda_of(int d2, int M)
+// lambda of Eq. fac:e1 for an offset with |o|^2 = d2, in grid units with
+// m = delta / h: 1 when |o| <= m - 1/2, m + 1/2 - |o| on the shell
+// m - 1/2 < |o| <= m, and 0 beyond m (an offset of the radius-ceil(m) disk that
+// is no bond).  bond_of decides |o| <= m on the integer d2 (a tie counts).
+bool bond_of(int d2, double m) { return (double)d2 <= m * m + 1e-9; }
+double lambda_of(int d2, double m)
 {
-    if (4 * d2 <= (2 * M - 1) * (2 * M - 1)) return 1.0;
-    return (double)M + 0.5 - std::sqrt((double)d2);
+    if (!bond_of(d2, m)) return 0.0;
+    return std::min(1.0, m + 0.5 - std::sqrt((double)d2));
 }
 
 static double alpha_of(int dim, double E, double delta, double thickness)
@@ -57,7 +59,7 @@ static void build_coefs(pd_grid *g)
         const int32_t *o = &g->off[3 * k];
         const int d2 = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
         const double r = std::sqrt((double)d2);
-        const double w = g->alpha1 * lambda_of(d2, g->M) * hp / (r * r * r);
+        const double w = g->alpha1 * lambda_of(d2, g->m) * hp / (r * r * r);
         double *c = &g->coef1[(size_t)nc * k];
         if (g->dim == 2) {
             c[0] = w * o[0] * o[0];
@@ -239,12 +241,16 @@ int pd_create_grid(int dim, const int64_t n[3], double h, double delta, const ui
         if (n[i] < 1 || n[i] > (1 << 20)) return fail(PD_ERR_INVALID, "grid extents must be in [1, 2^20]");
     if (!(h > 0) || !(delta > 0) || !std::isfinite(h) || !std::isfinite(delta))
         return fail(PD_ERR_INVALID, "h and delta must be positive");
-    const double ratio = delta / h;
-    const int M = (int)std::lround(ratio);
-    if (M < 1 || std::fabs(ratio - M) > 1e-9 * std::max(1.0, ratio))
-        return fail(PD_ERR_INVALID, "delta / h must be an integer >= 1");
+    // m = delta / h need not be an integer: the kernels work on the disk of radius
+    // M = ceil(m) and the offsets beyond m carry a zero coefficient and never break
+    double ratio = delta / h;
+    if (!(ratio >= 1.0 - 1e-9)) return fail(PD_ERR_INVALID, "delta / h must be at least 1");
+    const long near = std::lround(ratio);
+    const bool integral = std::fabs(ratio - (double)near) <= 1e-9 * std::max(1.0, ratio);
+    if (integral) ratio = (double)near;
+    const int M = integral ? (int)near : (int)std::ceil(ratio);
     if ((dim == 2 && M > kMaxM2) || (dim == 3 && M > kMaxM3))
-        return fail(PD_ERR_INVALID, "horizon M beyond the compiled maximum (2D 8, 3D 4)");
+        return fail(PD_ERR_INVALID, "horizon radius ceil(delta/h) beyond the compiled maximum (2D 8, 3D 4)");
     const int64_t N = n[0] * n[1] * (dim == 3 ? n[2] : 1);
     if (N > ((int64_t)1 << 31) - 1) return fail(PD_ERR_INVALID, "more than 2^31 - 1 nodes");
 
@@ -252,8 +258,9 @@ int pd_create_grid(int dim, const int64_t n[3], double h, double delta, const ui
     if (!g) return fail(PD_ERR_OOM, "host allocation failed");
     g->dim = dim;
     g->M = M;
+    g->m = ratio;
     g->h = h;
-    g->delta = M * h;
+    g->delta = integral ? M * h : delta;
     g->n[0] = n[0];
     g->n[1] = n[1];
     g->n[2] = (dim == 3) ? n[2] : 1;
@@ -549,6 +556,18 @@ int pd_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale
     if (rc) return rc;
     if (!u || !lam || !grad) return fail(PD_ERR_INVALID, "NULL vector");
     return launch_grad_modulus(g, u, lam, scale, grad, (cudaStream_t)stream);
+}
+
+int pd_critical_stretch(double G0, double E, double delta, int mode, double *s0)
+{
+    if (!s0) return fail(PD_ERR_INVALID, "s0 is NULL");
+    if (!(G0 > 0) || !(E > 0) || !(delta > 0) || !std::isfinite(G0) || !std::isfinite(E) || !std::isfinite(delta))
+        return fail(PD_ERR_INVALID, "G0, E and delta must be positive and finite");
+    const double pi = 3.14159265358979323846;
+    if (mode == PD_PLANE_STRESS) *s0 = std::sqrt(4.0 * pi * G0 / (9.0 * E * delta));
+    else if (mode == PD_PLANE_STRAIN) *s0 = std::sqrt(5.0 * pi * G0 / (12.0 * E * delta));
+    else return fail(PD_ERR_INVALID, "mode must be PD_PLANE_STRESS or PD_PLANE_STRAIN");
+    return PD_OK;
 }
 
 int pd_destroy(pd_grid *g)

@@ -113,12 +113,20 @@ k_df_gather(const T *__restrict__ u, T *__restrict__ out, int64_t N, int nx, int
 // double T that passes it.  k_break_thr finds T per offset by bisection over
 // the bit patterns of the non-negative doubles, with the same rounded
 // operations; k_break then needs no square root or division per bond.
+// Offsets of the radius-ceil(m) disk beyond m (non-integer delta / h) are no
+// bonds: their threshold is NaN, which no |xi + eta|^2 reaches.
 template <int DIM>
-__global__ void k_break_thr(int nnb, const int32_t *__restrict__ off, double h, double s0, double *thr)
+__global__ void k_break_thr(int nnb, const int32_t *__restrict__ off, double h, double s0, double m2, double *thr)
 {
     const int kk = nnb / 2 + blockIdx.x * blockDim.x + threadIdx.x;
     if (kk >= nnb) return;
     const int ox = off[3 * kk], oy = off[3 * kk + 1], oz = off[3 * kk + 2];
+    if ((double)(ox * ox + oy * oy + oz * oz) > m2 + 1e-9) {
+        thr[kk] = __longlong_as_double(0x7ff8000000000000ll);
+        double *xi = thr + nnb;
+        xi[3 * kk] = xi[3 * kk + 1] = xi[3 * kk + 2] = 0.0;
+        return;
+    }
     const double xi0 = __dmul_rn(h, (double)ox), xi1 = __dmul_rn(h, (double)oy), xi2 = __dmul_rn(h, (double)oz);
     double r2 = __dadd_rn(__dmul_rn(xi0, xi0), __dmul_rn(xi1, xi1));
     if (DIM == 3) r2 = __dadd_rn(r2, __dmul_rn(xi2, xi2));
@@ -209,8 +217,8 @@ __device__ __forceinline__ bool within(int64_t ax, int64_t ay, int64_t bx, int64
 }
 
 __global__ void __launch_bounds__(kBlk)
-k_segment(int64_t N, int nx, int ny, int nz, int nnb, const int32_t *__restrict__ off, uint32_t *mask, int64_t ax,
-          int64_t ay, int64_t bx, int64_t by, int64_t den, uint32_t *brflag, int32_t *brlist,
+k_segment(int64_t N, int nx, int ny, int nz, int nnb, const int32_t *__restrict__ off, double m2, uint32_t *mask,
+          int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t den, uint32_t *brflag, int32_t *brlist,
           unsigned long long *count)
 {
     unsigned long long newly = 0;
@@ -219,7 +227,9 @@ k_segment(int64_t N, int nx, int ny, int nz, int nnb, const int32_t *__restrict_
         node_coords(p, nx, ny, i, j, k);
         const int64_t px = den * (2 * i + 1), py = den * (2 * j + 1);
         for (int kk = nnb / 2; kk < nnb; ++kk) {   // upper half: q > p
-            const int qi = i + off[3 * kk], qj = j + off[3 * kk + 1], qk = k + off[3 * kk + 2];
+            const int ox = off[3 * kk], oy = off[3 * kk + 1], oz = off[3 * kk + 2];
+            if ((double)(ox * ox + oy * oy + oz * oz) > m2 + 1e-9) continue;   // no bond (beyond delta)
+            const int qi = i + ox, qj = j + oy, qk = k + oz;
             if (qi < 0 || qi >= nx || qj < 0 || qj >= ny || qk < 0 || qk >= nz) continue;
             const int64_t qx = den * (2 * qi + 1), qy = den * (2 * qj + 1);
             const int d1 = orient(ax, ay, bx, by, px, py), d2 = orient(ax, ay, bx, by, qx, qy);
@@ -383,9 +393,11 @@ int launch_break(pd_grid *g, const void *u, bool f64, int32_t *break_step, int32
     if (g->brk_thr_s0 != g->s0) {   // thresholds for this s0 (stream-ordered, no allocation)
         const int nh = g->nnb - g->nnb / 2;
         if (g->dim == 2)
-            k_break_thr<2><<<(nh + 127) / 128, 128, 0, s>>>(g->nnb, g->d_off, g->h, g->s0, g->d_brk_thr);
+            k_break_thr<2><<<(nh + 127) / 128, 128, 0, s>>>(g->nnb, g->d_off, g->h, g->s0, g->m * g->m,
+                                                            g->d_brk_thr);
         else
-            k_break_thr<3><<<(nh + 127) / 128, 128, 0, s>>>(g->nnb, g->d_off, g->h, g->s0, g->d_brk_thr);
+            k_break_thr<3><<<(nh + 127) / 128, 128, 0, s>>>(g->nnb, g->d_off, g->h, g->s0, g->m * g->m,
+                                                            g->d_brk_thr);
         PD_CUDA(cudaGetLastError());
         g->brk_thr_s0 = g->s0;
     }
@@ -407,7 +419,7 @@ int launch_break(pd_grid *g, const void *u, bool f64, int32_t *break_step, int32
 int launch_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, cudaStream_t s)
 {
     k_segment<<<grid_blocks(g->N), kBlk, 0, s>>>(g->N, (int)g->n[0], (int)g->n[1], (int)g->n[2], g->nnb, g->d_off,
-                                                  g->d_mask,
+                                                  g->m * g->m, g->d_mask,
                                                   2 * seg[0], 2 * seg[1], 2 * seg[2], 2 * seg[3], den, g->d_brflag,
                                                   g->d_brlist, g->d_count);
     PD_CUDA(cudaGetLastError());

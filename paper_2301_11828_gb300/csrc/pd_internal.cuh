@@ -78,6 +78,7 @@ struct pd_grid {
     int64_t n[3] = {1, 1, 1};
     int64_t N = 0;
     double h = 0, delta = 0;
+    double m = 1;                   // delta / h (the kernels' radius M is ceil(m))
     double E = 1, rho = 1, thickness = 1, s0 = 0;
     double alpha = 0, alpha1 = 0;   // micromodulus at E and at E = 1
     int device = 0;
@@ -180,7 +181,8 @@ constexpr uint32_t kForceMu = 0x80000000u;
 // Internal flag: the input already satisfies P u = u (the CG keeps its vectors projected).
 constexpr uint32_t kInputProjected = 0x40000000u;
 int upload_coefs(pd_grid *g);
-double lambda_of(int d2, int M);   // Eq. fac:e1 in grid units
+double lambda_of(int d2, double m);   // Eq. fac:e1 in grid units, m = delta / h
+bool bond_of(int d2, double m);        // |o| <= m for |o|^2 = d2
 
 // ------------------------------------------------------------------ surface correction (pd_surface.cu)
 // Class of a node for the surface-correction table: its distances to the low and

@@ -182,7 +182,7 @@ int surface_set(pd_grid *g, int mode)
     double full = 0.0;
     for (int k = 0; k < g->nnb; ++k) {
         const int32_t *o = &g->off[3 * k];
-        lam[k] = lambda_of(o[0] * o[0] + o[1] * o[1] + o[2] * o[2], M);
+        lam[k] = lambda_of(o[0] * o[0] + o[1] * o[1] + o[2] * o[2], g->m);
         full += lam[k];
     }
     int ncls = 1;

@@ -58,9 +58,9 @@ def test_invalid_arguments_fail_without_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.pd_create_grid(4, n, 0.1, 0.3, None, ctypes.byref(out)) == pd.PD_ERR_INVALID
     assert "dim" in pd.pd_last_error()
-    assert lib.pd_create_grid(2, n, 0.1, 0.25, None, ctypes.byref(out)) == pd.PD_ERR_INVALID
-    assert "integer" in pd.pd_last_error()
-    assert lib.pd_create_grid(2, n, 0.1, 0.9, None, ctypes.byref(out)) == pd.PD_ERR_INVALID
+    assert lib.pd_create_grid(2, n, 0.1, 0.05, None, ctypes.byref(out)) == pd.PD_ERR_INVALID   # delta < h
+    assert "at least 1" in pd.pd_last_error()
+    assert lib.pd_create_grid(2, n, 0.1, 0.95, None, ctypes.byref(out)) == pd.PD_ERR_INVALID   # radius 10 > 8
     assert lib.pd_destroy(None) == pd.PD_OK
     assert lib.pd_matvec(None, None, None, pd.PD_F32, None) == pd.PD_ERR_INVALID
 
@@ -72,3 +72,18 @@ def test_product_package_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "pd_oracle" not in txt, f
+
+
+def test_critical_stretch_host_helper(lib):
+    """Host-only entry point: agrees with the oracle's formula; refuses bad input."""
+    import oracle
+    import paper_2301_11828_gb300 as pd
+    for G0, E, d in [(1e3, 2e11, 3e-3), (0.5, 1.0, 0.03)]:
+        assert abs(pd.pd_critical_stretch(G0, E, d, pd.PD_PLANE_STRESS) - oracle.critical_stretch(G0, E, d, "stress")) \
+            <= 1e-15 * oracle.critical_stretch(G0, E, d, "stress")
+        assert abs(pd.pd_critical_stretch(G0, E, d, pd.PD_PLANE_STRAIN) - oracle.critical_stretch(G0, E, d, "strain")) \
+            <= 1e-15 * oracle.critical_stretch(G0, E, d, "strain")
+    with pytest.raises(pd.PDError):
+        pd.pd_critical_stretch(-1.0, 1.0, 1.0)
+    with pytest.raises(pd.PDError):
+        pd.pd_critical_stretch(1.0, 1.0, 1.0, 5)
