@@ -85,7 +85,7 @@ typedef enum {
 
 typedef struct {
     int dim;          /* 2 or 3 */
-    int M;            /* horizon in grid units */
+    int M;            /* kernel radius: ceil(delta / h) (= delta / h in the paper's examples) */
     int nnb;          /* number of neighbour offsets (28 for 2D M = 3) */
     int mask_words;   /* 32-bit words per node in the bond mask */
     int64_t n[3];     /* grid extents (n[2] = 1 in 2D) */
@@ -111,12 +111,16 @@ typedef struct {
 } pd_step_stats;
 
 /* Creates a grid of n[0] x n[1] (x n[2]) nodes with spacing h and horizon
- * delta = M h (Sec. 3, Sec. 4).  constrained: HOST uint8 [dim][N], nonzero
+ * delta (Sec. 3, Sec. 4).  m = delta / h need not be an integer: the bonds are
+ * the offsets with |o| <= m and lambda of Eq. fac:e1 uses the real delta; the
+ * kernels run on the disk of radius M = ceil(m), whose offsets beyond m carry
+ * a zero coefficient and never break (they appear in pd_get_offsets and the
+ * bond mask as intact).  constrained: HOST uint8 [dim][N], nonzero
  * marks a component in the volume-constrained set Omega_c (Sec. 3.3, and the
  * per-component remark of Sec. 3.4); NULL = none.  Sets E = 1, rho = 1,
  * thickness = 1, s0 = 0 (no breaking); every bond intact.
- * Errors: PD_ERR_INVALID (dim not 2/3, n < 1, h <= 0, delta/h not an integer
- * >= 1, M beyond the compiled maximum), PD_ERR_OOM, PD_ERR_CUDA. */
+ * Errors: PD_ERR_INVALID (dim not 2/3, n < 1, h <= 0, delta < h, ceil(delta/h)
+ * beyond the compiled maximum: 8 in 2D, 4 in 3D), PD_ERR_OOM, PD_ERR_CUDA. */
 int pd_create_grid(int dim, const int64_t n[3], double h, double delta,
                    const uint8_t *constrained, pd_grid **out);
 

@@ -331,12 +331,14 @@ class Grid:
 
     def __init__(self, dim: int, n: Sequence[int], h: float, M: int, constrained=None, E=1.0, rho=1.0,
                  thickness=1.0, s0=0.0, E_field=None, surface_correction: int = PD_SC_NONE):
-        self.dim, self.n, self.h, self.M = dim, tuple(int(v) for v in n), float(h), int(M)
-        self.handle = pd_create_grid(dim, self.n, h, M * h, constrained)
+        # M: delta / h (an integer in the paper's examples, any real >= 1 here)
+        self.dim, self.n, self.h, self.m = dim, tuple(int(v) for v in n), float(h), float(M)
+        self.handle = pd_create_grid(dim, self.n, h, self.m * h, constrained)
         self.set_material(E, rho, thickness, s0, E_field)
         if surface_correction:
             pd_set_surface_correction(self.handle, surface_correction)
         info = pd_get_info(self.handle)
+        self.M = info.M   # the kernels' radius, ceil(delta / h)
         self.nnb, self.mask_words, self.alpha = info.nnb, info.mask_words, info.alpha
 
     @property
