@@ -60,10 +60,10 @@ typedef enum {
 #define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
 #define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
-#define PD_ACCURATE       0x800u /* FP32 TMA-fed 2D stencil: sum c(o) ((u_p+o - u_p) + (u_p-o - u_p)) instead of
-                                    c(o) (u_p+o + u_p-o) against Kd u_p, so that the FP32 error is relative to
-                                    |K u| for smooth fields too (about 25% more arithmetic); the solvers' FP32
-                                    products use it.  Other kernels ignore the flag */
+#define PD_ACCURATE       0x800u /* FP32 TMA-fed 2D stencil and FP32 3D stencil: sum c(o) ((u_p+o - u_p) +
+                                    (u_p-o - u_p)) instead of c(o) (u_p+o + u_p-o) against Kd u_p, so that the FP32
+                                    error is relative to |K u| for smooth fields too (about 25% more arithmetic);
+                                    the 2D solvers' FP32 products use it.  Other kernels ignore the flag */
 
 /* ---- modes for pd_set_surface_correction ---- */
 #define PD_SC_NONE   0    /* the paper's operator A = A^ + D^e + D^f (default) */

@@ -6,6 +6,9 @@
 // of R outputs.  The (32 + 2M) x (8 + 2M) x (R + 2M) halo box of the three
 // components is staged in shared memory; for each (ox, oy) column pair the
 // thread loads the z-windows of columns (x+ox, y+oy) and (x-ox, y-oy).
+// DIFF (FP32 with PD_ACCURATE) sums (u~_{p+o} - u_p) + (u~_{p-o} - u_p) instead
+// of u~_{p+o} + u~_{p-o}: the FP32 error is then relative to |K u| on smooth
+// fields too, and K u = (Kd_p - Kd_int) u_p - sum.
 #include "pd_stencil.cuh"
 
 namespace pd {
@@ -40,7 +43,7 @@ __device__ __forceinline__ void pair3(T (&acc)[3][R], int r, bool nx_, bool ny_,
     }
 }
 
-template <typename T, int M>
+template <typename T, int M, bool DIFF>
 __global__ void __launch_bounds__(kThreads)
 k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
         const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
@@ -84,11 +87,21 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
 
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const T *base = s + (ty + M) * SX + (tx + M);   // column (x, y), plane 0
-    T acc[3][R];
+    T acc[3][R], ctr[3][DIFF ? R : 1];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[c][r] = T(0);
+        for (int r = 0; r < R; ++r) {
+            acc[c][r] = T(0);
+            if constexpr (DIFF) ctr[c][r] = base[c * PL + (r + M) * SX * SY];
+        }
+    // s for one offset pair: the pair sum, or the two differences to the output's own value
+    auto sum2 = [&](T a, T b, int c, int r) -> T {
+        if constexpr (DIFF)
+            return (a - ctr[c][r]) + (b - ctr[c][r]);
+        else
+            return a + b;
+    };
 
     static_for<0, M + 1>([&](auto OYI) {
         constexpr int oy = M - decltype(OYI)::value;
@@ -114,8 +127,9 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
 #pragma unroll
                     for (int r = 0; r < R; ++r)
                         pair3(acc, r, ox != 0, oy != 0, oz != 0, cxx, cxy, cxz, cyy, cyz, czz,
-                              wp[0][r + M + oz] + wm[0][r + M - oz], wp[1][r + M + oz] + wm[1][r + M - oz],
-                              wp[2][r + M + oz] + wm[2][r + M - oz]);
+                              sum2(wp[0][r + M + oz], wm[0][r + M - oz], 0, r),
+                              sum2(wp[1][r + M + oz], wm[1][r + M - oz], 1, r),
+                              sum2(wp[2][r + M + oz], wm[2][r + M - oz], 2, r));
                 }
             }
         });
@@ -134,7 +148,7 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
 #pragma unroll
         for (int r = 0; r < R; ++r)
             pair3(acc, r, false, false, true, cxx, cxy, cxz, cyy, cyz, czz, T(0), T(0),
-                  w0[2][r + M + oz] + w0[2][r + M - oz]);
+                  sum2(w0[2][r + M + oz], w0[2][r + M - oz], 2, r));
     }
 
     T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
@@ -158,6 +172,16 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
                 k3 = __ldg(q + 3);
                 k4 = __ldg(q + 4);
                 k5 = __ldg(q + 5);
+                if constexpr (DIFF) {   // the difference sums already hold -Kd_int u_p
+                    k0 -= kk[0];
+                    k1 -= kk[1];
+                    k2 -= kk[2];
+                    k3 -= kk[3];
+                    k4 -= kk[4];
+                    k5 -= kk[5];
+                }
+            } else if constexpr (DIFF) {
+                k0 = k1 = k2 = k3 = k4 = k5 = T(0);
             }
             const T u0 = w0[0][r + M], u1 = w0[1][r + M], u2 = w0[2][r + M];
             T f0 = dfma(k0, u0, dfma(k1, u1, dfma(k2, u2, -acc[0][r])));
@@ -212,12 +236,12 @@ PairTab<T, 3, M> make_pairs3(const pd_grid *g)
     return t;
 }
 
-template <typename T, int M>
+template <typename T, int M, bool DIFF>
 int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
     constexpr int R = rows3d<T, M>();
     const size_t smem = sizeof(T) * 3 * (kTX3 + 2 * M) * (kTY3 + 2 * M) * (R + 2 * M);
-    auto kern = k_tbt3d<T, M>;
+    auto kern = k_tbt3d<T, M, DIFF>;
     allow_smem(kern, smem);
     const int nzt = (int)((g->n[2] + R - 1) / R);
     if ((int64_t)nzt * a.batch > 65535) return fail(PD_ERR_INVALID, "3D batch too large for one launch");
@@ -234,11 +258,22 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 template <typename T>
 int run_t(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 4) {   // the difference form exists for FP32 only
+        if (a.accurate) {
+            switch (g->M) {
+                case 1: return run<T, 1, true>(g, a, s);
+                case 2: return run<T, 2, true>(g, a, s);
+                case 3: return run<T, 3, true>(g, a, s);
+                case 4: return run<T, 4, true>(g, a, s);
+            }
+            return fail(PD_ERR_INVALID, "horizon M not compiled for 3D");
+        }
+    }
     switch (g->M) {
-        case 1: return run<T, 1>(g, a, s);
-        case 2: return run<T, 2>(g, a, s);
-        case 3: return run<T, 3>(g, a, s);
-        case 4: return run<T, 4>(g, a, s);
+        case 1: return run<T, 1, false>(g, a, s);
+        case 2: return run<T, 2, false>(g, a, s);
+        case 3: return run<T, 3, false>(g, a, s);
+        case 4: return run<T, 4, false>(g, a, s);
     }
     return fail(PD_ERR_INVALID, "horizon M not compiled for 3D");
 }
