@@ -14,6 +14,13 @@
 //     iteration limit; on expiry the kernel records an error code and returns.
 //   * The x start of the box is rounded down to a 16-byte boundary (TMA rule)
 //     and the box is widened to cover the halo.
+//   * Buffers are released per warp: each warp arrives on the buffer's "empty"
+//     mbarrier when it has read its columns, and thread 0 waits on that
+//     barrier (bounded) before loading the buffer again.  Warps of a CTA drift
+//     up to kStages - 1 tiles apart instead of meeting at a block barrier
+//     after every tile (edge outputs take longer than interior ones).  When
+//     the input has to be projected, all threads rewrite the box, and the CTA
+//     runs in lockstep with block barriers instead.
 //   * For each offset pair the two components are handled as one packed
 //     FP32x2 value s = (s_x, s_y): the accumulators a1 += (cxx, cyy) * s and
 //     a2 += (cxy, cxy) * s give (K u) after the final swap
@@ -55,7 +62,8 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
     constexpr int NP = PackTab<M>::kPairs;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *const sbase = reinterpret_cast<float *>(smem_raw);   // buffer k at sbase + 2 * PLANE * k
-    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ __align__(8) uint64_t bars[kStages];    // full: the tile has landed
+    __shared__ __align__(8) uint64_t empty[kStages];   // every warp has read the buffer
     __shared__ int s_abort;
     // Edge-class diagonal table (Kd by clipped face distances), kept in shared
     // memory when small so that edge outputs do not wait on global loads.
@@ -65,11 +73,16 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         for (int i = threadIdx.x; i < KDS; i += kThreads) s_kd[i] = __ldg(kd + i);
 
     if (threadIdx.x == 0) {
-        for (int k = 0; k < kStages; ++k) mbar_init(&bars[k], 1);
+        for (int k = 0; k < kStages; ++k) {
+            mbar_init(&bars[k], 1);
+            mbar_init(&empty[k], kThreads / 32);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
     __syncthreads();
+    const bool lockstep = project_in != 0;   // the box is rewritten by all threads: block barriers
+    const int lane = threadIdx.x & 31;
 
     const int tx = threadIdx.x % kTXt, ty = threadIdx.x / kTXt;
     // Tile t lies in tile row r = t / tiles_x; the columns of each row are
@@ -104,19 +117,35 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
         const int cur = it % kStages;
         if (threadIdx.x == 0) {
-            // buffer (it - 1) % kStages was released by the barrier that ended the last iteration
+            // the next load goes to buffer (it - 1) % kStages, free once every warp has
+            // released its use it - 1 (lockstep: the block barrier that ended it - 1)
             const int64_t tn = t + (int64_t)(kStages - 1) * gridDim.x;
             if (tn < ntiles) {
-                issue((int)tn, (it + kStages - 1) % kStages);
-                ++n_issued;
+                const int prev = (it + kStages - 1) % kStages;
+                if (lockstep || it == 0 || mbar_wait(&empty[prev], ((it - 1) / kStages) & 1)) {
+                    issue((int)tn, prev);
+                    ++n_issued;
+                } else {
+                    atomicExch(err, 1);   // the warps waiting for that tile give up in turn
+                    s_abort = 1;
+                }
             }
         }
-        if (!mbar_wait(&bars[cur], (it / kStages) & 1)) {
-            atomicExch(err, 1);
-            s_abort = 1;
+        const bool ok = mbar_wait(&bars[cur], (it / kStages) & 1);
+        if (lockstep) {
+            if (!ok) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            }
+            __syncthreads();
+            if (s_abort) break;
+        } else if (__any_sync(0xffffffffu, !ok)) {   // warp-uniform decision
+            if (lane == 0) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            }
+            break;
         }
-        __syncthreads();
-        if (s_abort) break;
         int x0, y0, b;
         tile_coords(t, x0, y0, b);
         float *sx = sbase + 2 * PLANE * cur, *sy = sx + PLANE;
@@ -229,8 +258,14 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
             tile_body(std::false_type{});
         else
             tile_body(std::true_type{});
-        __syncthreads();   // all reads of buf[cur] done before it is refilled
+        if (lockstep) {
+            __syncthreads();   // all reads of buf[cur] done before it is refilled
+        } else {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[cur]);   // this warp's reads of buf[cur] are done
+        }
     }
+    __syncthreads();   // every warp has left the loop (and s_abort is visible)
     if (s_abort) {
         // let the copies still in flight land (bounded waits) before the CTA exits
         if (threadIdx.x == 0)
