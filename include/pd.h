@@ -158,6 +158,19 @@ int pd_matvec(pd_grid *g, const void *u, void *out, uint32_t flags, void *stream
 int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags,
                     void *stream);
 
+/* pd_matvec_batch for fields in HOST memory: u_host, out_host HOST
+ * [batch][dim][N] of the dtype in flags (page-locked memory -- cudaHostAlloc
+ * or cudaHostRegister -- gives full copy bandwidth; pageable memory works but
+ * the driver stages it).  The batch is cut into chunks of about 32 MB that are
+ * uploaded, multiplied and downloaded on three streams of the grid, so the two
+ * copy directions overlap each other and the products.  Ordered on `stream`:
+ * it starts after the work already queued there, and work queued afterwards
+ * starts after out_host is complete; the call itself returns at once.  Keeps
+ * four staging buffers of one chunk with the grid.  Errors as pd_matvec_batch,
+ * PD_ERR_OOM for the staging buffers. */
+int pd_matvec_batch_host(pd_grid *g, int64_t batch, const void *u_host, void *out_host, uint32_t flags,
+                         void *stream);
+
 /* Solves P K P u = P b (Eq. mat:e2 with h = 0 on Omega_c) by conjugate
  * gradients.  b, u: DEVICE double [dim][N]; u is the initial guess on entry
  * and the solution on exit (its constrained components are set to 0).

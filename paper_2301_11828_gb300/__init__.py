@@ -74,6 +74,7 @@ SIGNATURES = {
     "pd_set_surface_correction": (_I, [_VP, _I]),
     "pd_matvec": (_I, [_VP, _VP, _VP, _U32, _VP]),
     "pd_matvec_batch": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
+    "pd_matvec_batch_host": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
     "pd_cg_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
     "pd_adr_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
     "pd_step": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats), _VP]),
@@ -183,6 +184,21 @@ def pd_matvec(g, u, out, flags: int, stream=None):
 
 def pd_matvec_batch(g, batch: int, u, out, flags: int, stream=None):
     _check(load_library().pd_matvec_batch(g, int(batch), _dptr(u), _dptr(out), int(flags), _stream(stream)))
+
+
+def _hptr(t):
+    if t.is_cuda:
+        raise ValueError("expected a host (CPU) tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pd_matvec_batch_host(g, batch: int, u_host, out_host, flags: int, stream=None):
+    """K u for `batch` fields in HOST memory (pinned for full bandwidth), copies overlapped
+    with the product; ordered on `stream` (out_host is complete after it synchronises)."""
+    _check(load_library().pd_matvec_batch_host(g, int(batch), _hptr(u_host), _hptr(out_host), int(flags),
+                                               _stream(stream)))
 
 
 def pd_adr_solve(g, b, u, rtol: float, max_iter: int, stream=None, allow_not_converged=False, mode=PD_ADR_F64):

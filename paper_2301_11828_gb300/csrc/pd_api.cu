@@ -137,6 +137,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->ws);
     cg_release(g);
     adr_release(g);
+    hostpipe_release(g);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     delete g;
 }

@@ -121,6 +121,7 @@ struct pd_grid {
 
     void *cg = nullptr;        // CG workspace and captured graphs (pd_cg.cu)
     void *adr = nullptr;       // ADR workspace and captured graph (pd_adr.cu)
+    void *hostpipe = nullptr;  // streams, events and staging of pd_matvec_batch_host (pd_host.cu)
     bool no_tma = false;       // use the plain FP32 stencil instead of the TMA-fed one
     // surface correction (pd_surface.cu): mode, nu per class of clipped face distances,
     // the band of nodes within 2M of a face, three words of scratch
@@ -205,6 +206,7 @@ int launch_sc_gather(pd_grid *g, bool f64, const void *u, void *out, int64_t bat
 int surface_row_abs_max(pd_grid *g, double out[3], cudaStream_t s);   // band rows only; synchronises s
 void cg_release(pd_grid *g);
 void adr_release(pd_grid *g);
+void hostpipe_release(pd_grid *g);
 int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, cudaStream_t s,
            double *dot_partial = nullptr, double *dot_out = nullptr, unsigned int *retire = nullptr,
            double scale = 1.0);

@@ -334,3 +334,28 @@ def test_accurate_form_on_smooth_fields(pd, M):
     assert e_pair >= 20 * e_acc
     # the FP32 tolerance holds for the difference form on any field; the pair form can exceed it here
     assert rel_l2(acc, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_batch_from_host_memory(pd, dtype):
+    """pd_matvec_batch_host (chunks uploaded, multiplied and downloaded on three
+    streams) gives the same bits as the device call, pinned or pageable, for
+    batches that do and do not divide into chunks."""
+    w = syn.plate_static(256, 3, tag=2, u_amp=1.0)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+    fl = (pd.PD_F32 if dtype == torch.float32 else pd.PD_F64) | pd.PD_PROJECT
+    rng = np.random.default_rng(12)
+    for B, pin in ((1, True), (7, True), (33, False)):
+        U = torch.tensor(rng.uniform(-1, 1, (B, 2, w.n[1], w.n[0])), dtype=dtype)
+        if pin:
+            U = U.pin_memory()
+        O = torch.empty_like(U)
+        if pin:
+            O = O.pin_memory()
+        pd.pd_matvec_batch_host(g.handle, B, U, O, fl)
+        torch.cuda.synchronize()
+        Ud = U.cuda()
+        Od = torch.empty_like(Ud)
+        pd.pd_matvec_batch(g.handle, B, Ud, Od, fl)
+        torch.cuda.synchronize()
+        assert torch.equal(O, Od.cpu())
