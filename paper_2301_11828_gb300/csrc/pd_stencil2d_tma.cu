@@ -19,8 +19,8 @@
 //     barrier (bounded) before loading the buffer again.  Warps of a CTA drift
 //     up to kStages - 1 tiles apart instead of meeting at a block barrier
 //     after every tile (edge outputs take longer than interior ones).  When
-//     the input has to be projected, all threads rewrite the box, and the CTA
-//     runs in lockstep with block barriers instead.
+//     the input has to be projected (all threads rewrite the box), and for
+//     M > 3 (two CTAs per SM), the CTA runs in lockstep with block barriers.
 //   * For each offset pair the two components are handled as one packed
 //     FP32x2 value s = (s_x, s_y): the accumulators a1 += (cxx, cyy) * s and
 //     a2 += (cxy, cxy) * s give (K u) after the final swap
@@ -81,7 +81,10 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         s_abort = 0;
     }
     __syncthreads();
-    const bool lockstep = project_in != 0;   // the box is rewritten by all threads: block barriers
+    // lockstep (block barriers): when the box is rewritten by all threads, and for M > 3, where
+    // two CTAs per SM leave too few warps to cover warp 0 waiting for the slowest one
+    // (measured: M = 6 ran 15 % slower with per-warp release, M = 3 4 % faster)
+    const bool lockstep = project_in != 0 || M > 3;
     const int lane = threadIdx.x & 31;
 
     const int tx = threadIdx.x % kTXt, ty = threadIdx.x / kTXt;
