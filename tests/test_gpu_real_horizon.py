@@ -88,3 +88,19 @@ def test_real_horizon_solves(pd, mode):
     P = 1 - cons
     r = b * P - oracle.stiffness(2, n, h, m, oracle.alpha(2, 1.0, m * h), u.cpu().numpy(), cons=cons)
     assert np.linalg.norm(r) / np.linalg.norm(b * P) <= 1.05e-8
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_real_horizon_with_surface_correction(pd, dtype):
+    """The surface-correction factors use lambda at the real delta: nu and the
+    corrected product against the oracle at m = 2.5 (2D) and 1.5 (3D)."""
+    for dim, n, m in ((2, (96, 71), 2.5), (3, (20, 17, 15), 1.5)):
+        h = 1.0 / 64
+        rng = np.random.default_rng(3)
+        u = rng.uniform(-1, 1, (dim,) + tuple(reversed(n)))
+        g = pd.Grid(dim, n, h, m, surface_correction=pd.PD_SC_VOLUME)
+        ut = torch.tensor(u, dtype=dtype, device="cuda")
+        out = g.matvec(ut, flags=pd.PD_METHOD_STENCIL).double().cpu().numpy()
+        nu = oracle.surface_nu(dim, n, h, m)
+        ref = oracle.stiffness(dim, n, h, m, oracle.alpha(dim, 1.0, m * h), ut.double().cpu().numpy(), nu=nu)
+        assert rel_l2(out, ref) <= TOL[dtype]
