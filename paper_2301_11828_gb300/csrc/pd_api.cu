@@ -134,6 +134,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_coef1);
     cudaFree(g->d_nu_tab);
     cudaFree(g->d_band);
+    cudaFree(g->d_tma_flags);
     cudaFree(g->ws);
     cg_release(g);
     adr_release(g);

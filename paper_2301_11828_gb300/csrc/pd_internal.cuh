@@ -123,6 +123,8 @@ struct pd_grid {
     void *adr = nullptr;       // ADR workspace and captured graph (pd_adr.cu)
     void *hostpipe = nullptr;  // streams, events and staging of pd_matvec_batch_host (pd_host.cu)
     bool no_tma = false;       // use the plain FP32 stencil instead of the TMA-fed one
+    uint8_t *d_tma_flags = nullptr;   // per 64 x 32 tile: bit 0 an output is constrained, bit 1 its halo holds one
+    int tma_flags_M = -1;             // horizon the flags were computed for
     // surface correction (pd_surface.cu): mode, nu per class of clipped face distances,
     // the band of nodes within 2M of a face, three words of scratch
     int sc = 0;

@@ -26,6 +26,9 @@
 //     a2 += (cxy, cxy) * s give (K u) after the final swap
 //     a_x = a1.x + a2.y, a_y = a1.y + a2.x -- one packed add and two packed
 //     fused multiply-adds per pair instead of six scalar instructions.
+//   * With projection, only the tiles that hold a constrained output (or, for
+//     the input, a constrained node within the halo) take the masking paths;
+//     per-tile flags are computed once per grid (the constraints are fixed).
 //   * DIFF (PD_ACCURATE) sums the differences (u~_{p+o} - u_p) + (u~_{p-o} - u_p)
 //     instead, so that the FP32 error is relative to |K u| even for smooth
 //     fields (see tile_pairs); the solvers use it, the plain product does not.
@@ -53,7 +56,8 @@ template <int M, bool DIFF>
 __global__ void __launch_bounds__(kThreads, (M <= 3 || (M == 4 && !DIFF) ? 3 : 2))
 k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u, float *__restrict__ out, int nx,
             int ny, int64_t N, int tiles_x, int tiles_y, int ntiles, const uint8_t *__restrict__ cons,
-            int project_in, int project_out, const float *__restrict__ kd, float scale, PackTab<M> tab,
+            int project_in, int project_out, const uint8_t *__restrict__ tflags, const float *__restrict__ kd,
+            float scale, PackTab<M> tab,
             double *dot_partial, double *dot_out, unsigned int *retire, int *err)
 {
     constexpr int XL = x_lead<M>(), BX = box_x<M>(), BY = box_y<M>(), WL = kRt + 2 * M;
@@ -152,7 +156,10 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         int x0, y0, b;
         tile_coords(t, x0, y0, b);
         float *sx = sbase + 2 * PLANE * cur, *sy = sx + PLANE;
-        if (project_in) {
+        // projection where this tile needs it (uniform over the CTA)
+        const uint8_t tf = tflags ? __ldg(tflags + (y0 / kTYt) * tiles_x + x0 / kTXt) : 3;
+        const bool pin = project_in && (tf & 2), pout = project_out && (tf & 1);
+        if (pin) {
             for (int e = threadIdx.x; e < PLANE; e += kThreads) {
                 const int gx = x0 - XL + e % BX, gy = y0 - M + e / BX;
                 if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
@@ -207,7 +214,7 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
                 const bool warp_xe = __any_sync(0xffffffffu, lane_xe);     // warp holds an x-edge output
                 const int gy0 = y0 + ty * kRt;
                 const bool warp_ye = (gy0 < M) || (gy0 + kRt > ny - M);     // warp holds a y-edge row
-                if (full && !warp_xe && !warp_ye && !project_out && !dot_partial) {
+                if (full && !warp_xe && !warp_ye && !pout && !dot_partial) {
                     interior_epilogue();   // this warp's outputs are all interior
                     return;
                 }
@@ -242,7 +249,7 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
                     }
                     float fx = __fmaf_rn(kxx, up.x, __fmaf_rn(kxy, up.y, -ax));
                     float fy = __fmaf_rn(kxy, up.x, __fmaf_rn(kyy, up.y, -ay));
-                    if (project_out) {
+                    if (pout) {
                         const uint8_t m = __ldg(m0 + (int64_t)r * nx);
                         if (m & 1) fx = 0.f;
                         if (m & 2) fy = 0.f;
@@ -257,7 +264,7 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
             }
         };
         const bool interior = (x0 >= M) && (x0 + kTXt <= nx - M) && (y0 >= M) && (y0 + kTYt <= ny - M);
-        if (interior && !project_out && !dot_partial)
+        if (interior && !pout && !dot_partial)
             tile_body(std::false_type{});
         else
             tile_body(std::true_type{});
@@ -281,6 +288,25 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         const double s = block_sum(dot_blk_total, red);
         grid_finish(s, gridDim.x, blockIdx.x, dot_partial, dot_out, retire, red);
     }
+}
+
+// Per 64 x 32 tile: bit 0 when an output node is constrained, bit 1 when a node
+// within M of the tile (the part of the halo box the stencil reads) is.
+template <int M>
+__global__ void k_tma_flags(const uint8_t *__restrict__ cons, int nx, int ny, int tiles_x, int ntiles,
+                            uint8_t *__restrict__ flags)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int x0 = (t % tiles_x) * kTXt, y0 = (t / tiles_x) * kTYt;
+    uint8_t out = 0, halo = 0;
+    for (int y = max(0, y0 - M); y < min(ny, y0 + kTYt + M); ++y)
+        for (int x = max(0, x0 - M); x < min(nx, x0 + kTXt + M); ++x) {
+            const uint8_t c = cons[(int64_t)y * nx + x];
+            halo |= c;
+            if (y >= y0 && y < y0 + kTYt && x >= x0 && x < x0 + kTXt) out |= c;
+        }
+    flags[t] = (out ? 1 : 0) | (halo ? 2 : 0);
 }
 
 // ------------------------------------------------------------------ host side
@@ -310,9 +336,20 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     if (occ < 1) occ = 1;
     int blocks = (int)std::min<int64_t>(nt, (int64_t)occ * sms);
     if (a.dot_partial && a.batch != 1) return fail(PD_ERR_INVALID, "fused dot needs a single field");
+    const uint8_t *tflags = nullptr;
+    if (a.project) {   // the constraints are fixed per grid: the flags are computed once
+        const int nts = tiles_x * tiles_y;
+        if (g->tma_flags_M != M) {
+            if (!g->d_tma_flags) PD_CUDA(cudaMalloc(&g->d_tma_flags, (size_t)nts));
+            k_tma_flags<M><<<(nts + 127) / 128, 128, 0, s>>>(g->d_cons, nx, ny, tiles_x, nts, g->d_tma_flags);
+            PD_CUDA(cudaGetLastError());
+            g->tma_flags_M = M;
+        }
+        tflags = g->d_tma_flags;
+    }
     kern<<<blocks, kThreads, smem, s>>>(map, (const float *)a.u, (float *)a.out, nx, ny, g->N, tiles_x, tiles_y,
                                         (int)nt, g->d_cons, (a.project && !a.input_projected) ? 1 : 0,
-                                        a.project ? 1 : 0, g->d_kd32, (float)a.scale, make_pack<M>(g),
+                                        a.project ? 1 : 0, tflags, g->d_kd32, (float)a.scale, make_pack<M>(g),
                                         a.dot_partial, a.dot_out, a.retire, g->d_err);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
