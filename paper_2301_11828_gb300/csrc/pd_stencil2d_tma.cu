@@ -156,9 +156,14 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
         int x0, y0, b;
         tile_coords(t, x0, y0, b);
         float *sx = sbase + 2 * PLANE * cur, *sy = sx + PLANE;
-        // projection where this tile needs it (uniform over the CTA)
-        const uint8_t tf = tflags ? __ldg(tflags + (y0 / kTYt) * tiles_x + x0 / kTXt) : 3;
-        const bool pin = project_in && (tf & 2), pout = project_out && (tf & 1);
+        // projection where this tile needs it (uniform over the CTA; nothing to decide
+        // when the launch projects nothing)
+        bool pin = false, pout = false;
+        if (project_in | project_out) {
+            const uint8_t tf = tflags ? __ldg(tflags + (y0 / kTYt) * tiles_x + x0 / kTXt) : 3;
+            pin = project_in && (tf & 2);
+            pout = project_out && (tf & 1);
+        }
         if (pin) {
             for (int e = threadIdx.x; e < PLANE; e += kThreads) {
                 const int gx = x0 - XL + e % BX, gy = y0 - M + e / BX;
