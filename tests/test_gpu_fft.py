@@ -36,7 +36,7 @@ def test_fft_2d_matches_oracle(pd, dtype, n, M):
     ref = _K(2, n, h, M, un, E=0.7)
     # The FFT path forms Ctot u - sum c u~ and then removes the edge term, so its
     # rounding scales with |Ctot| |u|; on a grid where every bond leaves the grid
-    # (1 x 1) K u is exactly 0 and the error is judged against that scale.
+    # (1 x 1) K u is exactly 0 and the error is measured against that scale.
     side = 2 * M + 1
     e = np.zeros((2, side, side))
     e[0, M, M] = 1.0
