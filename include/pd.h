@@ -337,6 +337,14 @@ int pd_set_bond_mask(pd_grid *g, const uint32_t *mask, void *stream);
 int pd_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale,
                     double *grad, void *stream);
 
+/* Diagnostic of the bounded-wait error path that the persistent CG and the
+ * TMA pipelines use: one device thread polls a flag that nothing sets, at most
+ * `spins` times (about 0.3 us each), records the timeout in the grid's device
+ * error word and returns; the host reads the word, clears it and returns
+ * PD_ERR_TIMEOUT.  Nothing faults and the context stays usable.  spins in
+ * [1, 2^24].  Errors: PD_ERR_INVALID, PD_ERR_CUDA, PD_ERR_TIMEOUT (expected). */
+int pd_check_wait_timeout(pd_grid *g, int64_t spins, void *stream);
+
 /* Critical bond stretch from the energy release rate G0 (Eq. fra:s1):
  * s0 = sqrt(4 pi G0 / (9 E delta)) in plane stress (mode PD_PLANE_STRESS) and
  * sqrt(5 pi G0 / (12 E delta)) in plane strain (PD_PLANE_STRAIN), for the 2D

@@ -95,6 +95,7 @@ SIGNATURES = {
     "pd_grad_modulus": (_I, [_VP, _VP, _VP, _D, _VP, _VP]),
     "pd_destroy": (_I, [_VP]),
     "pd_critical_stretch": (_I, [_D, _D, _D, _I, ctypes.POINTER(_D)]),
+    "pd_check_wait_timeout": (_I, [_VP, _I64, _VP]),
     "pd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -165,6 +166,11 @@ def pd_set_material(g, E=1.0, rho=1.0, thickness=1.0, s0=0.0, E_field=None):
     import torch
     _check(load_library().pd_set_material(g, float(E), float(rho), float(thickness), float(s0),
                                           _dptr(E_field, torch.float64)))
+
+
+def pd_check_wait_timeout(g, spins: int, stream=None):
+    """Bounded device wait on a flag nothing sets: raises PDError(PD_ERR_TIMEOUT)."""
+    _check(load_library().pd_check_wait_timeout(g, int(spins), _stream(stream)))
 
 
 def pd_critical_stretch(G0: float, E: float, delta: float, mode: int = PD_PLANE_STRESS) -> float:

@@ -223,6 +223,19 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
     return launch_sc_gather(g, f64, u, out, batch, a.project, need_mu, scale, s);
 }
 
+// Diagnostic of the bounded-wait error path: one thread polls a device flag that
+// nothing sets, at most `spins` times with a short sleep between polls, and then
+// records the timeout in the grid's error word, as the library's waits do.
+__global__ void k_wait_unset_flag(const volatile int *flag, long long spins, int *err)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (long long i = 0; i < spins; ++i) {
+        if (*flag) return;
+        __nanosleep(256);
+    }
+    atomicExch(err, 2);
+}
+
 }  // namespace pd
 
 using namespace pd;
@@ -558,6 +571,24 @@ int pd_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale
     if (rc) return rc;
     if (!u || !lam || !grad) return fail(PD_ERR_INVALID, "NULL vector");
     return launch_grad_modulus(g, u, lam, scale, grad, (cudaStream_t)stream);
+}
+
+int pd_check_wait_timeout(pd_grid *g, int64_t spins, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (spins < 1 || spins > ((int64_t)1 << 24)) return fail(PD_ERR_INVALID, "spins must be in [1, 2^24]");
+    cudaStream_t s = (cudaStream_t)stream;
+    int *flag = reinterpret_cast<int *>(g->d_count + 7);   // a counter word the library never writes
+    PD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    k_wait_unset_flag<<<1, 32, 0, s>>>(flag, (long long)spins, g->d_err);
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaStreamSynchronize(s));
+    int derr = 0;
+    PD_CUDA(cudaMemcpy(&derr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!derr) return PD_OK;
+    PD_CUDA(cudaMemset(g->d_err, 0, sizeof(int)));   // reported once; the context stays usable
+    return fail(PD_ERR_TIMEOUT, "a bounded device wait gave up (diagnostic wait on a flag nothing sets)");
 }
 
 int pd_critical_stretch(double G0, double E, double delta, int mode, double *s0)

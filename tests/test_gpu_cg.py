@@ -149,3 +149,21 @@ def test_mixed_cg_generic_graph_path(pd):
     st = pd.pd_cg_solve(g.handle, b, u, 1e-8, 200000, pd.PD_CG_MIXED)
     assert st.persistent == 0
     assert _true_rel(w, u.cpu().numpy(), oracle.alpha(2, 1.0, w.delta)) <= 1.05e-8
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(pd):
+    """A device wait on a flag that nothing sets runs out after its limit, the
+    error word reaches the host as PD_ERR_TIMEOUT, is cleared, and the context
+    keeps working (a product and a solve afterwards)."""
+    w = syn.plate_static(64, 3, tag=5, u_amp=0.0)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+    with pytest.raises(pd.PDError) as e:
+        pd.pd_check_wait_timeout(g.handle, 4096)
+    assert e.value.code == pd.PD_ERR_TIMEOUT
+    assert pd.pd_get_info(g.handle).device_error == 0
+    u = torch.tensor(w.b, device="cuda")
+    out = g.matvec(u, flags=pd.PD_METHOD_STENCIL)
+    al = oracle.alpha(2, 1.0, w.delta)
+    assert rel_l2(out.cpu().numpy(), oracle.stiffness(2, w.n, w.h, w.M, al, w.b)) <= 1e-12
+    x, st = g.cg_solve(u, rtol=1e-8)
+    assert st.rel_residual <= 1e-8
