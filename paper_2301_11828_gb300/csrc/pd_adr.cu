@@ -23,6 +23,10 @@
 // chunk has an even number of iterations, so every replay starts on the same
 // buffer.  Everything is FP64, as in the oracle; the update multiplies by the
 // reciprocals of D and 2 + c instead of dividing element by element.
+//
+// PD_ADR_MIXED runs the same iteration on FP32 vectors with an FP64 base point
+// that is refreshed at every tenfold drop of the residual (the "mixed
+// precision" section below says how it keeps the FP64 iteration count).
 #include <cuda_runtime.h>
 
 #include <algorithm>
