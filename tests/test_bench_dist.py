@@ -72,3 +72,12 @@ def test_reference_arm_line_on_rank0():
     assert line["impl"] == "reference" and line["unit"] == "GDOF/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_recorded_traffic_belongs_to_the_current_kernel_sources():
+    """The DRAM traffic bench.py reports was captured on the kernel sources whose
+    hash it records; a change to those sources without a new capture must show
+    up here (bench.py then reports traffic as null)."""
+    import bench
+    assert bench.TRAFFIC["bytes_per_field"] > 0
+    assert bench._src_hash(bench.TRAFFIC["sources"]) == bench.TRAFFIC["sha256"]

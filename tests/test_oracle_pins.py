@@ -544,6 +544,12 @@ def test_surface_nu_hand_values():
     assert nu[0, 0, 0] == 2.0 and nu[3, 3, 3] == 2.0
     assert nu[0, 0, 1] == 1.5 and nu[0, 1, 1] == 1.2
     assert np.all(nu[1:3, 1:3, 1:3] == 1.0)
+    # 3D M = 2: |o|^2 = 1 (6 bonds, lambda 1), 2 (12, lambda 1), 3 (8, lambda 2.5 - sqrt 3),
+    # 4 (6, lambda 1/2): V_full = 21 + 8 (2.5 - sqrt 3); a corner keeps 3 + 3 + (2.5 - sqrt 3) + 1.5
+    l3 = 2.5 - math.sqrt(3.0)
+    nu = oracle.surface_nu(3, (6, 6, 6), 1.0 / 8, 2)
+    assert abs(nu[0, 0, 0] - (21 + 8 * l3) / (7.5 + l3)) <= 1e-14
+    assert nu[2:4, 2:4, 2:4].min() == 1.0 and nu[2:4, 2:4, 2:4].max() == 1.0
 
 
 @pytest.mark.parametrize("dim,n,M", [(2, (8, 8), 2), (2, (11, 7), 3), (3, (5, 6, 7), 2)])
