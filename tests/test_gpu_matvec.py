@@ -359,3 +359,23 @@ def test_batch_from_host_memory(pd, dtype):
         pd.pd_matvec_batch(g.handle, B, Ud, Od, fl)
         torch.cuda.synchronize()
         assert torch.equal(O, Od.cpu())
+
+
+def test_headline_launch_configuration_sampled(pd):
+    """The timed configuration itself: 32 fields of the 1024^2 plate (delta = 3h,
+    FP32, TMA stencil) in one batched launch; three of the fields (first, middle,
+    last) are checked in full against the oracle."""
+    w = syn.large_plate(3)
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=w.constrained)
+    B = 32
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    U = torch.empty((B, 2, w.n[1], w.n[0]), dtype=torch.float32, device="cuda")
+    U.uniform_(-1.0, 1.0, generator=gen)
+    O = torch.empty_like(U)
+    pd.pd_matvec_batch(g.handle, B, U, O, pd.PD_F32 | pd.PD_METHOD_STENCIL)
+    torch.cuda.synchronize()
+    al = oracle.alpha(2, 1.0, w.delta)
+    for b in (0, 17, 31):
+        ref = oracle.stiffness(2, w.n, w.h, w.M, al, U[b].double().cpu().numpy())
+        assert rel_l2(O[b].double().cpu().numpy(), ref) <= 2e-5
