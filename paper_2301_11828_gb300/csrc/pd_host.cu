@@ -114,7 +114,13 @@ extern "C" int pd_matvec_batch_host(pd_grid *g, int64_t batch, const void *u_hos
         PD_CUDA(cudaStreamWaitEvent(p->st[1], p->in_ready[slot], 0));
         if (k >= 2) PD_CUDA(cudaStreamWaitEvent(p->st[1], p->out_free[slot], 0));
         rc = matvec(g, nf, in[slot], outb[slot], flags, p->st[1]);
-        if (rc) return rc;
+        if (rc) {   // keep the caller's stream ordered after the copies already queued
+            for (auto &st : p->st) {
+                cudaEventRecord(p->end, st);
+                cudaStreamWaitEvent(s, p->end, 0);
+            }
+            return rc;
+        }
         PD_CUDA(cudaEventRecord(p->in_free[slot], p->st[1]));
         PD_CUDA(cudaEventRecord(p->out_ready[slot], p->st[1]));
         // download once computed
