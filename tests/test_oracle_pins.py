@@ -719,3 +719,24 @@ def test_offsets_and_lambda_for_real_m(dim, m, count, shell):
     # hand values at m = 2.5: |o| = 2 is inside (lambda 1), |o| = sqrt(5) on the shell
     assert oracle.lam(2.0, 2.5, 1.0) == 1.0
     assert abs(oracle.lam(math.sqrt(5), 2.5, 1.0) - (3.0 - math.sqrt(5))) <= 1e-15
+
+
+def test_kw_block_geometry():
+    """The 3D block's inputs: notches at 3/8 and 5/8 of the length from the y = 0
+    face to half the width; the velocity zone is the first M layers strictly
+    between the notches, y component only, at v0; nothing else is constrained."""
+    w = syn.kw_block(201, 101, 9, 3, v0=0.00634)
+    den = w.extra["notch_den"]
+    (a, b) = w.extra["notches"]
+    assert a[0] / den == 3 * 201 / 8 and b[0] / den == 5 * 201 / 8
+    assert a[1] == b[1] == 0 and a[3] / den == b[3] / den == 101 / 2
+    cons, vp = w.constrained, w.extra["v_prescribed"]
+    assert cons[0].sum() == 0 and cons[2].sum() == 0
+    zone = cons[1].astype(bool)
+    k, j, i = np.nonzero(zone)
+    assert set(j.tolist()) == {0, 1, 2}
+    xc = i + 0.5
+    assert np.all(xc > 3 * 201 / 8) and np.all(xc < 5 * 201 / 8)
+    assert zone.sum() == 9 * 3 * int(((np.arange(201) + 0.5 > 3 * 201 / 8) & (np.arange(201) + 0.5 < 5 * 201 / 8)).sum())
+    assert np.all(vp[1][zone] == 0.00634) and np.all(vp[1][~zone] == 0) and vp[0].sum() == vp[2].sum() == 0
+    assert abs(w.extra["dt"] - 0.06747 / 201) <= 1e-15
