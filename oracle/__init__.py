@@ -60,6 +60,8 @@ def lib():
             L.or_lambda.restype = ctypes.c_double
             L.or_alpha.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.or_alpha.restype = ctypes.c_double
+            L.or_bond_constant.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.or_bond_constant.restype = ctypes.c_double
             L.or_bond_block.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
             L.or_force.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    dp, dp, dp, dp, dp]
@@ -89,6 +91,8 @@ def lib():
             L.or_row_abs_max.restype = ctypes.c_int
             L.or_threads.argtypes = []
             L.or_threads.restype = ctypes.c_int
+            L.or_set_threads.argtypes = [ctypes.c_int]
+            L.or_set_threads.restype = None
             _lib = L
     return _lib
 
@@ -98,6 +102,11 @@ def lib():
 def threads() -> int:
     """OpenMP threads the oracle's node loops use."""
     return int(lib().or_threads())
+
+
+def set_threads(n: int) -> None:
+    """Sets the OpenMP threads of the oracle's node loops (timing on one core)."""
+    lib().or_set_threads(int(n))
 
 
 def _n64(n):
@@ -139,6 +148,13 @@ def lam(r: float, delta: float, dx: float) -> float:
 def alpha(dim: int, E: float, delta: float, thickness: float = 1.0) -> float:
     """Micromodulus constant of Sec. 2.1."""
     return lib().or_alpha(dim, E, delta, thickness)
+
+
+def bond_constant(dim: int, E: float, delta: float, thickness: float = 1.0) -> float:
+    """alpha times V_q / h^dim, the constant the force routines take as alpha_:
+    the node volume of Eq. mat:f1 is h^2 t for a 2D plate of thickness t
+    (alpha t in 2D, alpha in 3D; equal to alpha at unit thickness)."""
+    return lib().or_bond_constant(dim, E, delta, thickness)
 
 
 def bond_block(dim: int, o, h: float, M: int, alpha_: float) -> np.ndarray:

@@ -80,6 +80,15 @@ double or_alpha(int dim, double E, double delta, double thickness)
     return 12.0 * E / (M_PI * delta * delta * delta * delta);
 }
 
+/* Eq. mat:f1 weighs neighbour q by V_q, the volume of node q: h^dim in 3D and,
+ * for the plate of thickness t, h^2 t in 2D.  The routines below take the
+ * constant that multiplies lambda h^dim: alpha V_q / h^dim (alpha t in 2D). */
+double or_bond_constant(int dim, double E, double delta, double thickness)
+{
+    const double a = or_alpha(dim, E, delta, thickness);
+    return dim == 2 ? a * thickness : a;
+}
+
 /* Bond block lambda_q V_q C(xi) of Eqs. ker:e1 and mat:f1 for offset o:
  * c[a][b] = alpha xi_a xi_b / |xi|^3 * lambda * h^dim with xi = h o. */
 static void bond_block(int dim, const int32_t *o, double h, double m, double alpha,
@@ -521,5 +530,16 @@ int or_threads(void)
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/* Sets the number of OpenMP threads of the node loops (n >= 1); used to time the
+ * oracle on one core beside all cores. */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }

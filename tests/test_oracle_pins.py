@@ -137,6 +137,31 @@ def test_quadratic_field_continuum_limit(dim, Ms, target):
     assert errs[-1] < 0.06
 
 
+@pytest.mark.parametrize("t", [0.4, 2.5])
+def test_plate_thickness(t):
+    """Sec. 2.1 puts the plate thickness t in the 2D alpha (9E / (pi delta^3 t)),
+    and Eq. mat:f1 weighs each neighbour by its node volume, h^2 t for the
+    plate.  alpha itself scales as 1/t; the constant the force routines take
+    (alpha V_q / h^2) does not depend on t, and with it the quadratic field of
+    P4 tends to the plane-stress value 2.25E at any thickness, while alpha
+    alone with an area volume (a dropped t) would give 2.25E / t."""
+    delta = 3.0 / 64
+    a1, at = oracle.alpha(2, 1.0, delta), oracle.alpha(2, 1.0, delta, t)
+    assert abs(at * t / a1 - 1.0) < 1e-15
+    assert abs(oracle.bond_constant(2, 1.0, delta, t) / a1 - 1.0) < 1e-15
+    assert oracle.bond_constant(3, 1.0, delta, t) == oracle.alpha(3, 1.0, delta)   # 3D: no thickness
+    M, h = 24, 1.0 / 64
+    n = (2 * M + 3,) * 2
+    X = _field_coords(n, h)
+    u = np.zeros_like(X)
+    u[0] = X[0] ** 2
+    c = (M + 1,) * 2
+    fx = oracle.force(2, n, h, M, oracle.bond_constant(2, 1.0, M * h, t), u)[(0,) + c]
+    assert abs(fx / 2.25 - 1.0) < 0.06
+    fa = oracle.force(2, n, h, M, oracle.alpha(2, 1.0, M * h, t), u)[(0,) + c]
+    assert abs(fa * t / 2.25 - 1.0) < 0.06 and abs(fa / 2.25 - 1.0) > 0.3
+
+
 @pytest.mark.parametrize("dim,n,M", [(2, (11, 7), 1), (2, (11, 7), 2), (2, (8, 8), 3), (2, (9, 10), 4),
                                      (3, (5, 6, 4), 1), (3, (5, 4, 6), 2), (2, (10, 9), 2.5), (2, (9, 9), 3.7),
                                      (3, (5, 6, 5), 1.5)])
