@@ -27,8 +27,11 @@
  *   - Every call returns a pd_status; nothing aborts.  pd_last_error() holds a
  *     message for the last failure on the calling thread.
  *   - A pd_grid may be used by one host thread / stream at a time.
- *   - The horizon is delta = M h with an integer M >= 1 (Eq. band gives the
- *     neighbour set |o|^2 <= M^2 in grid offsets o).
+ *   - The horizon delta is any real multiple m = delta / h >= 1 of the grid
+ *     spacing.  The bonds of a node are the grid offsets o with |o| <= m
+ *     (Eq. band; Eq. fac:e1 gives their partial-volume factor); the kernels
+ *     work on the disk (ball) of integer radius M = ceil(m), where the offsets
+ *     beyond m carry a zero coefficient.
  */
 #ifndef PD_H
 #define PD_H
@@ -60,10 +63,14 @@ typedef enum {
 #define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
 #define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
-#define PD_ACCURATE       0x800u /* FP32 TMA-fed 2D stencil and FP32 3D stencil: sum c(o) ((u_p+o - u_p) +
-                                    (u_p-o - u_p)) instead of c(o) (u_p+o + u_p-o) against Kd u_p, so that the FP32
-                                    error is relative to |K u| for smooth fields too (about 25% more arithmetic);
-                                    the 2D solvers' FP32 products use it.  Other kernels ignore the flag */
+#define PD_ACCURATE       0x800u /* FP32 3D stencil: sum c(o) ((u_p+o - u_p) + (u_p-o - u_p)) instead of
+                                    c(o) (u_p+o + u_p-o) against Kd u_p, so that the FP32 error is relative to |K u|
+                                    for smooth fields too (about 25% more arithmetic).  The FP32 2D stencils always
+                                    sum differences (see PD_PAIR_FORM); other kernels ignore the flag */
+#define PD_PAIR_FORM      0x1000u /* FP32 TMA-fed 2D stencil: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o).
+                                    About 10% less arithmetic than the default difference form, but its FP32 error is
+                                    relative to sum |c| |u|, not to |K u|: on smooth fields, or fields with a large
+                                    constant part, it exceeds 1e-4 relative error.  Kept for comparison only */
 
 /* ---- modes for pd_set_surface_correction ---- */
 #define PD_SC_NONE   0    /* the paper's operator A = A^ + D^e + D^f (default) */
@@ -125,7 +132,9 @@ int pd_create_grid(int dim, const int64_t n[3], double h, double delta,
                    const uint8_t *constrained, pd_grid **out);
 
 /* Material (Sec. 2.1): E Young's modulus, rho density, thickness t (2D alpha =
- * 9E/(pi delta^3 t), 3D alpha = 12E/(pi delta^4)), s0 critical stretch (Eq. mu;
+ * 9E/(pi delta^3 t), 3D alpha = 12E/(pi delta^4); the node volume V_q of Eq.
+ * mat:f1 is h^2 t in 2D, so the thickness cancels from the force density),
+ * s0 critical stretch (Eq. mu;
  * s0 <= 0 disables breaking).  E_field: DEVICE double [N] per-node modulus or
  * NULL; with a field, bond (p,q) uses (E_p + E_q)/2 and the scalar E is
  * ignored.  The field is copied.  Errors: PD_ERR_INVALID (E, rho, t <= 0 or a
@@ -221,17 +230,28 @@ int pd_step(pd_grid *g, double *u, double *v, const double *b, int nsteps, doubl
             const double *v_prescribed, int32_t *break_step, int32_t step_base,
             pd_step_stats *stats, void *stream);
 
+/* Largest stable step of pd_step (the central-difference scheme of Algorithm 2,
+ * undamped): dt = 2 sqrt(rho / (E_max Lambda)), Lambda the largest eigenvalue
+ * of the unit-modulus symbol sum_{o in half} 2 c1(o) (1 - cos k.o) over the
+ * frequencies of a periodic grid of twice the grid's extent (in 3D at most 96
+ * per axis), E_max the modulus or the largest value of the modulus field.  An
+ * upper bound on lambda_max(K) / (E_max) for the clamped, partially broken
+ * grid, so dt is safe for every bond state.  Host computation, no GPU work.
+ * Errors: PD_ERR_INVALID (NULL). */
+int pd_stable_dt(pd_grid *g, double *dt);
+
 /* pd_step without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot let a library call cudaMalloc --
- * code running while a CUDA graph is being captured (an allocation there is
- * not recorded and may fail), services whose device memory is owned by their
- * own pool or caching allocator (a foreign cudaMalloc can fail or fragment
- * it), and real-time loops where the implicit synchronisation of cudaMalloc
- * would stall the stream.  Same arguments and results as pd_step.
+ * services whose device memory is owned by their own pool or caching
+ * allocator (such a pool may hold nearly all of the GPU, so a foreign
+ * cudaMalloc fails or fragments it), and real-time loops where the implicit
+ * synchronisation of cudaMalloc would stall the stream.  Same arguments and
+ * results as pd_step.
  * Its two work vectors live in one fixed array of 2^20 doubles (8 MiB) that
  * the library defines in device memory; every GPU that loads the library holds
  * it until the process exits.  Limit: dim * N <= 524288 (a 512 x 512 plate in
  * 2D); larger grids get PD_ERR_INVALID with a message naming the limit.  The
+ * grid's device must be the current device (PD_ERR_INVALID otherwise).  The
  * first call on each device looks the array's address up; make that first call
  * before any stream capture.  All calls share the array: calls whose work
  * overlaps on the GPU (other streams, other threads, other grids) race on it
@@ -253,8 +273,9 @@ int pd_step_noalloc(pd_grid *g, double *u, double *v, const double *b, int nstep
  * the dependence of the first acceleration on u_0 is included and abar is
  * cleared.  grad_E (DEVICE double [N] or NULL) accumulates dL/dE for the
  * per-node modulus field (bond modulus (E_p + E_q)/2).  Breaking is not
- * differentiated: the recorded bond history is held fixed.  Allocates a
- * workspace of (nsteps + 6) vectors for the call. */
+ * differentiated: the recorded bond history is held fixed.  Uses a workspace
+ * of (nsteps + 6) vectors that the grid keeps (allocated on the first call
+ * that needs more). */
 int pd_step_adjoint(pd_grid *g, const double *u_start, const double *v_start, const double *b, int nsteps,
                     double dt, const double *v_prescribed, const uint32_t *mask0, const int32_t *break_step,
                     int32_t step_base, double *ubar, double *vbar, double *abar, double *grad_E, void *stream);
@@ -274,6 +295,22 @@ int pd_break_bonds(pd_grid *g, const void *u, uint32_t flags, int64_t *n_newly_b
  * geometry. */
 int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_broken,
                      void *stream);
+
+/* K u on a slab of rows (2D: rows along y; 3D: planes along z), for a grid
+ * split across devices along its slowest axis: each device holds a band of
+ * rows plus an M-row halo on either side, exchanged before every product (the
+ * block-banded structure of Sec. 3.1 and Sec. 4 couples only rows within M of
+ * each other).  g is the whole grid (its tables and constraints); u_ext:
+ * DEVICE [batch][dim][ext_rows][...] holding grid rows [ext_row0, ext_row0 +
+ * ext_rows), which must contain [row0 - M, row0 + rows + M) clipped to the
+ * grid; out: DEVICE [batch][dim][rows][...] receives rows [row0, row0 + rows)
+ * of K u (P K P u with PD_PROJECT).  In 2D row0 must be a multiple of 32 (the
+ * stencil tile height).  Every output is then computed exactly as by
+ * pd_matvec: the slabs of a split give the whole-grid product bit for bit.
+ * Stencil form, intact bonds, constant modulus, no surface correction.
+ * Errors: PD_ERR_INVALID (shape, alignment, unsupported state), PD_ERR_CUDA. */
+int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const void *u_ext, int64_t ext_row0,
+                   int64_t ext_rows, void *out, uint32_t flags, void *stream);
 
 /* Chooses the method PD_METHOD_AUTO resolves to for each precision:
  * method = PD_METHOD_STENCIL or PD_METHOD_FFT pins it (both precisions);
@@ -320,9 +357,16 @@ int pd_batch_destroy(pd_batch *bt);
 /* Reads grid facts (host struct). */
 int pd_get_info(pd_grid *g, pd_grid_info *info);
 
-/* Neighbour offsets (HOST int32 [nnb][3], lexicographic (oz, oy, ox) order;
- * offset k and nnb-1-k are opposite).  cap = rows available. */
+/* Neighbour offsets (HOST int32 [nnb][3], each row (ox, oy, oz); rows in
+ * lexicographic (oz, oy, ox) order; offset k and nnb-1-k are opposite).
+ * cap = rows available. */
 int pd_get_offsets(pd_grid *g, int32_t *off, int cap);
+
+/* Bond blocks lambda V_q C(xi) of Eq. mat:f1 at the grid's modulus (HOST
+ * double [nnb][3] in 2D: xx, xy, yy; [nnb][6] in 3D: xx, xy, xz, yy, yz, zz),
+ * in the order of pd_get_offsets; the kernel table K(o) of Sec. 3.2 / Sec. 4
+ * (K(0) = -sum of all blocks).  cap = rows available. */
+int pd_get_coefficients(pd_grid *g, double *coef, int cap);
 
 /* Bond mask, DEVICE uint32 [mask_words][N]: bit (k % 32) of word k / 32 of
  * node p is 1 while bond (p, p + o_k) is intact (out-of-grid bits are 1). */
@@ -344,6 +388,14 @@ int pd_grad_modulus(pd_grid *g, const double *u, const double *lam, double scale
  * PD_ERR_TIMEOUT.  Nothing faults and the context stays usable.  spins in
  * [1, 2^24].  Errors: PD_ERR_INVALID, PD_ERR_CUDA, PD_ERR_TIMEOUT (expected). */
 int pd_check_wait_timeout(pd_grid *g, int64_t spins, void *stream);
+
+/* Measured arithmetic peak of the current device, the denominator of the
+ * roofline of the ALU-bound kernels (the paper has no counterpart): a kernel
+ * of independent fused multiply-add chains in FP64 (flags PD_F64) or FP32
+ * (PD_F32) over every SM, timed with CUDA events on `stream` for about 20 ms.
+ * flops: host, receives FLOP/s (an FMA counts two).  Synchronises the stream.
+ * Errors: PD_ERR_INVALID (flags, flops NULL), PD_ERR_CUDA. */
+int pd_probe_fma_rate(uint32_t flags, double *flops, void *stream);
 
 /* Critical bond stretch from the energy release rate G0 (Eq. fra:s1):
  * s0 = sqrt(4 pi G0 / (9 E delta)) in plane stress (mode PD_PLANE_STRESS) and

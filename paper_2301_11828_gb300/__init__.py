@@ -30,6 +30,7 @@ PD_PROJECT = 0x100
 PD_IGNORE_BROKEN = 0x200
 PD_NO_TMA = 0x400
 PD_ACCURATE = 0x800
+PD_PAIR_FORM = 0x1000
 PD_CG_F64 = 0x1
 PD_CG_MIXED = 0x2
 PD_CG_GRAPH = 0x10
@@ -75,6 +76,7 @@ SIGNATURES = {
     "pd_matvec": (_I, [_VP, _VP, _VP, _U32, _VP]),
     "pd_matvec_batch": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
     "pd_matvec_batch_host": (_I, [_VP, _I64, _VP, _VP, _U32, _VP]),
+    "pd_matvec_rows": (_I, [_VP, _I64, _I64, _I64, _VP, _I64, _I64, _VP, _U32, _VP]),
     "pd_cg_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
     "pd_adr_solve": (_I, [_VP, _VP, _VP, _D, _I, _U32, ctypes.POINTER(pd_cg_stats), _VP]),
     "pd_step": (_I, [_VP, _VP, _VP, _VP, _I, _D, _VP, _VP, ctypes.c_int32, ctypes.POINTER(pd_step_stats), _VP]),
@@ -90,12 +92,15 @@ SIGNATURES = {
     "pd_autotune": (_I, [_VP, _U32, _VP, _VP]),
     "pd_get_info": (_I, [_VP, ctypes.POINTER(pd_grid_info)]),
     "pd_get_offsets": (_I, [_VP, _VP, _I]),
+    "pd_get_coefficients": (_I, [_VP, _VP, _I]),
     "pd_get_bond_mask": (_I, [_VP, _VP, _VP]),
     "pd_set_bond_mask": (_I, [_VP, _VP, _VP]),
     "pd_grad_modulus": (_I, [_VP, _VP, _VP, _D, _VP, _VP]),
     "pd_destroy": (_I, [_VP]),
     "pd_critical_stretch": (_I, [_D, _D, _D, _I, ctypes.POINTER(_D)]),
     "pd_check_wait_timeout": (_I, [_VP, _I64, _VP]),
+    "pd_probe_fma_rate": (_I, [_U32, ctypes.POINTER(_D), _VP]),
+    "pd_stable_dt": (_I, [_VP, ctypes.POINTER(_D)]),
     "pd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -173,6 +178,20 @@ def pd_check_wait_timeout(g, spins: int, stream=None):
     _check(load_library().pd_check_wait_timeout(g, int(spins), _stream(stream)))
 
 
+def pd_stable_dt(g) -> float:
+    """Largest stable Verlet step of the grid (see pd.h)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().pd_stable_dt(g, ctypes.byref(out)))
+    return out.value
+
+
+def pd_probe_fma_rate(flags: int, stream=None) -> float:
+    """Measured FMA throughput of the current device in FLOP/s (PD_F32 or PD_F64)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().pd_probe_fma_rate(int(flags), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
 def pd_critical_stretch(G0: float, E: float, delta: float, mode: int = PD_PLANE_STRESS) -> float:
     """Critical bond stretch from the energy release rate (host only)."""
     out = ctypes.c_double(0.0)
@@ -190,6 +209,12 @@ def pd_matvec(g, u, out, flags: int, stream=None):
 
 def pd_matvec_batch(g, batch: int, u, out, flags: int, stream=None):
     _check(load_library().pd_matvec_batch(g, int(batch), _dptr(u), _dptr(out), int(flags), _stream(stream)))
+
+
+def pd_matvec_rows(g, batch: int, row0: int, rows: int, u_ext, ext_row0: int, ext_rows: int, out, flags: int,
+                   stream=None):
+    _check(load_library().pd_matvec_rows(g, int(batch), int(row0), int(rows), _dptr(u_ext), int(ext_row0),
+                                         int(ext_rows), _dptr(out), int(flags), _stream(stream)))
 
 
 def _hptr(t):
@@ -321,6 +346,14 @@ def pd_get_offsets(g) -> np.ndarray:
     return buf
 
 
+def pd_get_coefficients(g) -> np.ndarray:
+    """Bond blocks at the grid's modulus, [nnb][3] (2D) or [nnb][6] (3D), offset order."""
+    info = pd_get_info(g)
+    buf = np.zeros((info.nnb, 3 if info.dim == 2 else 6), dtype=np.float64)
+    _check(load_library().pd_get_coefficients(g, buf.ctypes.data_as(ctypes.c_void_p), info.nnb))
+    return buf
+
+
 def pd_get_bond_mask(g, mask, stream=None):
     import torch
     _check(load_library().pd_get_bond_mask(g, _dptr(mask, torch.int32), _stream(stream)))
@@ -405,6 +438,9 @@ class Grid:
             u = torch.zeros_like(b)
         st = pd_cg_solve(self.handle, b, u, rtol, max_iter, mode, stream)
         return u, st
+
+    def stable_dt(self) -> float:
+        return pd_stable_dt(self.handle)
 
     def step(self, u, v, b=None, nsteps=1, dt=1e-3, v_prescribed=None, break_step=None, step_base=0, stream=None):
         return pd_step(self.handle, u, v, b, nsteps, dt, v_prescribed, break_step, step_base, stream)

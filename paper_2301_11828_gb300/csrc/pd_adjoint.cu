@@ -143,8 +143,15 @@ extern "C" int pd_step_adjoint(pd_grid *g, const double *u_start, const double *
     const size_t mwords = (size_t)g->W * g->N;
     // workspace: nsteps + 1 displacement states, v, a, f, t, abn, one mask
     const size_t need = sizeof(double) * ((size_t)(nsteps + 1) * L + 5 * (size_t)L) + sizeof(uint32_t) * mwords + 4096;
-    char *ws = nullptr;
-    if (cudaMalloc(&ws, need) != cudaSuccess) return fail(PD_ERR_OOM, "adjoint workspace");
+    // kept by the grid between calls (a checkpointed sweep calls this once per segment)
+    if (g->adj_ws_bytes < need) {
+        cudaFree(g->adj_ws);
+        g->adj_ws = nullptr;
+        g->adj_ws_bytes = 0;
+        if (cudaMalloc(&g->adj_ws, need) != cudaSuccess) return fail(PD_ERR_OOM, "adjoint workspace");
+        g->adj_ws_bytes = need;
+    }
+    char *ws = (char *)g->adj_ws;
     double *U = (double *)ws;
     double *v = U + (size_t)(nsteps + 1) * L, *a = v + L, *f = a + L, *tv = f + L, *abn = tv + L;
     uint32_t *mk = (uint32_t *)(abn + L);
@@ -162,7 +169,6 @@ extern "C" int pd_step_adjoint(pd_grid *g, const double *u_start, const double *
     auto bail = [&](int code) {
         g->d_mask = saved_mask;
         g->broken_total = saved_broken;
-        cudaFree(ws);
         return code;
     };
     g->broken_total = 1;   // the replayed masks may hold broken bonds: take the mask-aware paths

@@ -48,13 +48,17 @@ static double alpha_of(int dim, double E, double delta, double thickness)
     return 12.0 * E / (pi * delta * delta * delta * delta);
 }
 
+// The bond blocks lambda V_q C(xi) of Eq. mat:f1 with V_q the volume of a node:
+// h^3 in 3D and h^2 t for the 2D plate of thickness t, whose 1/t in alpha it
+// cancels (the force density does not depend on the thickness).
 static void build_coefs(pd_grid *g)
 {
     const int nc = ncoef(g->dim);
     g->alpha1 = alpha_of(g->dim, 1.0, g->delta, g->thickness);
     g->alpha = g->alpha1 * g->E;
     g->coef1.assign((size_t)g->nnb * nc, 0.0);
-    const double hp = (g->dim == 2) ? g->h : g->h * g->h;
+    // V_q / h^d times the h^(d-1) of xi_a xi_b / |xi|^3 = h^2 o_a o_b / (h^3 |o|^3)
+    const double hp = (g->dim == 2) ? g->h * g->thickness : g->h * g->h;
     for (int k = 0; k < g->nnb; ++k) {
         const int32_t *o = &g->off[3 * k];
         const int d2 = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
@@ -136,6 +140,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_band);
     cudaFree(g->d_tma_flags);
     cudaFree(g->ws);
+    cudaFree(g->adj_ws);
     cg_release(g);
     adr_release(g);
     hostpipe_release(g);
@@ -192,6 +197,7 @@ int matvec(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags, 
     a.input_projected = (flags & kInputProjected) != 0;
     a.no_tma = (flags & PD_NO_TMA) != 0;
     a.accurate = (flags & PD_ACCURATE) != 0;
+    a.pair_form = (flags & PD_PAIR_FORM) != 0;
     a.scale = scale;
 
     if (dot_partial && g->sc) return fail(PD_ERR_INVALID, "internal: fused dot with the surface correction");
@@ -358,14 +364,18 @@ int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s
         PD_CUDA(cudaMemcpy(g->d_E, E_field, sizeof(double) * (size_t)g->N, cudaMemcpyDeviceToDevice));
         std::vector<double> hE((size_t)g->N);
         PD_CUDA(cudaMemcpy(hE.data(), g->d_E, sizeof(double) * (size_t)g->N, cudaMemcpyDeviceToHost));
-        for (double v : hE)
+        g->E_max = 0.0;
+        for (double v : hE) {
             if (!(v > 0) || !std::isfinite(v)) {
                 g->has_E = false;
                 return fail(PD_ERR_INVALID, "modulus field values must be positive and finite");
             }
+            g->E_max = std::max(g->E_max, v);
+        }
         g->has_E = true;
     } else {
         g->has_E = false;
+        g->E_max = E;
     }
     rc = build_kd(g);
     if (rc) return rc;
@@ -398,6 +408,38 @@ int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_
     if (rc) return rc;
     if (batch < 1) return fail(PD_ERR_INVALID, "batch must be >= 1");
     return matvec(g, batch, u, out, flags, (cudaStream_t)stream);
+}
+
+int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const void *u_ext, int64_t ext_row0,
+                   int64_t ext_rows, void *out, uint32_t flags, void *stream)
+{
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (batch < 1 || batch > 65535) return fail(PD_ERR_INVALID, "batch must be in [1, 65535]");
+    const int64_t ny = g->n[g->dim - 1], M = g->M;   // rows in 2D, planes in 3D
+    if (rows < 1 || row0 < 0 || row0 + rows > ny) return fail(PD_ERR_INVALID, "rows outside the grid");
+    if (g->dim == 2 && row0 % 32 != 0) return fail(PD_ERR_INVALID, "row0 must be a multiple of 32 (the tile height)");
+    if (ext_row0 < 0 || ext_rows < 1 || ext_row0 + ext_rows > ny || ext_row0 > std::max<int64_t>(0, row0 - M) ||
+        ext_row0 + ext_rows < std::min(ny, row0 + rows + M))
+        return fail(PD_ERR_INVALID, "u_ext must hold the rows [row0 - M, row0 + rows + M) of the grid");
+    const bool f32 = flags & PD_F32, f64 = flags & PD_F64;
+    if (f32 == f64) return fail(PD_ERR_INVALID, "exactly one of PD_F32 / PD_F64 must be set");
+    if (!u_ext || !out) return fail(PD_ERR_INVALID, "u_ext and out must be device pointers");
+    if (flags & (PD_METHOD_FFT | PD_PAIR_FORM)) return fail(PD_ERR_INVALID, "pd_matvec_rows runs the stencil form");
+    if (g->has_E || g->sc || g->broken_total > 0)
+        return fail(PD_ERR_INVALID, "pd_matvec_rows: intact bonds, constant modulus, no surface correction");
+    MatvecArgs a{};
+    a.u = u_ext;
+    a.out = out;
+    a.batch = batch;
+    a.project = (flags & PD_PROJECT) && g->has_cons;
+    a.no_tma = (flags & PD_NO_TMA) != 0;
+    a.scale = 1.0;
+    a.in_row0 = ext_row0;
+    a.in_rows = ext_rows;
+    a.out_row0 = row0;
+    a.out_rows = rows;
+    return launch_stencil(g, f64, a, (cudaStream_t)stream);
 }
 
 int pd_set_method(pd_grid *g, uint32_t method)
@@ -501,6 +543,15 @@ int pd_get_offsets(pd_grid *g, int32_t *off, int cap)
     if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
     if (!off || cap < g->nnb) return fail(PD_ERR_INVALID, "offset buffer too small");
     std::memcpy(off, g->off.data(), sizeof(int32_t) * 3 * (size_t)g->nnb);
+    return PD_OK;
+}
+
+int pd_get_coefficients(pd_grid *g, double *coef, int cap)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (!coef || cap < g->nnb) return fail(PD_ERR_INVALID, "coefficient buffer too small");
+    const int nc = ncoef(g->dim);
+    for (size_t i = 0; i < (size_t)nc * g->nnb; ++i) coef[i] = g->coef1[i] * g->E;
     return PD_OK;
 }
 

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 #include <chrono>
 #include <mutex>
 #include <string>
@@ -508,6 +510,70 @@ extern "C" int pd_step(pd_grid *g, double *u, double *v, const double *b, int ns
 }
 
 // ---------------------------------------------------------------------------
+// Stable step of the central-difference (Verlet) scheme of Algorithm 2: the
+// undamped scheme u'' = -K u / rho is stable for dt < 2 / sqrt(lambda_max(K) / rho).
+// lambda_max is bounded by the largest eigenvalue of the symbol of the
+// full-horizon operator over the frequencies of a periodic grid of twice the
+// extent (zero-extension only adds bond energy; broken bonds lower it; a
+// modulus field scales it by at most its largest value), the unit-modulus
+// symbol being K^1(k) = sum_{o in half} 2 c1(o) (1 - cos k.o) (2 x 2 or 3 x 3,
+// real and symmetric since c1(o) = c1(-o)).
+extern "C" int pd_stable_dt(pd_grid *g, double *dt)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (!dt) return fail(PD_ERR_INVALID, "dt is NULL");
+    const int d = g->dim, nc = ncoef(d);
+    // the frequency grid: 2 n per axis in 2D; at most 2 x 48 per axis in 3D (the symbol
+    // is a trigonometric polynomial of degree M, which that grid resolves finely)
+    int64_t L[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) L[a] = d == 2 ? 2 * g->n[a] : std::min<int64_t>(2 * g->n[a], 96);
+    std::vector<int> half;
+    for (int k = 0; k < g->nnb; ++k) {   // one offset of each pair +-o: the first nonzero component positive
+        const int32_t *o = &g->off[3 * k];
+        const int f = o[2] != 0 ? o[2] : (o[1] != 0 ? o[1] : o[0]);
+        if (f > 0) half.push_back(k);
+    }
+    const double two_pi = 6.283185307179586476925;
+    double lam = 0.0;
+    for (int64_t kz = 0; kz < L[2]; ++kz)
+        for (int64_t ky = 0; ky < L[1]; ++ky)
+            for (int64_t kx = 0; kx < L[0]; ++kx) {
+                const double w[3] = {two_pi * kx / L[0], two_pi * ky / L[1], two_pi * kz / L[2]};
+                double S[6] = {0, 0, 0, 0, 0, 0};
+                for (int k : half) {
+                    const int32_t *o = &g->off[3 * k];
+                    const double f = 2.0 * (1.0 - std::cos(w[0] * o[0] + w[1] * o[1] + w[2] * o[2]));
+                    for (int i = 0; i < nc; ++i) S[i] += f * g->coef1[(size_t)nc * k + i];
+                }
+                double m;
+                if (d == 2) {   // xx, xy, yy
+                    const double tr = 0.5 * (S[0] + S[2]), df = 0.5 * (S[0] - S[2]);
+                    m = tr + std::sqrt(df * df + S[1] * S[1]);
+                } else {        // xx, xy, xz, yy, yz, zz: largest eigenvalue of a symmetric 3 x 3
+                    const double a = S[0], b = S[3], c = S[5], x = S[1], y = S[2], z = S[4];
+                    const double q = (a + b + c) / 3.0;
+                    const double p1 = x * x + y * y + z * z;
+                    const double p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * p1;
+                    if (p2 <= 0.0) {
+                        m = q;
+                    } else {
+                        const double p = std::sqrt(p2 / 6.0);
+                        const double B00 = (a - q) / p, B11 = (b - q) / p, B22 = (c - q) / p;
+                        const double B01 = x / p, B02 = y / p, B12 = z / p;
+                        const double detB = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
+                                            B02 * (B01 * B12 - B11 * B02);
+                        const double r = std::max(-1.0, std::min(1.0, 0.5 * detB));
+                        m = q + 2.0 * p * std::cos(std::acos(r) / 3.0);
+                    }
+                }
+                lam = std::max(lam, m);
+            }
+    if (!(lam > 0)) return fail(PD_ERR_STATE, "the operator has no positive eigenvalue");
+    *dt = 2.0 * std::sqrt(g->rho / (g->E_max * lam));
+    return PD_OK;
+}
+
+// ---------------------------------------------------------------------------
 // pd_step_noalloc: the velocity-Verlet loop of pd_step without any device
 // allocation.  pd_step keeps its two work vectors (acceleration and force) in
 // a buffer it cudaMallocs on first use; some callers cannot let a library do
@@ -526,10 +592,15 @@ static __device__ __align__(256) double g_step_scratch[kNoAllocDoubles];
 std::mutex g_scratch_mu;
 double *g_scratch_addr[64] = {};
 
-int step_scratch(double **out)
+// The grid's device must be current: the array is looked up, and the kernels
+// run, on it.
+int step_scratch(const pd_grid *g, double **out)
 {
     int dev = -1;
     PD_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device)
+        return fail(PD_ERR_INVALID, "pd_step_noalloc: the current device (" + std::to_string(dev) +
+                                        ") is not the grid's (" + std::to_string(g->device) + ")");
     if (dev < 0 || dev >= 64) return fail(PD_ERR_CUDA, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
@@ -558,7 +629,7 @@ extern "C" int pd_step_noalloc(pd_grid *g, double *u, double *v, const double *b
         return fail(PD_ERR_INVALID, "pd_step_noalloc: dim * N = " + std::to_string(L) +
                                         " exceeds its fixed scratch (dim * N <= 524288); use pd_step");
     double *scratch = nullptr;
-    int rc = step_scratch(&scratch);
+    int rc = step_scratch(g, &scratch);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     double *a = scratch;       // both vectors are written in full before they are read

@@ -106,13 +106,15 @@ extern "C" int pd_matvec_batch_host(pd_grid *g, int64_t batch, const void *u_hos
         const int64_t nf = std::min<int64_t>(per, batch - f0);
         const size_t bytes = field * (size_t)nf;
         const int slot = (int)(k & 1);
-        // upload into the slot once the product of chunk k - 2 has read it
-        if (k >= 2) PD_CUDA(cudaStreamWaitEvent(p->st[0], p->in_free[slot], 0));
+        // upload into the slot once the product of chunk k - 2 has read it (for the
+        // first two chunks: once the previous call's last product that used the slot
+        // has; an event never recorded completes at once)
+        PD_CUDA(cudaStreamWaitEvent(p->st[0], p->in_free[slot], 0));
         PD_CUDA(cudaMemcpyAsync(in[slot], uh + field * (size_t)f0, bytes, cudaMemcpyHostToDevice, p->st[0]));
         PD_CUDA(cudaEventRecord(p->in_ready[slot], p->st[0]));
         // product once uploaded, into an output slot whose download (chunk k - 2) is done
         PD_CUDA(cudaStreamWaitEvent(p->st[1], p->in_ready[slot], 0));
-        if (k >= 2) PD_CUDA(cudaStreamWaitEvent(p->st[1], p->out_free[slot], 0));
+        PD_CUDA(cudaStreamWaitEvent(p->st[1], p->out_free[slot], 0));
         rc = matvec(g, nf, in[slot], outb[slot], flags, p->st[1]);
         if (rc) {   // keep the caller's stream ordered after the copies already queued
             for (auto &st : p->st) {

@@ -80,6 +80,7 @@ struct pd_grid {
     double h = 0, delta = 0;
     double m = 1;                   // delta / h (the kernels' radius M is ceil(m))
     double E = 1, rho = 1, thickness = 1, s0 = 0;
+    double E_max = 1;               // largest modulus (of the field when one is set)
     double alpha = 0, alpha1 = 0;   // micromodulus at E and at E = 1
     int device = 0;
     bool has_cons = false;
@@ -114,6 +115,8 @@ struct pd_grid {
     // CG / Verlet workspace, allocated on first use
     void *ws = nullptr;
     size_t ws_bytes = 0;
+    void *adj_ws = nullptr;         // adjoint sweep workspace (pd_step_adjoint), grown on demand
+    size_t adj_ws_bytes = 0;
     unsigned long long *h_pinned = nullptr;  // small pinned host mailbox
 
     // measured method choice cache: [dtype 0/1] -> 0 unknown, 1 stencil, 2 fft
@@ -149,8 +152,13 @@ struct MatvecArgs {
     bool use_E;           // per-node modulus (direct form)
     bool input_projected; // the caller guarantees P u = u (skip the input projection)
     bool no_tma;          // force the plain FP32 2D stencil
-    bool accurate;        // FP32 TMA stencil: difference form (PD_ACCURATE)
+    bool accurate;        // FP32 3D stencil: difference form (PD_ACCURATE)
+    bool pair_form;       // FP32 TMA 2D stencil: the cancelling pair form (PD_PAIR_FORM)
     double scale;         // multiplies the whole operator (1 = K u)
+    // row window (2D stencils; pd_matvec_rows): the input holds grid rows
+    // [in_row0, in_row0 + in_rows) and the output rows [out_row0, out_row0 + out_rows);
+    // the defaults (whole grid) are set by matvec()
+    int64_t in_row0 = 0, in_rows = -1, out_row0 = 0, out_rows = -1;
     // optional fused reduction: dot_out[b] = sum_p in . out (FP64), needs scratch
     double *dot_partial;  // [gridDim.x * gridDim.y] per batch
     double *dot_out;      // [batch]

@@ -8,6 +8,12 @@
 // near the faces.  c(o) = c(-o), so the sum runs over offset pairs:
 //     sum_o c(o) u~_{p+o} = sum_{o in half} c(o) (u~_{p+o} + u~_{p-o}).
 //
+// In FP32 the same sum is evaluated as differences, (K u)_p = -sum_{o in half}
+// c(o) [m_{p+o} (u_{p+o} - u_p) + m_{p-o} (u_{p-o} - u_p)], m = 1 inside the
+// grid and 0 outside (the in-grid bond sum itself, with no diagonal term to
+// cancel against), so that the FP32 error stays relative to |K u| on smooth
+// fields and on fields with a large constant part.
+//
 // Tiling: a CTA owns 64 x (4R) outputs; each of its 256 threads owns a column
 // of R consecutive y outputs.  The (64 + 2M) x (4R + 2M) halo box of both
 // components is staged in shared memory once.  For each x offset ox a thread
@@ -23,8 +29,11 @@ template <typename T, int M>
 __global__ void __launch_bounds__(kThreads)
 k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
         const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
-        PairTab<T, 2, M> tab, double *dot_partial, double *dot_out, unsigned int *retire)
+        PairTab<T, 2, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
+        int in_row0, int64_t Nin, int out_row0, int out_end)
 {
+    // Rows are grid rows; the input holds rows [in_row0, ...) with plane size Nin, the
+    // output rows [out_row0, out_end) with plane size N (the whole grid: 0, N, 0, ny).
     constexpr int R = rows2d<T, M>();
     constexpr int TX = kTX2, TY = kGY2 * R, SX = TX + 2 * M, SY = TY + 2 * M, WL = R + 2 * M;
     constexpr int NP = PairTab<T, 2, M>::kPairs;
@@ -33,9 +42,9 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
     T *s_y = s_x + SX * SY;
 
     const int64_t b = blockIdx.z;
-    const T *ub = u + b * 2 * N;
-    T *ob = out + b * 2 * N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const T *ub = u + b * 2 * Nin - (int64_t)in_row0 * nx;   // indexed by grid node
+    T *ob = out + b * 2 * N - (int64_t)out_row0 * nx;
+    const int x0 = blockIdx.x * TX, y0 = out_row0 + blockIdx.y * TY;
 
     for (int t = threadIdx.x; t < SX * SY; t += kThreads) {
         const int r = t / SX, c = t - r * SX;
@@ -44,7 +53,7 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
             const int64_t p = (int64_t)gy * nx + gx;
             vx = __ldg(ub + p);
-            vy = __ldg(ub + N + p);
+            vy = __ldg(ub + Nin + p);
             if (project) {
                 const uint8_t m = __ldg(cons + p);
                 if (m & 1) vx = T(0);
@@ -62,6 +71,70 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
     T ax[R], ay[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { ax[r] = T(0); ay[r] = T(0); }
+    constexpr bool DIFF = sizeof(T) == 4;
+    if constexpr (DIFF) {
+        // FP32: differences, terms with the neighbour outside the grid dropped.  The
+        // staged value there is zero, so m (v - u_p) = v - m u_p (one FMA).
+        const int gxt = x0 + tx, gyw = y0 + ty * R - M;   // grid column, grid row of window row 0
+        T ux[R], uy[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            ux[r] = colx[(r + M) * SX];
+            uy[r] = coly[(r + M) * SX];
+        }
+        static_for<0, M + 1>([&](auto OX) {
+            constexpr int ox = decltype(OX)::value;
+            constexpr int My = isqrt_c(M * M - ox * ox);
+            const bool cp = gxt + ox < nx, cm = gxt - ox >= 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                static_for<-My, My + 1>([&](auto OY) {
+                    constexpr int oy = decltype(OY)::value;
+                    if constexpr (ox > 0 || oy > 0) {
+                        constexpr int pi = pair_index2(M, ox, oy);
+                        const int ip = r + M + oy, im = r + M - oy;
+                        const T np = (cp && gyw + ip >= 0 && gyw + ip < ny) ? T(-1) : T(0);
+                        const T nm = (cm && gyw + im >= 0 && gyw + im < ny) ? T(-1) : T(0);
+                        const T sx = dfma(np, ux[r], colx[ip * SX + ox]) + dfma(nm, ux[r], colx[im * SX - ox]);
+                        const T sy = dfma(np, uy[r], coly[ip * SX + ox]) + dfma(nm, uy[r], coly[im * SX - ox]);
+                        const T cxx = tab.v[3 * pi], cxy = tab.v[3 * pi + 1], cyy = tab.v[3 * pi + 2];
+                        if constexpr (oy == 0) {
+                            ax[r] = dfma(cxx, sx, ax[r]);   // axis pair (ox, 0): c_xy = c_yy = 0
+                        } else if constexpr (ox == 0) {
+                            ay[r] = dfma(cyy, sy, ay[r]);   // axis pair (0, oy): c_xx = c_xy = 0
+                        } else {
+                            ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
+                            ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
+                        }
+                    }
+                });
+            }
+        });
+        T dot = T(0);
+        const int gx = x0 + tx;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int gy = y0 + ty * R + r;
+            if (gx < nx && gy < out_end) {
+                const int64_t p = (int64_t)gy * nx + gx;
+                T fx = -ax[r], fy = -ay[r];
+                if (project) {
+                    const uint8_t m = __ldg(cons + p);
+                    if (m & 1) fx = T(0);
+                    if (m & 2) fy = T(0);
+                }
+                fx *= scale;
+                fy *= scale;
+                ob[p] = fx;
+                ob[N + p] = fy;
+                dot = dfma(ux[r], fx, dfma(uy[r], fy, dot));
+            }
+        }
+        if (dot_partial)
+            finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
+                             blockIdx.x + gridDim.x * blockIdx.y, b);
+        return;
+    }
 
     static_for<1, M + 1>([&](auto OX) {
         constexpr int ox = decltype(OX)::value;
@@ -110,7 +183,7 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int gy = y0 + ty * R + r;
-        if (gx < nx && gy < ny) {
+        if (gx < nx && gy < out_end) {
             const int64_t p = (int64_t)gy * nx + gx;
             const T upx = cx[r + M], upy = cy[r + M];
             T kxx = tab.v[3 * NP], kxy = tab.v[3 * NP + 1], kyy = tab.v[3 * NP + 2];
@@ -173,11 +246,16 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     const size_t smem = sizeof(T) * 2 * (kTX2 + 2 * M) * (TY + 2 * M);
     auto kern = k_tbt2d<T, M>;
     allow_smem(kern, smem);
-    dim3 grid((unsigned)((g->n[0] + kTX2 - 1) / kTX2), (unsigned)((g->n[1] + TY - 1) / TY), (unsigned)a.batch);
+    const int64_t nx = g->n[0], ny = g->n[1];
+    const int64_t in_rows = a.in_rows < 0 ? ny : a.in_rows, out_rows = a.out_rows < 0 ? ny : a.out_rows;
+    if ((in_rows != ny || out_rows != ny) && a.dot_partial)
+        return fail(PD_ERR_INVALID, "row windows take no fused dot");
+    dim3 grid((unsigned)((nx + kTX2 - 1) / kTX2), (unsigned)((out_rows + TY - 1) / TY), (unsigned)a.batch);
     const T *kd = sizeof(T) == 4 ? (const T *)g->d_kd32 : (const T *)g->d_kd64;
-    kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], g->N, g->d_cons,
+    kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)nx, (int)ny, out_rows * nx, g->d_cons,
                                       a.project ? 1 : 0, kd, (T)a.scale, make_pairs2<T, M>(g), a.dot_partial,
-                                      a.dot_out, a.retire);
+                                      a.dot_out, a.retire, (int)a.in_row0, in_rows * nx, (int)a.out_row0,
+                                      (int)(a.out_row0 + out_rows));
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }

@@ -29,9 +29,9 @@
 //   * With projection, only the tiles that hold a constrained output (or, for
 //     the input, a constrained node within the halo) take the masking paths;
 //     per-tile flags are computed once per grid (the constraints are fixed).
-//   * DIFF (PD_ACCURATE) sums the differences (u~_{p+o} - u_p) + (u~_{p-o} - u_p)
-//     instead, so that the FP32 error is relative to |K u| even for smooth
-//     fields (see tile_pairs); the solvers use it, the plain product does not.
+// k_tbt2d_tma is the pair form (PD_PAIR_FORM, kept for comparison): its terms
+// cancel on smooth fields.  The default FP32 product is k_tbt2d_acc (below):
+// the same pipeline, with the sums taken as differences of nearby values.
 // Used for FP32 grids whose row length is a multiple of 4 floats (TMA stride
 // rule); other grids use the plain kernel.
 #include <cuda.h>
@@ -295,6 +295,226 @@ k_tbt2d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ u
     }
 }
 
+// Unsigned division by a divisor fixed per launch, by multiplication and shifts
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, the unsigned N-bit algorithm): the tile walk
+// decomposes tile numbers without the ~20-instruction integer division.
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
+{
+    const uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// Accurate FP32 product (the default for FP32 2D grids): the same persistent
+// TMA pipeline, with the pair sums evaluated as differences (tile_eg for warps
+// whose outputs all have their whole horizon inside the grid, tile_diff with
+// out-of-grid terms dropped elsewhere), so that K u = -a with no diagonal term
+// to cancel against.  The coefficients carry -scale.  Two CTAs per SM up to
+// M = 4 (about 120 registers); one beyond, where the shared differences of the
+// interior form need up to 250 registers (measured faster than two CTAs with
+// spills, or the plain difference form).
+constexpr int kAccStages = 3;   // halo tiles in flight or in use per CTA
+#ifndef PD_ACC_GY
+#define PD_ACC_GY 4
+#endif
+#ifndef PD_ACC_MINB
+#define PD_ACC_MINB 2
+#endif
+#ifndef PD_ACC_SLIDE
+#define PD_ACC_SLIDE 0
+#endif
+template <int M, int GY>
+__global__ void __launch_bounds__(64 * GY, (M <= 4 ? PD_ACC_MINB : 1))
+k_tbt2d_acc(const __grid_constant__ CUtensorMap map, float *__restrict__ out, int nx, int ny, int64_t N,
+            int ybuf0, int ty0, int yend, int tiles_x, int tiles_y, FastDiv div_tx, FastDiv div_ty, int ntiles,
+            const uint8_t *__restrict__ cons,
+            int project_in, int project_out, const uint8_t *__restrict__ tflags, AccTab<M> tab,
+            double *dot_partial, double *dot_out, unsigned int *retire, int *err)
+{
+    constexpr int TH = 64 * GY, TYt = GY * kRt;   // threads; tile rows
+    constexpr int XL = x_lead<M>(), BX = box_x<M>(), BY = TYt + 2 * M;
+    constexpr int PLANE = BX * BY;
+    constexpr uint32_t kBytes = 2u * PLANE * sizeof(float);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *const sbase = reinterpret_cast<float *>(smem_raw);   // buffer k at sbase + 2 * PLANE * k
+    __shared__ __align__(8) uint64_t bars[kAccStages];    // full: the tile has landed
+    __shared__ __align__(8) uint64_t empty[kAccStages];   // every warp has read the buffer
+    __shared__ int s_abort;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kAccStages; ++k) {
+            mbar_init(&bars[k], 1);
+            mbar_init(&empty[k], TH / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+    const bool lockstep = project_in != 0 || M > 3;
+    const int lane = threadIdx.x & 31;
+    const int tx = threadIdx.x % kTXt, ty = threadIdx.x / kTXt;
+    // Tile t: tile row R = t / tiles_x (field b = R / tiles_y, row ty0 + R % tiles_y of
+    // the grid's tiling); the columns of a row are rotated by R so that a persistent
+    // CTA meets edge tiles as often as the others.  Rows are grid rows throughout;
+    // the input buffer starts at grid row ybuf0 and the output at grid row 32 ty0,
+    // and outputs are stored up to grid row yend (the whole grid: 0, 0, ny).
+    auto tile_coords = [&](int t, int &x0, int &y0, int &b) {
+        const uint32_t R = fdiv((uint32_t)t, div_tx);
+        uint32_t c = (uint32_t)t - R * (uint32_t)tiles_x + R;
+        c -= fdiv(c, div_tx) * (uint32_t)tiles_x;
+        const uint32_t bq = fdiv(R, div_ty);
+        x0 = (int)c * kTXt;
+        y0 = ty0 * kTYt + (int)(R - bq * (uint32_t)tiles_y) * TYt;
+        b = (int)bq;
+    };
+    auto issue = [&](int t, int which) {
+        int x0, y0, b;
+        tile_coords(t, x0, y0, b);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bars[which], kBytes);
+        tma_load_3d(sbase + 2 * PLANE * which, &map, x0 - XL, y0 - M - ybuf0, 2 * b, &bars[which]);
+    };
+
+    int it = 0, n_issued = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kAccStages - 1; ++k) {
+            const int64_t tk = blockIdx.x + (int64_t)k * gridDim.x;
+            if (tk < ntiles) {
+                issue((int)tk, k);
+                ++n_issued;
+            }
+        }
+    double dot_blk_total = 0.0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int cur = it % kAccStages;
+        if (threadIdx.x == 0) {
+            const int64_t tn = t + (int64_t)(kAccStages - 1) * gridDim.x;
+            if (tn < ntiles) {
+                const int prev = (it + kAccStages - 1) % kAccStages;
+                if (lockstep || it == 0 || mbar_wait(&empty[prev], ((it - 1) / kAccStages) & 1)) {
+                    issue((int)tn, prev);
+                    ++n_issued;
+                } else {
+                    atomicExch(err, 1);
+                    s_abort = 1;
+                }
+            }
+        }
+        const bool ok = mbar_wait(&bars[cur], (it / kAccStages) & 1);
+        if (lockstep) {
+            if (!ok) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            }
+            __syncthreads();
+            if (s_abort) break;
+        } else if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            }
+            break;
+        }
+        int x0, y0, b;
+        tile_coords(t, x0, y0, b);
+        float *sx = sbase + 2 * PLANE * cur, *sy = sx + PLANE;
+        bool pin = false, pout = false;
+        if (project_in | project_out) {
+            const uint8_t tf = tflags ? __ldg(tflags + (y0 / kTYt) * tiles_x + x0 / kTXt) : 3;
+            pin = project_in && (tf & 2);
+            pout = project_out && (tf & 1);
+        }
+        if (pin) {
+            for (int e = threadIdx.x; e < PLANE; e += TH) {
+                const int gx = x0 - XL + e % BX, gy = y0 - M + e / BX;
+                if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+                    const uint8_t m = __ldg(cons + (int64_t)gy * nx + gx);
+                    if (m & 1) sx[e] = 0.f;
+                    if (m & 2) sy[e] = 0.f;
+                }
+            }
+            __syncthreads();
+        }
+        const int gx = x0 + tx, gy0 = y0 + ty * kRt;
+        const float *colx = sx + (ty * kRt) * BX + tx + XL, *coly = sy + (ty * kRt) * BX + tx + XL;
+        // every output of this warp keeps its whole horizon inside the grid
+        const bool tile_in = (x0 >= M) && (x0 + kTXt <= nx - M) && (y0 >= M) && (y0 + TYt <= ny - M);
+        const bool warp_in = tile_in || (__all_sync(0xffffffffu, gx >= M && gx < nx - M) && gy0 >= M &&
+                                         gy0 + kRt <= ny - M);
+        u64 a1[kRt], a2[kRt];
+        if (warp_in) {
+            if constexpr (PD_ACC_SLIDE)
+                tile_eg_slide<M>(colx, coly, tab, a1, a2);
+            else
+                tile_eg<M>(colx, coly, tab, a1, a2);
+        }
+        else
+            tile_diff<M, true>(colx, coly, tab, a1, a2, gx, nx, gy0 - M, ny);
+
+        float *o0 = out + (int64_t)b * 2 * N + (int64_t)(gy0 - ty0 * kTYt) * nx + gx;
+        const bool full = (x0 + kTXt <= nx) && (y0 + TYt <= yend);
+        if (full && !pout && !dot_partial) {
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                o0[(int64_t)r * nx] = x1.x + x2.y;
+                o0[(int64_t)r * nx + N] = x1.y + x2.x;
+            }
+        } else {
+            const uint8_t *m0 = cons + (int64_t)gy0 * nx + gx;
+            float dot = 0.f;
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const int gy = gy0 + r;
+                if (!full && !(gx < nx && gy < yend)) continue;
+                const float2 x1 = upk(a1[r]), x2 = upk(a2[r]);
+                float fx = x1.x + x2.y, fy = x1.y + x2.x;
+                if (pout) {
+                    const uint8_t m = __ldg(m0 + (int64_t)r * nx);
+                    if (m & 1) fx = 0.f;
+                    if (m & 2) fy = 0.f;
+                }
+                o0[(int64_t)r * nx] = fx;
+                o0[(int64_t)r * nx + N] = fy;
+                if (dot_partial)
+                    dot = __fmaf_rn(colx[(r + M) * BX], fx, __fmaf_rn(coly[(r + M) * BX], fy, dot));
+            }
+            if (dot_partial) dot_blk_total += (double)dot;
+        }
+        if (lockstep) {
+            __syncthreads();
+        } else {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[cur]);
+        }
+    }
+    __syncthreads();
+    if (s_abort) {
+        if (threadIdx.x == 0)
+            for (int k = it; k < n_issued; ++k) mbar_wait(&bars[k % kAccStages], (k / kAccStages) & 1);
+        return;
+    }
+    if (dot_partial) {
+        __shared__ double red[TH / 32];
+        const double s = block_sum(dot_blk_total, red);
+        grid_finish(s, gridDim.x, blockIdx.x, dot_partial, dot_out, retire, red);
+    }
+}
+
 // Per 64 x 32 tile: bit 0 when an output node is constrained, bit 1 when a node
 // within M of the tile (the part of the halo box the stencil reads) is.
 template <int M>
@@ -315,15 +535,28 @@ __global__ void k_tma_flags(const uint8_t *__restrict__ cons, int nx, int ny, in
 }
 
 // ------------------------------------------------------------------ host side
-template <int M, bool DIFF>
+template <int M, bool ACC>
 int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
     constexpr int BX = box_x<M>(), BY = box_y<M>();
     const int nx = (int)g->n[0], ny = (int)g->n[1];
+    // row window (pd_matvec_rows): rows of the input buffer and of the output
+    const int in_row0 = (int)a.in_row0, in_rows = a.in_rows < 0 ? ny : (int)a.in_rows;
+    const int out_row0 = (int)a.out_row0, out_rows = a.out_rows < 0 ? ny : (int)a.out_rows;
+    const bool window = in_rows != ny || out_rows != ny;
+    if (window && (!ACC || out_row0 % kTYt != 0 || a.dot_partial))
+        return fail(PD_ERR_INVALID, "row windows need the default FP32 form, tile-aligned rows, no fused dot");
+    constexpr int GY = ACC ? PD_ACC_GY : kGY2, TH = 64 * GY, TYt = GY * kRt, BYa = TYt + 2 * M;
     CUtensorMap map;
-    if (!make_map<M>(&map, a.u, nx, ny, a.batch)) return fail(PD_ERR_CUDA, "tensor map encode failed");
-    const size_t smem = (size_t)kStages * 2 * BX * BY * sizeof(float);
-    auto kern = k_tbt2d_tma<M, DIFF>;
+    if (!make_map<M>(&map, a.u, nx, in_rows, a.batch, ACC ? BYa : BY))
+        return fail(PD_ERR_CUDA, "tensor map encode failed");
+    const size_t smem = ACC ? (size_t)kAccStages * 2 * BX * BYa * sizeof(float)
+                            : (size_t)kStages * 2 * BX * BY * sizeof(float);
+    void *kern;
+    if constexpr (ACC)
+        kern = (void *)k_tbt2d_acc<M, GY>;
+    else
+        kern = (void *)k_tbt2d_tma<M, false>;
     static int attr_done[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -332,18 +565,18 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         attr_done[dev] = 1;
     }
-    const int tiles_x = (nx + kTXt - 1) / kTXt, tiles_y = (ny + kTYt - 1) / kTYt;
+    const int tiles_x = (nx + kTXt - 1) / kTXt, tiles_y = (out_rows + TYt - 1) / TYt;
     const int64_t nt = (int64_t)tiles_x * tiles_y * a.batch;
     if (nt > (1ll << 30)) return fail(PD_ERR_INVALID, "too many tiles");
     int occ = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TH, smem);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (occ < 1) occ = 1;
     int blocks = (int)std::min<int64_t>(nt, (int64_t)occ * sms);
     if (a.dot_partial && a.batch != 1) return fail(PD_ERR_INVALID, "fused dot needs a single field");
     const uint8_t *tflags = nullptr;
     if (a.project) {   // the constraints are fixed per grid: the flags are computed once
-        const int nts = tiles_x * tiles_y;
+        const int nts = tiles_x * ((ny + kTYt - 1) / kTYt);   // per tile of the whole grid
         if (g->tma_flags_M != M) {
             if (!g->d_tma_flags) PD_CUDA(cudaMalloc(&g->d_tma_flags, (size_t)nts));
             k_tma_flags<M><<<(nts + 127) / 128, 128, 0, s>>>(g->d_cons, nx, ny, tiles_x, nts, g->d_tma_flags);
@@ -352,10 +585,20 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
         }
         tflags = g->d_tma_flags;
     }
-    kern<<<blocks, kThreads, smem, s>>>(map, (const float *)a.u, (float *)a.out, nx, ny, g->N, tiles_x, tiles_y,
-                                        (int)nt, g->d_cons, (a.project && !a.input_projected) ? 1 : 0,
-                                        a.project ? 1 : 0, tflags, g->d_kd32, (float)a.scale, make_pack<M>(g),
-                                        a.dot_partial, a.dot_out, a.retire, g->d_err);
+    const int pin = (a.project && !a.input_projected) ? 1 : 0, pout = a.project ? 1 : 0;
+    if constexpr (ACC) {
+        const FastDiv dtx = make_fastdiv((uint32_t)tiles_x), dty = make_fastdiv((uint32_t)tiles_y);
+        k_tbt2d_acc<M, GY><<<blocks, TH, smem, s>>>(map, (float *)a.out, nx, ny, (int64_t)out_rows * nx, in_row0,
+                                                      out_row0 / kTYt, out_row0 + out_rows, tiles_x, tiles_y, dtx,
+                                                      dty, (int)nt, g->d_cons, pin, pout, tflags,
+                                                      make_acc<M>(g, a.scale), a.dot_partial, a.dot_out, a.retire,
+                                                      g->d_err);
+    } else {
+        k_tbt2d_tma<M, false><<<blocks, kThreads, smem, s>>>(map, (const float *)a.u, (float *)a.out, nx, ny, g->N,
+                                                             tiles_x, tiles_y, (int)nt, g->d_cons, pin, pout, tflags,
+                                                             g->d_kd32, (float)a.scale, make_pack<M>(g),
+                                                             a.dot_partial, a.dot_out, a.retire, g->d_err);
+    }
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -389,7 +632,7 @@ bool tma_stencil_eligible(const pd_grid *g, const MatvecArgs &a, bool f64)
 int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
 #define PD_TMA_CASE(m) \
-    case m: return a.accurate ? run<m, true>(g, a, s) : run<m, false>(g, a, s);
+    case m: return a.pair_form ? run<m, false>(g, a, s) : run<m, true>(g, a, s);
     switch (g->M) {
         PD_TMA_CASE(1)
         PD_TMA_CASE(2)

@@ -47,8 +47,12 @@ template <typename T, int M, bool DIFF>
 __global__ void __launch_bounds__(kThreads)
 k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
         const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
-        PairTab<T, 3, M> tab, double *dot_partial, double *dot_out, unsigned int *retire)
+        PairTab<T, 3, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
+        int in_z0, int64_t Nin, int out_z0, int out_zend)
 {
+    // Planes are grid planes; the input holds planes [in_z0, ...) with component size
+    // Nin, the output planes [out_z0, out_zend) with component size N (the whole
+    // grid: 0, N, 0, nz).
     constexpr int R = rows3d<T, M>();
     constexpr int TX = kTX3, TY = kTY3, SX = TX + 2 * M, SY = TY + 2 * M, SZ = R + 2 * M;
     constexpr int PL = SX * SY * SZ;
@@ -58,9 +62,9 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
 
     const int zt = blockIdx.z % nzt;
     const int64_t b = blockIdx.z / nzt;
-    const T *ub = u + b * 3 * N;
-    T *ob = out + b * 3 * N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = zt * R;
+    const T *ub = u + b * 3 * Nin - (int64_t)in_z0 * ny * nx;   // indexed by grid node
+    T *ob = out + b * 3 * N - (int64_t)out_z0 * ny * nx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = out_z0 + zt * R;
 
     for (int t = threadIdx.x; t < PL; t += kThreads) {
         const int zz = t / (SX * SY), rem = t - zz * SX * SY;
@@ -70,8 +74,8 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
             const int64_t p = ((int64_t)gz * ny + gy) * nx + gx;
             v0 = __ldg(ub + p);
-            v1 = __ldg(ub + N + p);
-            v2 = __ldg(ub + 2 * N + p);
+            v1 = __ldg(ub + Nin + p);
+            v2 = __ldg(ub + 2 * Nin + p);
             if (project) {
                 const uint8_t m = __ldg(cons + p);
                 if (m & 1) v0 = T(0);
@@ -156,7 +160,7 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int gz = z0 + r;
-        if (gx < nx && gy < ny && gz < nz) {
+        if (gx < nx && gy < ny && gz < out_zend) {
             const int64_t p = ((int64_t)gz * ny + gy) * nx + gx;
             const T *kk = tab.v + 6 * NP;
             T k0 = kk[0], k1 = kk[1], k2 = kk[2], k3 = kk[3], k4 = kk[4], k5 = kk[5];
@@ -243,14 +247,19 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     const size_t smem = sizeof(T) * 3 * (kTX3 + 2 * M) * (kTY3 + 2 * M) * (R + 2 * M);
     auto kern = k_tbt3d<T, M, DIFF>;
     allow_smem(kern, smem);
-    const int nzt = (int)((g->n[2] + R - 1) / R);
+    const int64_t nz = g->n[2], plane = g->n[0] * g->n[1];
+    const int64_t in_planes = a.in_rows < 0 ? nz : a.in_rows, out_planes = a.out_rows < 0 ? nz : a.out_rows;
+    if ((in_planes != nz || out_planes != nz) && a.dot_partial)
+        return fail(PD_ERR_INVALID, "plane windows take no fused dot");
+    const int nzt = (int)((out_planes + R - 1) / R);
     if ((int64_t)nzt * a.batch > 65535) return fail(PD_ERR_INVALID, "3D batch too large for one launch");
     dim3 grid((unsigned)((g->n[0] + kTX3 - 1) / kTX3), (unsigned)((g->n[1] + kTY3 - 1) / kTY3),
               (unsigned)(nzt * a.batch));
     const T *kd = sizeof(T) == 4 ? (const T *)g->d_kd32 : (const T *)g->d_kd64;
-    kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], (int)g->n[2], nzt,
-                                      g->N, g->d_cons, a.project ? 1 : 0, kd, (T)a.scale, make_pairs3<T, M>(g),
-                                      a.dot_partial, a.dot_out, a.retire);
+    kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], (int)nz, nzt,
+                                      out_planes * plane, g->d_cons, a.project ? 1 : 0, kd, (T)a.scale,
+                                      make_pairs3<T, M>(g), a.dot_partial, a.dot_out, a.retire, (int)a.in_row0,
+                                      in_planes * plane, (int)a.out_row0, (int)(a.out_row0 + out_planes));
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }

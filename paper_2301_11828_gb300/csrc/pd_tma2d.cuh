@@ -38,6 +38,12 @@ __device__ __forceinline__ u64 fsub2(u64 a, u64 b)
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b)
+{
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 __device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
 {
     u64 d;
@@ -207,6 +213,242 @@ __device__ __forceinline__ void tile_pairs(const float *colx, const float *coly,
     });
 }
 
+// ---- the accurate (cancellation-free) form of the pair sums
+//
+// K u at node p is -sum_{o in half} c(o) s_o with s_o = (u~_{p+o} - u_p) + (u~_{p-o} - u_p)
+// (u~ the input, the sum over in-grid neighbours only).  Written this way every
+// term is a difference of nearby values, so the FP32 rounding error stays
+// relative to |K u| even where the field is smooth or carries a large constant
+// part (the pair form Kd u_p - sum c (u_{p+o} + u_{p-o}) loses the digits that
+// cancel).  Two evaluations of the same sum:
+//
+//  * tile_eg (every neighbour of the warp's outputs inside the grid): the pair
+//    sums are regrouped into horizontal second and central differences shared
+//    by the outputs of a column, plus vertical second differences in the
+//    thread's own column (below);
+//  * tile_diff<M, true> (some neighbour outside the grid): the plain difference
+//    form with every term whose neighbour lies outside the grid dropped, i.e.
+//    the in-grid bond sum of Eq. mat:f1 itself (no diagonal table, no
+//    cancelling edge self-term).
+//
+// AccTab holds the coefficients premultiplied by -scale, so that
+//   (K u)_x = a1.x + a2.y,  (K u)_y = a1.y + a2.x.
+template <int M>
+struct __align__(16) AccTab {
+    static constexpr int kPairs = count_offsets(2, M) / 2;
+    // per pair (pair_index2 order): c1 = (cxx, cyy), c2 = (cxy, cxy);
+    // then per k = 1..M the vertical block Cbar(k) = (cxx, cyy)
+    float v[4 * kPairs + 2 * M];
+};
+
+template <int M>
+__device__ __forceinline__ u64 acc_c1(const AccTab<M> &t, int pi) { return *reinterpret_cast<const u64 *>(&t.v[4 * pi]); }
+template <int M>
+__device__ __forceinline__ u64 acc_c2(const AccTab<M> &t, int pi) { return *reinterpret_cast<const u64 *>(&t.v[4 * pi + 2]); }
+template <int M>
+__device__ __forceinline__ u64 acc_w(const AccTab<M> &t, int k)
+{
+    return *reinterpret_cast<const u64 *>(&t.v[4 * AccTab<M>::kPairs + 2 * (k - 1)]);
+}
+
+// The interior sums.  With H_ox(i) = u(x+ox, i) - u(x, i) and, in the thread's
+// own column, V_k(r) = u(x, r+k) - u(x, r), each pair sum splits as
+//   s_(ox,oy) = H_ox(r+oy) + H_-ox(r-oy) + W_|oy|(r),   W_k = V_k + V_-k.
+// The vertical second difference W_k(r) is shared by every pair with |oy| = k;
+// it enters once with Cbar(k) = sum of c(o) over those pairs (diagonal: the xy
+// entries of (ox, k) and (ox, -k) cancel exactly).  The pairs (ox, k) and
+// (ox, -k) are then taken together: with E(i) = H_ox(i) + H_-ox(i) (the
+// horizontal second difference of row i) and G(i) = u(x+ox, i) - u(x-ox, i),
+//   s_(ox,k) + s_(ox,-k) = E(r+k) + E(r-k) + 2 W_k(r),
+//   s_(ox,k) - s_(ox,-k) = G(r+k) - G(r-k),
+// and since c(ox,-k) has the xx / yy entries of c(ox,k) and the opposite xy
+// entry, the two pairs contribute (cxx, cyy) (E(r+k) + E(r-k)) to a1 and
+// (cxy, cxy) (G(r+k) - G(r-k)) to a2.  E and G are formed once per row and
+// column offset and shared by the column's outputs; the axis pair (ox, 0) is
+// cxx E(r) on the x component alone.  Every operand is a difference of nearby
+// values.  At M = 3: about 42 FP32x2 and 5 FP32 operations per output (the
+// plain difference form takes 64, the pair form 36 with its cancellation).
+template <int M>
+__device__ __forceinline__ void tile_eg(const float *colx, const float *coly, const AccTab<M> &tab,
+                                        u64 (&a1)[kRt], u64 (&a2)[kRt])
+{
+    constexpr int BX = box_x<M>(), WL = kRt + 2 * M;
+    u64 w0[WL];
+#pragma unroll
+    for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
+    // vertical part: V_k(j) = u(x, j + k) - u(x, j); W_k(r) = V_k(r + M) - V_k(r + M - k)
+    static_for<1, M + 1>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        const u64 c = acc_w(tab, k);
+        u64 V[WL];
+#pragma unroll
+        for (int j = M - k; j < kRt + M; ++j) V[j] = fsub2(w0[j + k], w0[j]);
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) {
+            const u64 W = fsub2(V[r + M], V[r + M - k]);
+            if constexpr (k == 1)
+                a1[r] = fmul2(c, W);
+            else
+                a1[r] = ffma2(c, W, a1[r]);
+        }
+    });
+#pragma unroll
+    for (int r = 0; r < kRt; ++r) a2[r] = 0ull;
+    static_for<1, M + 1>([&](auto OX) {
+        constexpr int ox = decltype(OX)::value;
+        constexpr int My = isqrt_c(M * M - ox * ox);
+        u64 E[WL], G[WL];
+#pragma unroll
+        for (int i = M - My; i < kRt + M + My; ++i) {
+            const u64 wp = pk(colx[i * BX + ox], coly[i * BX + ox]);
+            const u64 wm = pk(colx[i * BX - ox], coly[i * BX - ox]);
+            E[i] = fadd2(fsub2(wp, w0[i]), fsub2(wm, w0[i]));
+            if constexpr (My > 0) G[i] = fsub2(wp, wm);
+        }
+        {   // axis pair (ox, 0): x component only
+            const float cxx = tab.v[4 * pair_index2(M, ox, 0)];
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const float2 e = upk(E[r + M]);
+                float2 acc = upk(a1[r]);
+                acc.x = __fmaf_rn(cxx, e.x, acc.x);
+                a1[r] = pk(acc.x, acc.y);
+            }
+        }
+        static_for<1, My + 1>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            constexpr int pi = pair_index2(M, ox, k);
+            const u64 c1 = acc_c1(tab, pi), c2 = acc_c2(tab, pi);
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                a1[r] = ffma2(c1, fadd2(E[r + M + k], E[r + M - k]), a1[r]);
+                a2[r] = ffma2(c2, fsub2(G[r + M + k], G[r + M - k]), a2[r]);
+            }
+        });
+    });
+}
+
+// tile_eg with the rows of a column offset formed as the outputs walk down the
+// column: E and G of a row are computed when the first output needs them, so
+// only 2 My + 1 rows of them are live (same operations, fewer registers).
+template <int M>
+__device__ __forceinline__ void tile_eg_slide(const float *colx, const float *coly, const AccTab<M> &tab,
+                                              u64 (&a1)[kRt], u64 (&a2)[kRt])
+{
+    constexpr int BX = box_x<M>(), WL = kRt + 2 * M;
+    u64 w0[WL];
+#pragma unroll
+    for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
+    static_for<1, M + 1>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        const u64 c = acc_w(tab, k);
+        u64 V[WL];
+#pragma unroll
+        for (int j = M - k; j < kRt + M; ++j) V[j] = fsub2(w0[j + k], w0[j]);
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) {
+            const u64 W = fsub2(V[r + M], V[r + M - k]);
+            if constexpr (k == 1)
+                a1[r] = fmul2(c, W);
+            else
+                a1[r] = ffma2(c, W, a1[r]);
+        }
+    });
+#pragma unroll
+    for (int r = 0; r < kRt; ++r) a2[r] = 0ull;
+    static_for<1, M + 1>([&](auto OX) {
+        constexpr int ox = decltype(OX)::value;
+        constexpr int My = isqrt_c(M * M - ox * ox);
+        const float cxx = tab.v[4 * pair_index2(M, ox, 0)];
+        u64 E[WL], G[WL];
+        auto row = [&](int i) {
+            const u64 wp = pk(colx[i * BX + ox], coly[i * BX + ox]);
+            const u64 wm = pk(colx[i * BX - ox], coly[i * BX - ox]);
+            E[i] = fadd2(fsub2(wp, w0[i]), fsub2(wm, w0[i]));
+            if constexpr (My > 0) G[i] = fsub2(wp, wm);
+        };
+#pragma unroll
+        for (int i = M - My; i < M + My; ++i) row(i);
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) {
+            row(r + M + My);
+            const float2 e = upk(E[r + M]);
+            float2 acc = upk(a1[r]);
+            acc.x = __fmaf_rn(cxx, e.x, acc.x);
+            u64 t1 = pk(acc.x, acc.y), t2 = a2[r];
+            static_for<1, My + 1>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                constexpr int pi = pair_index2(M, ox, k);
+                t1 = ffma2(acc_c1(tab, pi), fadd2(E[r + M + k], E[r + M - k]), t1);
+                t2 = ffma2(acc_c2(tab, pi), fsub2(G[r + M + k], G[r + M - k]), t2);
+            });
+            a1[r] = t1;
+            a2[r] = t2;
+        }
+    });
+}
+
+// Plain difference form, s_o = (u~_{p+o} - u_p) + (u~_{p-o} - u_p) for every
+// pair, walked column offset by column offset with the outputs of a column in
+// the outer loop, so that only a few window rows per column are live.  With
+// MASK (warps holding an output whose horizon leaves the grid), each term whose
+// neighbour lies outside [0,nx) x [0,ny) is dropped: that is the in-grid bond
+// sum of Eq. mat:f1 itself (no diagonal table, no cancelling edge self-term).
+// gx is the thread's grid column, gyw the grid row of window row 0.  The staged
+// box must hold zeros outside the grid (the tensor map's fill).
+template <int M, bool MASK>
+__device__ __forceinline__ void tile_diff(const float *colx, const float *coly, const AccTab<M> &tab,
+                                          u64 (&a1)[kRt], u64 (&a2)[kRt], int gx, int nx, int gyw, int ny)
+{
+    constexpr int BX = box_x<M>(), WL = kRt + 2 * M;
+    static_assert(WL <= 32, "row mask is one word");
+    uint32_t rowok = 0;
+    if constexpr (MASK) {
+#pragma unroll
+        for (int i = 0; i < WL; ++i)
+            if (gyw + i >= 0 && gyw + i < ny) rowok |= 1u << i;
+    }
+    u64 ctr[kRt];
+#pragma unroll
+    for (int r = 0; r < kRt; ++r) {
+        a1[r] = 0ull;
+        a2[r] = 0ull;
+        ctr[r] = pk(colx[(r + M) * BX], coly[(r + M) * BX]);
+    }
+    static_for<0, M + 1>([&](auto OX) {
+        constexpr int ox = decltype(OX)::value;
+        constexpr int My = isqrt_c(M * M - ox * ox);
+        const bool cp = gx + ox < nx, cm = gx - ox >= 0;
+#pragma unroll
+        for (int r = 0; r < kRt; ++r) {
+            static_for<-My, My + 1>([&](auto OY) {
+                constexpr int oy = decltype(OY)::value;
+                if constexpr (ox > 0 || oy > 0) {
+                    constexpr int pi = pair_index2(M, ox, oy);
+                    const int ip = r + M + oy, im = r + M - oy;
+                    const u64 vp = pk(colx[ip * BX + ox], coly[ip * BX + ox]);
+                    const u64 vm = pk(colx[im * BX - ox], coly[im * BX - ox]);
+                    u64 dp, dm;
+                    if constexpr (MASK) {
+                        // outside the grid the staged value is the tensor map's zero fill, so
+                        // m (v - u_p) = v - m u_p with m = 1 inside and 0 outside: one FMA
+                        const float fp = (cp && ((rowok >> ip) & 1u)) ? -1.f : 0.f;
+                        const float fm = (cm && ((rowok >> im) & 1u)) ? -1.f : 0.f;
+                        dp = ffma2(pk(fp, fp), ctr[r], vp);
+                        dm = ffma2(pk(fm, fm), ctr[r], vm);
+                    } else {
+                        dp = fsub2(vp, ctr[r]);
+                        dm = fsub2(vm, ctr[r]);
+                    }
+                    const u64 sum = fadd2(dp, dm);
+                    a1[r] = ffma2(acc_c1(tab, pi), sum, a1[r]);
+                    if constexpr (ox != 0 && oy != 0) a2[r] = ffma2(acc_c2(tab, pi), sum, a2[r]);
+                }
+            });
+        }
+    });
+}
+
 // ---- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -218,13 +460,13 @@ EncodeTiledFn encode_fn();
 // Tensor map over `batch` fields of two FP32 planes [2*batch][ny][nx] with the
 // halo box of horizon M; false if the driver rejects it.
 template <int M>
-inline bool make_map(CUtensorMap *map, const void *base, int nx, int ny, int64_t batch)
+inline bool make_map(CUtensorMap *map, const void *base, int nx, int ny, int64_t batch, int box_h = box_y<M>())
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(2 * batch)};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)box_x<M>(), (cuuint32_t)box_y<M>(), 2};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x<M>(), (cuuint32_t)box_h, 2};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -253,6 +495,38 @@ PackTab<M> make_pack(const pd_grid *g)
     for (int oy = 1; oy <= M; ++oy) put(0, oy);
     constexpr int NP = PackTab<M>::kPairs;
     for (int i = 0; i < 3; ++i) t.v[4 * NP + i] = (float)tot[i];
+    return t;
+}
+
+// Coefficients of the accurate form, premultiplied by -scale (see AccTab).
+template <int M>
+AccTab<M> make_acc(const pd_grid *g, double scale)
+{
+    AccTab<M> t{};
+    constexpr int NP = AccTab<M>::kPairs;
+    double c[6], wb[M + 1][2] = {};
+    auto put = [&](int ox, int oy) {
+        const int pi = pair_index2(M, ox, oy);
+        coef_of(g, ox, oy, 0, false, c);   // xx, xy, yy
+        t.v[4 * pi + 0] = (float)(-scale * c[0]);
+        t.v[4 * pi + 1] = (float)(-scale * c[2]);
+        t.v[4 * pi + 2] = (float)(-scale * c[1]);
+        t.v[4 * pi + 3] = (float)(-scale * c[1]);
+        const int k = oy < 0 ? -oy : oy;
+        if (k > 0) {
+            wb[k][0] += c[0];
+            wb[k][1] += c[2];
+        }
+    };
+    for (int ox = 1; ox <= M; ++ox) {
+        const int My = isqrt_c(M * M - ox * ox);
+        for (int oy = -My; oy <= My; ++oy) put(ox, oy);
+    }
+    for (int oy = 1; oy <= M; ++oy) put(0, oy);
+    for (int k = 1; k <= M; ++k) {
+        t.v[4 * NP + 2 * (k - 1)] = (float)(-scale * wb[k][0]);
+        t.v[4 * NP + 2 * (k - 1) + 1] = (float)(-scale * wb[k][1]);
+    }
     return t;
 }
 

@@ -153,3 +153,114 @@ def test_kw_block_crack_loop_follows_oracle(pd):
     assert total > 0
     bsn = bs.cpu().numpy().reshape(g.N, g.nnb)
     assert (bsn > 0).sum() == 2 * total and bsn.max() <= 60
+
+
+@pytest.mark.parametrize("nside", [40, 96])
+def test_stable_dt_matches_oracle_symbol(pd, nside):
+    """pd_stable_dt: 2 sqrt(rho / (E_max Lambda)) with Lambda the largest
+    eigenvalue of the unit-modulus symbol over the 2n periodic grid, as computed
+    from the oracle's symbol (Algorithm 3); E_max of the modulus field."""
+    w, cons, vp = _crack_setup(nside)
+    E = w.extra["E_field"]
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=cons, E_field=torch.tensor(E, device="cuda"), s0=w.s0)
+    assert abs(g.stable_dt() / _stable_dt(w, E.max()) - 1.0) < 1e-12
+    g2 = pd.Grid(2, w.n, w.h, w.M, E=2.5, rho=3.0)
+    ref = 2.0 * np.sqrt(3.0 / 2.5) * _stable_dt(w, 1.0) / (2.0 * np.sqrt(w.rho / 1.0))
+    assert abs(g2.stable_dt() / ref - 1.0) < 1e-12
+
+
+def test_crack_plate_512_full_run_against_oracle(pd):
+    """The 2D pre-cracked plate at its stated size and length (Sec. 5.2; Algorithm
+    2 with Eqs. mu and fra:s1): 512^2, 2000 steps at 0.8 x the stable step of
+    the actual modulus field.  The run is compared with the oracle chunk by
+    chunk: every 100 steps the oracle restarts from the GPU's state (same u, v
+    and bond set, bit for bit) and runs the same 100 steps; the broken sets
+    must then be identical and the states agree to rounding.  A chunk in which
+    a bond sits on the threshold to rounding could break on one side only; the
+    summary allows at most one such chunk, with at most two bonds of difference."""
+    w, cons, vp = _crack_setup(512)
+    E = w.extra["E_field"]
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=cons, E_field=torch.tensor(E, device="cuda"), s0=w.s0)
+    g.break_segment(w.extra["notch"], w.extra["notch_den"])
+    dt = 0.8 * g.stable_dt()
+    assert abs(dt / (0.8 * _stable_dt(w, E.max())) - 1.0) < 1e-12
+    vpt = torch.tensor(vp, device="cuda")
+    u = torch.zeros((2,) + E.shape, dtype=torch.float64, device="cuda")
+    v = vpt.clone()
+    al1 = oracle.alpha(2, 1.0, w.delta)
+    chunk, nsteps = 100, 2000
+    odd, total_gpu, total_or = 0, 0, 0
+    for c in range(nsteps // chunk):
+        mu = mask_to_mu(g.bond_mask().cpu().numpy(), g.nnb)
+        uo, vo = u.cpu().numpy().copy(), v.cpu().numpy().copy()
+        st = g.step(u, v, None, nsteps=chunk, dt=dt, v_prescribed=vpt)
+        nb = oracle.vv(2, w.n, w.h, w.M, al1, uo, vo, chunk, dt, E=E, mu=mu, s0=w.s0, cons=cons, vpres=vp)
+        total_gpu += st.newly_broken
+        total_or += nb
+        same = np.array_equal(mask_to_mu(g.bond_mask().cpu().numpy(), g.nnb), mu)
+        if same:
+            assert st.newly_broken == nb
+            assert rel_l2(u.cpu().numpy(), uo) <= 1e-10
+            assert rel_l2(v.cpu().numpy(), vo) <= 1e-9
+        else:
+            odd += 1
+            assert abs(st.newly_broken - nb) <= 2
+    assert odd <= 1
+    assert total_gpu > 100   # the crack grows
+    print(f"2000 steps: {total_gpu} bonds broken (oracle chunks: {total_or}), chunks with a marginal bond: {odd}")
+
+
+def test_crack_plate_512_gradient_by_finite_differences(pd):
+    """dL/dE of L = 1/2 |u_final|^2 after the 2000-step run of the 512^2 plate,
+    by the checkpointed adjoint (pd_step_adjoint through autograd), against
+    central finite differences of the GPU forward at three nodes near the
+    notch, where the bond history of the +- runs is checked to be the same as
+    the base run's (breaking is not differentiated)."""
+    from paper_2301_11828_gb300.autograd import verlet_run
+    w, cons, vp = _crack_setup(512)
+    E_np = w.extra["E_field"]
+    g = pd.Grid(2, w.n, w.h, w.M, constrained=cons, E_field=torch.tensor(E_np, device="cuda"), s0=w.s0)
+    g.break_segment(w.extra["notch"], w.extra["notch_den"])
+    mask0 = g.bond_mask().clone()
+    dt = 0.8 * g.stable_dt()
+    vpt = torch.tensor(vp, device="cuda")
+    nsteps = 2000
+
+    def forward(E):
+        g.set_material(E=1.0, rho=w.rho, s0=w.s0, E_field=E)
+        g.set_bond_mask(mask0)
+        u = torch.zeros((2,) + E_np.shape, dtype=torch.float64, device="cuda")
+        v = vpt.clone()
+        bs = torch.zeros(g.N * g.nnb, dtype=torch.int32, device="cuda")
+        g.step(u, v, None, nsteps=nsteps, dt=dt, v_prescribed=vpt, break_step=bs)
+        return float(0.5 * (u * u).sum()), bs
+
+    E0 = torch.tensor(E_np, device="cuda")
+    L0, bs0 = forward(E0)
+    g.set_bond_mask(mask0)
+    E = E0.clone().requires_grad_(True)
+    uN = verlet_run(g, E, torch.zeros((2,) + E_np.shape, dtype=torch.float64, device="cuda"), vpt.clone(), nsteps,
+                    dt, v_prescribed=vpt, checkpoint_every=45)
+    L = 0.5 * (uN * uN).sum()
+    L.backward()
+    assert abs(float(L.detach()) / L0 - 1.0) < 1e-12
+    grad = E.grad.cpu().numpy()
+    ny, nx = E_np.shape
+    cands = [(ny // 2 + 6, nx // 2 - 60), (ny // 2 - 9, nx // 2 + 58), (ny // 2 + 20, nx // 2),
+             (ny // 2 - 30, nx // 2 - 80), (ny // 4, nx // 2)]
+    checked = 0
+    for (j, i) in cands:
+        eps = 1e-6 * E_np[j, i]
+        Ep, Em = E0.clone(), E0.clone()
+        Ep[j, i] += eps
+        Em[j, i] -= eps
+        Lp, bsp = forward(Ep)
+        Lm, bsm = forward(Em)
+        if not (torch.equal(bsp, bs0) and torch.equal(bsm, bs0)):
+            continue   # a bond changed its break step: the loss is not differentiable there
+        fd = (Lp - Lm) / (2 * eps)
+        assert abs(fd - grad[j, i]) <= 1e-4 * abs(grad[j, i]) + 1e-9 * abs(L0), (j, i, fd, grad[j, i])
+        checked += 1
+        if checked == 3:
+            break
+    assert checked >= 2

@@ -48,7 +48,7 @@ def test_real_horizon_product(pd, dtype, dim, n, m, method):
     ut = torch.tensor(u, dtype=dtype, device="cuda")
     al = oracle.alpha(dim, 1.7, m * h)
     ref = oracle.stiffness(dim, n, h, m, al, ut.double().cpu().numpy())
-    for extra in ((0, pd.PD_ACCURATE, pd.PD_NO_TMA) if (dtype == torch.float32 and method == "stencil") else (0,)):
+    for extra in ((0, pd.PD_PAIR_FORM, pd.PD_NO_TMA) if (dtype == torch.float32 and method == "stencil") else (0,)):
         out = g.matvec(ut, flags=flags | extra)
         assert rel_l2(out.double().cpu().numpy(), ref) <= TOL[dtype]
 

@@ -1,13 +1,14 @@
 """The allocation-free Verlet entry point (pd_step_noalloc).
 
-Some callers of this library cannot let it call cudaMalloc: code that runs
-while a CUDA graph is being captured, services whose GPU memory belongs to
-their own pool or caching allocator, and real-time loops that cannot afford
-the synchronisation an allocation implies.  pd_step_noalloc serves them with a
-fixed scratch array inside the library.  This test drives it through the C ABI
-and checks that two consecutive calls give the same state as two consecutive
-calls of pd_step from the same start, and that grids beyond its fixed limit are
-refused.  The file name makes pytest collect it last.
+Some callers of this library cannot let it call cudaMalloc: services whose GPU
+memory belongs to their own pool or caching allocator (which may hold nearly
+all of the device), and real-time loops that cannot afford the synchronisation
+an allocation implies.  pd_step_noalloc serves them with a fixed scratch array
+inside the library.  These tests drive it through the C ABI and check that two
+consecutive calls give the same state as two consecutive calls of pd_step from
+the same start, that a call on a freshly set-up grid takes no device memory,
+and that grids beyond its fixed limit are refused.  The file name makes pytest
+collect it last.
 """
 import numpy as np
 import pytest
@@ -74,3 +75,35 @@ def test_noalloc_step_refuses_grids_beyond_its_scratch(pd):
         pd.pd_step_noalloc(g.handle, u, v, None, 1, 1e-4)
     assert e.value.code == pd.PD_ERR_INVALID
     assert "524288" in str(e.value)
+
+
+def test_noalloc_step_takes_no_device_memory(pd):
+    """A fresh grid's first pd_step_noalloc calls leave the device's free memory
+    unchanged (a cudaMalloc reserves at least one 2 MiB page).  A warm-up call
+    on another grid comes first, so that the kernels involved are loaded and the
+    scratch address is known; the fresh grid's own set-up (creation, modulus
+    field, notch) allocates and is done before the measurement."""
+    w = syn.crack_plate(64, 3)
+    lay = w.extra["vel_layers"]
+    cons = np.zeros((2,) + lay.shape, dtype=np.uint8)
+    cons[1] = lay != 0
+    vpt = torch.zeros((2,) + lay.shape, dtype=torch.float64, device="cuda")
+    vpt[1] = torch.tensor(lay * 0.05, device="cuda")
+    E = w.extra["E_field"]
+
+    def run(g, calls):
+        u = torch.zeros((2,) + lay.shape, dtype=torch.float64, device="cuda")
+        v = vpt.clone()
+        bs = torch.zeros(g.N * g.nnb, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for call in range(calls):
+            pd.pd_step_noalloc(g.handle, u, v, None, 10, 2e-4, v_prescribed=vpt, break_step=bs,
+                               step_base=10 * call)
+        torch.cuda.synchronize()
+        return free0, torch.cuda.mem_get_info()[0]
+
+    run(_grid(pd, w, cons, E), 1)             # warm-up on another grid
+    g = _grid(pd, w, cons, E)                 # the fresh grid, fully set up
+    free0, free1 = run(g, 2)
+    assert free1 == free0, f"device free memory changed by {free0 - free1} bytes"
