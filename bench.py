@@ -46,8 +46,8 @@ TRAFFIC = {
                 "paper_2301_11828_gb300/csrc/pd_stencil.cuh", "paper_2301_11828_gb300/csrc/pd_reduce.cuh"],
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch on 32 fields (the ncu capture
     # summarised under profiles/) divided by 32; valid while the sources hash to sha256
-    "sha256": "",
-    "bytes_per_field": 0,
+    "sha256": "00e50a1cf07865f9cd3d7d8369d758f4f6867aeb2aa9b3c2707485447a3c2ae8",
+    "bytes_per_field": 15674072,
 }
 
 
@@ -468,18 +468,21 @@ def _crack512(torch, pd, syn, dev, oracle, nsteps=2000):
     mask0 = g.bond_mask().clone()
     dt = 0.8 * g.stable_dt()
     vpt = torch.tensor(vp, device=dev)
-    res = {"steps": nsteps, "dt": dt, "stable_dt": dt / 0.8, "E_max": float(E_np.max()), "notch_bonds": notch}
+    v_init = np.where(cons != 0, vp, w.extra["v_ramp"])   # the ramp inside, the layers' velocity on them
+    v0t = torch.tensor(v_init, device=dev)
+    res = {"steps": nsteps, "dt": dt, "stable_dt": dt / 0.8, "E_max": float(E_np.max()), "notch_bonds": notch,
+           "initial_velocity": "uniform stretch rate (v0 (2y/L - 1)), edge layers at +-v0"}
     # warm-up on the same grid (workspaces, the adjoint's segment buffers), then the bond state reset
     u = torch.zeros((2,) + lay.shape, dtype=torch.float64, device=dev)
-    v = vpt.clone()
+    v = v0t.clone()
     g.step(u, v, None, nsteps=5, dt=dt, v_prescribed=vpt)
     E = Et.clone().requires_grad_(True)
-    uN = verlet_run(g, E, torch.zeros_like(u), vpt.clone(), 50, dt, v_prescribed=vpt, checkpoint_every=45)
+    uN = verlet_run(g, E, torch.zeros_like(u), v0t.clone(), 50, dt, v_prescribed=vpt, checkpoint_every=45)
     (0.5 * (uN * uN).sum()).backward()
     g.set_bond_mask(mask0)
     # forward, timed
     u.zero_()
-    v.copy_(vpt)
+    v.copy_(v0t)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = g.step(u, v, None, nsteps=nsteps, dt=dt, v_prescribed=vpt)
@@ -493,7 +496,7 @@ def _crack512(torch, pd, syn, dev, oracle, nsteps=2000):
     E = Et.clone().requires_grad_(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    uN = verlet_run(g, E, torch.zeros_like(u), vpt.clone(), nsteps, dt, v_prescribed=vpt, checkpoint_every=45)
+    uN = verlet_run(g, E, torch.zeros_like(u), v0t.clone(), nsteps, dt, v_prescribed=vpt, checkpoint_every=45)
     loss = 0.5 * (uN * uN).sum()
     loss.backward()
     torch.cuda.synchronize()
@@ -502,11 +505,11 @@ def _crack512(torch, pd, syn, dev, oracle, nsteps=2000):
     # the first 100 steps against the oracle's Verlet loop from the same state
     g.set_bond_mask(mask0)
     u.zero_()
-    v.copy_(vpt)
+    v.copy_(v0t)
     st = g.step(u, v, None, nsteps=100, dt=dt, v_prescribed=vpt)
     mu = oracle.intact_mu(2, w.n, w.M)
     oracle.prenotch(w.n, w.M, w.extra["notch"], w.extra["notch_den"], mu)
-    uo, vo = np.zeros((2,) + lay.shape), vp.copy()
+    uo, vo = np.zeros((2,) + lay.shape), v_init.copy()
     nb = oracle.vv(2, w.n, w.h, w.M, oracle.alpha(2, 1.0, w.delta), uo, vo, 100, dt, E=E_np, mu=mu, s0=w.s0,
                    cons=cons, vpres=vp)
     res["first_100_steps_vs_oracle"] = {"u_rel_l2": _rel(u.cpu().numpy(), uo), "v_rel_l2": _rel(v.cpu().numpy(), vo),
@@ -560,13 +563,27 @@ def _extras(torch, pd, syn, dev):
     out["variants_rel_l2_vs_oracle"] = {k: float(f"{v:.3e}") for k, v in verr.items()}
     out["variants_fp64_frac_of_measured_fp64_peak"] = vfrac
     out["cufft_comparison"] = _cufft_comparison(torch, pd, syn, dev, oracle)
-    # autotuned method choice per horizon / precision on the 1024^2 plate
+    # the autotuner's choice (method; FP32 2D stencil tile height) per horizon and precision on
+    # the 1024^2 plate and the 128^3 cube, with the time of each candidate; "fixed" is the
+    # untuned default (the 64 x 32 stencil tile)
     tune = {}
-    for M in (3, 6):
-        w = syn.large_plate(M)
-        g = pd.Grid(2, w.n, w.h, w.M)
+    for key, w in (("plate1024_M3", syn.large_plate(3)), ("plate1024_M4", syn.large_plate(4)),
+                   ("plate1024_M6", syn.large_plate(6)), ("cube128_M3", syn.cube(128, 3))):
+        g = pd.Grid(w.dim, w.n, w.h, w.M)
         t = g.autotune()
-        tune[f"M{M}"] = {k: round(v, 4) for k, v in t.items()}
+        info = pd.pd_get_info(g.handle)
+        ent = {k: round(v, 4) for k, v in t.items()}
+        ent["f32_method"] = "fft" if info.auto_method[0] == pd.PD_METHOD_FFT else "stencil"
+        ent["f64_method"] = "fft" if info.auto_method[1] == pd.PD_METHOD_FFT else "stencil"
+        ent["f32_stencil_tile_rows"] = int(info.stencil_tile_rows)
+        if w.dim == 2 and w.M <= 4:
+            g.set_stencil_tile_rows(32)
+            U = torch.zeros((1, 2) + tuple(reversed(w.n)), dtype=torch.float32, device=dev)
+            O = torch.empty_like(U)
+            ent["f32_stencil_fixed_tile32_ms"] = round(_time_fn(torch, lambda: g.matvec(U, O, flags=pd.PD_METHOD_STENCIL),
+                                                                reps=20) * 1e3, 4)
+            g.set_stencil_tile_rows(ent["f32_stencil_tile_rows"])
+        tune[key] = ent
         g.close()
     out["autotune_ms_per_field"] = tune
     # static solve on the 1024^2 plate (clamp left, traction right), rtol 1e-8

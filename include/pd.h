@@ -100,6 +100,8 @@ typedef struct {
     double h, delta, alpha;  /* spacing, horizon, micromodulus constant at the set modulus */
     int64_t n_broken_nodes;  /* nodes with at least one broken bond (Omega_br) */
     int32_t device_error;    /* nonzero once a bounded device-side wait ran out (PD_ERR_TIMEOUT cause) */
+    int32_t auto_method[2];  /* what PD_METHOD_AUTO runs for FP32 / FP64: PD_METHOD_STENCIL or PD_METHOD_FFT */
+    int32_t stencil_tile_rows;  /* FP32 2D stencil tile height (32 or 16; set by the autotuner) */
 } pd_grid_info;
 
 typedef struct {
@@ -319,14 +321,35 @@ int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const 
  * without a modulus field.  Host-only; no device work. */
 int pd_set_method(pd_grid *g, uint32_t method);
 
-/* Measures both methods of K u for the precision(s) in flags (PD_F32 and/or
- * PD_F64) on scratch vectors of this grid (allocated and freed inside the
- * call, CUDA events on `stream`; three warm-up launches each, then five
- * alternating trials of ten launches per method, each method keeping its
- * fastest trial) and records the faster one for PD_METHOD_AUTO.  times_ms: host double [4] or
- * NULL, receives {stencil f32, fft f32, stencil f64, fft f64} in ms (0 where
- * not measured). */
+/* Pins the tile height of the FP32 TMA-fed 2D stencil: 32 rows (64 x 32
+ * outputs per tile, the default) or 16 (64 x 16; used at M <= 4).  Both give
+ * identical results; only the speed differs.  Host-only.  Errors:
+ * PD_ERR_INVALID (rows not 16 or 32). */
+int pd_set_stencil_tile_rows(pd_grid *g, int rows);
+
+/* Autotuner: measures the candidates of K u for the precision(s) in flags
+ * (PD_F32 and/or PD_F64) -- the direct stencil and, without a modulus field,
+ * the FFT tiles; for FP32 2D grids on the TMA-fed stencil at M <= 4 also the
+ * stencil's tile height (64 x 32 or 64 x 16 outputs) -- on scratch vectors the
+ * grid keeps (allocated on the first call), CUDA events on `stream`: three
+ * warm-up launches each, then five rounds of ten launches per candidate in
+ * turn, each keeping its fastest round.  Records the fastest candidate for
+ * PD_METHOD_AUTO and the faster stencil tile for every stencil product.
+ * times_ms: host double [4] or NULL, receives {stencil f32, fft f32, stencil
+ * f64, fft f64} in ms per field (the faster stencil tile; 0 where not
+ * measured). */
 int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream);
+
+/* pd_autotune with a cache: cache_path names a JSON file of entries
+ *   "<key>": {"method": "stencil"|"fft", "tile_rows": 32|16, "ms_per_field": t}
+ * keyed by dimension, extents, delta/h, precision (and a modulus field), device
+ * name and SM count.  When the file holds an entry for every precision in
+ * flags, the recorded choice is applied without measuring (*from_cache = 1);
+ * otherwise pd_autotune runs and its choice is added to the file (written to
+ * cache_path.tmp, then renamed).  from_cache, times_ms: host or NULL.  Errors:
+ * as pd_autotune; PD_ERR_INVALID when the file cannot be written. */
+int pd_autotune_cached(pd_grid *g, uint32_t flags, const char *cache_path, int *from_cache, double *times_ms,
+                       void *stream);
 
 /* ---- batches of independent static solves ----
  * A pd_batch groups `count` existing 2D grids (each with its own size,

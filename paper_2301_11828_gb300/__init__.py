@@ -55,7 +55,8 @@ class pd_grid_info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("M", ctypes.c_int), ("nnb", ctypes.c_int), ("mask_words", ctypes.c_int),
                 ("n", ctypes.c_int64 * 3), ("N", ctypes.c_int64), ("h", ctypes.c_double),
                 ("delta", ctypes.c_double), ("alpha", ctypes.c_double), ("n_broken_nodes", ctypes.c_int64),
-                ("device_error", ctypes.c_int32)]
+                ("device_error", ctypes.c_int32), ("auto_method", ctypes.c_int32 * 2),
+                ("stencil_tile_rows", ctypes.c_int32)]
 
 
 class pd_cg_stats(ctypes.Structure):
@@ -89,7 +90,9 @@ SIGNATURES = {
     "pd_break_bonds": (_I, [_VP, _VP, _U32, ctypes.POINTER(_I64), _VP]),
     "pd_break_segment": (_I, [_VP, ctypes.POINTER(_I64), _I64, ctypes.POINTER(_I64), _VP]),
     "pd_set_method": (_I, [_VP, _U32]),
+    "pd_set_stencil_tile_rows": (_I, [_VP, _I]),
     "pd_autotune": (_I, [_VP, _U32, _VP, _VP]),
+    "pd_autotune_cached": (_I, [_VP, _U32, ctypes.c_char_p, ctypes.POINTER(_I), _VP, _VP]),
     "pd_get_info": (_I, [_VP, ctypes.POINTER(pd_grid_info)]),
     "pd_get_offsets": (_I, [_VP, _VP, _I]),
     "pd_get_coefficients": (_I, [_VP, _VP, _I]),
@@ -333,6 +336,20 @@ def pd_autotune(g, flags: int = PD_F32 | PD_F64, stream=None):
     return {"stencil_f32_ms": t[0], "fft_f32_ms": t[1], "stencil_f64_ms": t[2], "fft_f64_ms": t[3]}
 
 
+def pd_autotune_cached(g, cache_path: str, flags: int = PD_F32 | PD_F64, stream=None):
+    """pd_autotune through a JSON cache file; returns (times, from_cache)."""
+    t = (ctypes.c_double * 4)()
+    hit = ctypes.c_int(0)
+    _check(load_library().pd_autotune_cached(g, int(flags), os.fsencode(cache_path), ctypes.byref(hit), t,
+                                             _stream(stream)))
+    return ({"stencil_f32_ms": t[0], "fft_f32_ms": t[1], "stencil_f64_ms": t[2], "fft_f64_ms": t[3]},
+            bool(hit.value))
+
+
+def pd_set_stencil_tile_rows(g, rows: int):
+    _check(load_library().pd_set_stencil_tile_rows(g, int(rows)))
+
+
 def pd_get_info(g) -> pd_grid_info:
     info = pd_grid_info()
     _check(load_library().pd_get_info(g, ctypes.byref(info)))
@@ -453,6 +470,9 @@ class Grid:
 
     def prefer_method(self, method: int):
         pd_set_method(self.handle, method)
+
+    def set_stencil_tile_rows(self, rows: int):
+        pd_set_stencil_tile_rows(self.handle, rows)
 
     def autotune(self, flags: int = PD_F32 | PD_F64, stream=None):
         return pd_autotune(self.handle, flags, stream)

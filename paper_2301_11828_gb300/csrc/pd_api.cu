@@ -141,6 +141,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_tma_flags);
     cudaFree(g->ws);
     cudaFree(g->adj_ws);
+    cudaFree(g->tune_ws);
     cg_release(g);
     adr_release(g);
     hostpipe_release(g);
@@ -442,6 +443,15 @@ int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const 
     return launch_stencil(g, f64, a, (cudaStream_t)stream);
 }
 
+int pd_set_stencil_tile_rows(pd_grid *g, int rows)
+{
+    if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
+    if (rows != 32 && rows != 16) return fail(PD_ERR_INVALID, "tile rows must be 32 or 16");
+    g->stencil_tile_rows = rows;
+    ++g->op_stamp;
+    return PD_OK;
+}
+
 int pd_set_method(pd_grid *g, uint32_t method)
 {
     if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
@@ -456,62 +466,6 @@ int pd_set_method(pd_grid *g, uint32_t method)
         return fail(PD_ERR_INVALID, "method must be PD_METHOD_AUTO, PD_METHOD_STENCIL or PD_METHOD_FFT");
     }
     ++g->op_stamp;
-    return PD_OK;
-}
-
-int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream)
-{
-    int rc = check_grid(g);
-    if (rc) return rc;
-    if (!(flags & (PD_F32 | PD_F64))) return fail(PD_ERR_INVALID, "flags must name PD_F32 and/or PD_F64");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (times_ms)
-        for (int i = 0; i < 4; ++i) times_ms[i] = 0.0;
-    const size_t bytes = sizeof(double) * (size_t)g->dim * g->N;
-    void *u = nullptr, *o = nullptr;
-    if (cudaMalloc(&u, bytes) != cudaSuccess || cudaMalloc(&o, bytes) != cudaSuccess) {
-        cudaFree(u);
-        return fail(PD_ERR_OOM, "autotune scratch");
-    }
-    cudaMemsetAsync(u, 0, bytes, s);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    const bool fft_ok = !g->has_E;
-    for (int prec = 0; prec < 2 && rc == PD_OK; ++prec) {
-        const uint32_t dt = prec ? PD_F64 : PD_F32;
-        if (!(flags & dt)) continue;
-        // Alternate the candidates over several trials and keep each one's fastest
-        // trial, so that a clock ramp or a neighbour's burst does not decide.
-        float best[2] = {1e30f, 1e30f};
-        const int nm = fft_ok ? 2 : 1;
-        for (int m = 0; m < nm && rc == PD_OK; ++m)
-            for (int w = 0; w < 3 && rc == PD_OK; ++w)
-                rc = matvec(g, 1, u, o, dt | (m ? PD_METHOD_FFT : PD_METHOD_STENCIL) | PD_IGNORE_BROKEN, s);
-        for (int trial = 0; trial < 5 && rc == PD_OK; ++trial) {
-            for (int m = 0; m < nm && rc == PD_OK; ++m) {
-                const uint32_t fl = dt | (m ? PD_METHOD_FFT : PD_METHOD_STENCIL) | PD_IGNORE_BROKEN;
-                const int reps = 10;
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < reps && rc == PD_OK; ++r) rc = matvec(g, 1, u, o, fl, s);
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms / reps < best[m]) best[m] = ms / reps;
-            }
-        }
-        if (times_ms)
-            for (int m = 0; m < nm; ++m) times_ms[2 * prec + m] = best[m];
-        g->auto_choice[prec] = (fft_ok && best[1] < best[0]) ? 2 : 1;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(u);
-    cudaFree(o);
-    ++g->op_stamp;
-    if (rc) return rc;
-    PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
 
@@ -535,6 +489,8 @@ int pd_get_info(pd_grid *g, pd_grid_info *info)
     int derr = 0;
     PD_CUDA(cudaMemcpy(&derr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     info->device_error = derr;
+    for (int i = 0; i < 2; ++i) info->auto_method[i] = g->auto_choice[i] == 2 ? PD_METHOD_FFT : PD_METHOD_STENCIL;
+    info->stencil_tile_rows = g->stencil_tile_rows;
     return PD_OK;
 }
 

@@ -121,6 +121,9 @@ struct pd_grid {
 
     // measured method choice cache: [dtype 0/1] -> 0 unknown, 1 stencil, 2 fft
     int auto_choice[2] = {0, 0};
+    // FP32 2D stencil tile height chosen by the autotuner: 32 (default) or 16 rows
+    int stencil_tile_rows = 32;
+    void *tune_ws = nullptr;         // autotuner scratch (two vectors), kept by the grid
 
     void *cg = nullptr;        // CG workspace and captured graphs (pd_cg.cu)
     void *adr = nullptr;       // ADR workspace and captured graph (pd_adr.cu)

@@ -328,17 +328,8 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
 // interior form need up to 250 registers (measured faster than two CTAs with
 // spills, or the plain difference form).
 constexpr int kAccStages = 3;   // halo tiles in flight or in use per CTA
-#ifndef PD_ACC_GY
-#define PD_ACC_GY 4
-#endif
-#ifndef PD_ACC_MINB
-#define PD_ACC_MINB 2
-#endif
-#ifndef PD_ACC_SLIDE
-#define PD_ACC_SLIDE 0
-#endif
 template <int M, int GY>
-__global__ void __launch_bounds__(64 * GY, (M <= 4 ? PD_ACC_MINB : 1))
+__global__ void __launch_bounds__(64 * GY, (M <= 4 ? 2 : 1))
 k_tbt2d_acc(const __grid_constant__ CUtensorMap map, float *__restrict__ out, int nx, int ny, int64_t N,
             int ybuf0, int ty0, int yend, int tiles_x, int tiles_y, FastDiv div_tx, FastDiv div_ty, int ntiles,
             const uint8_t *__restrict__ cons,
@@ -456,12 +447,8 @@ k_tbt2d_acc(const __grid_constant__ CUtensorMap map, float *__restrict__ out, in
         const bool warp_in = tile_in || (__all_sync(0xffffffffu, gx >= M && gx < nx - M) && gy0 >= M &&
                                          gy0 + kRt <= ny - M);
         u64 a1[kRt], a2[kRt];
-        if (warp_in) {
-            if constexpr (PD_ACC_SLIDE)
-                tile_eg_slide<M>(colx, coly, tab, a1, a2);
-            else
-                tile_eg<M>(colx, coly, tab, a1, a2);
-        }
+        if (warp_in)
+            tile_eg<M>(colx, coly, tab, a1, a2);
         else
             tile_diff<M, true>(colx, coly, tab, a1, a2, gx, nx, gy0 - M, ny);
 
@@ -535,7 +522,7 @@ __global__ void k_tma_flags(const uint8_t *__restrict__ cons, int nx, int ny, in
 }
 
 // ------------------------------------------------------------------ host side
-template <int M, bool ACC>
+template <int M, bool ACC, int GYA = kGY2>
 int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
     constexpr int BX = box_x<M>(), BY = box_y<M>();
@@ -546,7 +533,7 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     const bool window = in_rows != ny || out_rows != ny;
     if (window && (!ACC || out_row0 % kTYt != 0 || a.dot_partial))
         return fail(PD_ERR_INVALID, "row windows need the default FP32 form, tile-aligned rows, no fused dot");
-    constexpr int GY = ACC ? PD_ACC_GY : kGY2, TH = 64 * GY, TYt = GY * kRt, BYa = TYt + 2 * M;
+    constexpr int GY = ACC ? GYA : kGY2, TH = 64 * GY, TYt = GY * kRt, BYa = TYt + 2 * M;
     CUtensorMap map;
     if (!make_map<M>(&map, a.u, nx, in_rows, a.batch, ACC ? BYa : BY))
         return fail(PD_ERR_CUDA, "tensor map encode failed");
@@ -557,7 +544,7 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
         kern = (void *)k_tbt2d_acc<M, GY>;
     else
         kern = (void *)k_tbt2d_tma<M, false>;
-    static int attr_done[64] = {0};
+    static int attr_done[64] = {0};   // per instantiation
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_done[dev]) {
@@ -632,7 +619,10 @@ bool tma_stencil_eligible(const pd_grid *g, const MatvecArgs &a, bool f64)
 int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
 #define PD_TMA_CASE(m) \
-    case m: return a.pair_form ? run<m, false>(g, a, s) : run<m, true>(g, a, s);
+    case m:                                                                                  \
+        if (a.pair_form) return run<m, false>(g, a, s);                                      \
+        if (m <= 4 && g->stencil_tile_rows == 16) return run<m, true, (m <= 4 ? 2 : kGY2)>(g, a, s); \
+        return run<m, true>(g, a, s);
     switch (g->M) {
         PD_TMA_CASE(1)
         PD_TMA_CASE(2)

@@ -297,16 +297,29 @@ __device__ __forceinline__ void tile_eg(const float *colx, const float *coly, co
     static_for<1, M + 1>([&](auto OX) {
         constexpr int ox = decltype(OX)::value;
         constexpr int My = isqrt_c(M * M - ox * ox);
+        const float cxx = tab.v[4 * pair_index2(M, ox, 0)];
+        if constexpr (My == 0) {
+            // only the axis pair (ox, 0): the x component of E alone, in scalar FP32
+#pragma unroll
+            for (int r = 0; r < kRt; ++r) {
+                const int i = r + M;
+                const float ux = upk(w0[i]).x;
+                const float e = (colx[i * BX + ox] - ux) + (colx[i * BX - ox] - ux);
+                float2 acc = upk(a1[r]);
+                acc.x = __fmaf_rn(cxx, e, acc.x);
+                a1[r] = pk(acc.x, acc.y);
+            }
+            return;
+        }
         u64 E[WL], G[WL];
 #pragma unroll
         for (int i = M - My; i < kRt + M + My; ++i) {
             const u64 wp = pk(colx[i * BX + ox], coly[i * BX + ox]);
             const u64 wm = pk(colx[i * BX - ox], coly[i * BX - ox]);
             E[i] = fadd2(fsub2(wp, w0[i]), fsub2(wm, w0[i]));
-            if constexpr (My > 0) G[i] = fsub2(wp, wm);
+            G[i] = fsub2(wp, wm);
         }
         {   // axis pair (ox, 0): x component only
-            const float cxx = tab.v[4 * pair_index2(M, ox, 0)];
 #pragma unroll
             for (int r = 0; r < kRt; ++r) {
                 const float2 e = upk(E[r + M]);
@@ -325,66 +338,6 @@ __device__ __forceinline__ void tile_eg(const float *colx, const float *coly, co
                 a2[r] = ffma2(c2, fsub2(G[r + M + k], G[r + M - k]), a2[r]);
             }
         });
-    });
-}
-
-// tile_eg with the rows of a column offset formed as the outputs walk down the
-// column: E and G of a row are computed when the first output needs them, so
-// only 2 My + 1 rows of them are live (same operations, fewer registers).
-template <int M>
-__device__ __forceinline__ void tile_eg_slide(const float *colx, const float *coly, const AccTab<M> &tab,
-                                              u64 (&a1)[kRt], u64 (&a2)[kRt])
-{
-    constexpr int BX = box_x<M>(), WL = kRt + 2 * M;
-    u64 w0[WL];
-#pragma unroll
-    for (int i = 0; i < WL; ++i) w0[i] = pk(colx[i * BX], coly[i * BX]);
-    static_for<1, M + 1>([&](auto K) {
-        constexpr int k = decltype(K)::value;
-        const u64 c = acc_w(tab, k);
-        u64 V[WL];
-#pragma unroll
-        for (int j = M - k; j < kRt + M; ++j) V[j] = fsub2(w0[j + k], w0[j]);
-#pragma unroll
-        for (int r = 0; r < kRt; ++r) {
-            const u64 W = fsub2(V[r + M], V[r + M - k]);
-            if constexpr (k == 1)
-                a1[r] = fmul2(c, W);
-            else
-                a1[r] = ffma2(c, W, a1[r]);
-        }
-    });
-#pragma unroll
-    for (int r = 0; r < kRt; ++r) a2[r] = 0ull;
-    static_for<1, M + 1>([&](auto OX) {
-        constexpr int ox = decltype(OX)::value;
-        constexpr int My = isqrt_c(M * M - ox * ox);
-        const float cxx = tab.v[4 * pair_index2(M, ox, 0)];
-        u64 E[WL], G[WL];
-        auto row = [&](int i) {
-            const u64 wp = pk(colx[i * BX + ox], coly[i * BX + ox]);
-            const u64 wm = pk(colx[i * BX - ox], coly[i * BX - ox]);
-            E[i] = fadd2(fsub2(wp, w0[i]), fsub2(wm, w0[i]));
-            if constexpr (My > 0) G[i] = fsub2(wp, wm);
-        };
-#pragma unroll
-        for (int i = M - My; i < M + My; ++i) row(i);
-#pragma unroll
-        for (int r = 0; r < kRt; ++r) {
-            row(r + M + My);
-            const float2 e = upk(E[r + M]);
-            float2 acc = upk(a1[r]);
-            acc.x = __fmaf_rn(cxx, e.x, acc.x);
-            u64 t1 = pk(acc.x, acc.y), t2 = a2[r];
-            static_for<1, My + 1>([&](auto K) {
-                constexpr int k = decltype(K)::value;
-                constexpr int pi = pair_index2(M, ox, k);
-                t1 = ffma2(acc_c1(tab, pi), fadd2(E[r + M + k], E[r + M - k]), t1);
-                t2 = ffma2(acc_c2(tab, pi), fsub2(G[r + M + k], G[r + M - k]), t2);
-            });
-            a1[r] = t1;
-            a2[r] = t2;
-        }
     });
 }
 

@@ -143,6 +143,9 @@ def crack_plate(nside: int = 512, M: int = 3, tag: int = 4) -> Workload:
     The notch is the closed segment y = L/2, |x - L/2| <= 0.1 L, given in
     ``extra['notch']`` as integer numerators over ``extra['notch_den']`` in units
     of h measured from the grid corner (node i sits at i + 1/2).
+    ``extra['v_ramp']`` is an initial y-velocity field that matches the edge
+    layers (v0 (2 y / L - 1) at node height y): started from it, the plate
+    stretches at a uniform rate instead of being struck at its edges.
     """
     n = (nside, nside)
     den = 10
@@ -152,7 +155,10 @@ def crack_plate(nside: int = 512, M: int = 3, tag: int = 4) -> Workload:
         name=f"crack2d_{nside}x{nside}_M{M}", dim=2, n=n, M=M, h=1.0 / nside,
         s0=1e-3, rho=1.0,
         extra=dict(E_field=lognormal_modulus(n, 0.1, tag), notch=notch, notch_den=den,
-                   vel_layers=velocity_layers_2d(n, M), v0=1e-3))
+                   vel_layers=velocity_layers_2d(n, M), v0=1e-3,
+                   v_ramp=np.stack([np.zeros((nside, nside)),
+                                    np.repeat((1e-3 * (2.0 * (np.arange(nside) + 0.5) / nside - 1.0))[:, None],
+                                              nside, axis=1)])))
 
 
 def kw_block(nx: int = 201, ny: int = 101, nz: int = 9, M: int = 3, v0: float = 0.00634) -> Workload:

@@ -1,0 +1,72 @@
+"""The autotuner (pd_autotune, pd_autotune_cached): the candidates it measures,
+the choice it records, the JSON cache that replays that choice, and that the
+stencil's tile height changes no result bit."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pd():
+    import paper_2301_11828_gb300 as pd
+    pd.load_library()
+    return pd
+
+
+def test_tuned_choice_is_the_fastest_and_is_cached(pd, tmp_path):
+    path = str(tmp_path / "tune.json")
+    w = syn.large_plate(3)
+    g = pd.Grid(2, w.n, w.h, w.M)
+    t, hit = pd.pd_autotune_cached(g.handle, path)
+    assert not hit
+    info = pd.pd_get_info(g.handle)
+    assert info.stencil_tile_rows in (16, 32)
+    for prec, (st, ff) in enumerate((("stencil_f32_ms", "fft_f32_ms"), ("stencil_f64_ms", "fft_f64_ms"))):
+        assert t[st] > 0 and t[ff] > 0
+        want = pd.PD_METHOD_FFT if t[ff] < t[st] else pd.PD_METHOD_STENCIL
+        assert info.auto_method[prec] == want
+    entries = json.load(open(path))
+    assert len(entries) == 2 and all(e["tile_rows"] in (16, 32) for e in entries.values())
+    # a second grid of the same geometry takes the recorded choice without measuring
+    g2 = pd.Grid(2, w.n, w.h, w.M)
+    t2, hit2 = pd.pd_autotune_cached(g2.handle, path)
+    assert hit2
+    info2 = pd.pd_get_info(g2.handle)
+    assert list(info2.auto_method) == list(info.auto_method)
+    assert info2.stencil_tile_rows == info.stencil_tile_rows
+    # another horizon is a new entry
+    w6 = syn.large_plate(6)
+    g6 = pd.Grid(2, w6.n, w6.h, w6.M)
+    _, hit6 = pd.pd_autotune_cached(g6.handle, path, flags=pd.PD_F32)
+    assert not hit6 and len(json.load(open(path))) == 3
+
+
+@pytest.mark.parametrize("M", [2, 3, 4])
+def test_stencil_tile_height_changes_no_bit(pd, M):
+    """Both stencil tiles of the autotuner (64 x 32 and 64 x 16 outputs) give the
+    same bits: every output is formed by the same operations in either."""
+    n = (200, 150)
+    rng = np.random.default_rng(M)
+    cons = syn.clamp_left(2, n, M)
+    g = pd.Grid(2, n, 1.0 / 200, M, constrained=cons)
+    U = torch.tensor(rng.uniform(-1, 1, (3, 2, n[1], n[0])), dtype=torch.float32, device="cuda")
+    outs = {}
+    path_rows = []
+    for rows in (32, 16):
+        g.set_stencil_tile_rows(rows)
+        assert pd.pd_get_info(g.handle).stencil_tile_rows == rows
+        for proj in (0, pd.PD_PROJECT):
+            outs[(rows, proj)] = g.matvec(U, flags=pd.PD_METHOD_STENCIL | proj)
+    for proj in (0, pd.PD_PROJECT):
+        assert torch.equal(outs[(32, proj)], outs[(16, proj)])
+        ref = oracle.stiffness(2, n, 1.0 / 200, M, oracle.alpha(2, 1.0, M / 200), U[1].double().cpu().numpy(),
+                               cons=cons if proj else None)
+        assert rel_l2(outs[(16, proj)][1].double().cpu().numpy(), ref) <= 2e-5
