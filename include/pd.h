@@ -63,14 +63,14 @@ typedef enum {
 #define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
 #define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
-#define PD_ACCURATE       0x800u /* FP32 3D stencil: sum c(o) ((u_p+o - u_p) + (u_p-o - u_p)) instead of
-                                    c(o) (u_p+o + u_p-o) against Kd u_p, so that the FP32 error is relative to |K u|
-                                    for smooth fields too (about 25% more arithmetic).  The FP32 2D stencils always
-                                    sum differences (see PD_PAIR_FORM); other kernels ignore the flag */
-#define PD_PAIR_FORM      0x1000u /* FP32 TMA-fed 2D stencil: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o).
-                                    About 10% less arithmetic than the default difference form, but its FP32 error is
-                                    relative to sum |c| |u|, not to |K u|: on smooth fields, or fields with a large
-                                    constant part, it exceeds 1e-4 relative error.  Kept for comparison only */
+#define PD_ACCURATE       0x800u /* accepted for compatibility: every FP32 stencil sums differences of
+                                    nearby values by default (see PD_PAIR_FORM) */
+#define PD_PAIR_FORM      0x1000u /* FP32 stencils: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o)
+                                    instead of the default difference form.  Less arithmetic, but its
+                                    FP32 error is relative to sum |c| |u|, not to |K u|: on smooth fields,
+                                    or fields with a large constant part, it exceeds 1e-4 relative
+                                    error (2D).  For comparison, and for inner solver products whose
+                                    rounding an FP64 refinement corrects */
 
 /* ---- modes for pd_set_surface_correction ---- */
 #define PD_SC_NONE   0    /* the paper's operator A = A^ + D^e + D^f (default) */
@@ -334,7 +334,10 @@ int pd_set_stencil_tile_rows(pd_grid *g, int rows);
  * grid keeps (allocated on the first call), CUDA events on `stream`: three
  * warm-up launches each, then five rounds of ten launches per candidate in
  * turn, each keeping its fastest round.  Records the fastest candidate for
- * PD_METHOD_AUTO and the faster stencil tile for every stencil product.
+ * PD_METHOD_AUTO and the faster stencil tile for every stencil product.  In
+ * FP32 the FFT tiles are timed but not chosen: their rounding error is relative
+ * to |u| |K| rather than |K u|, over the FP32 tolerance on smooth fields
+ * (PD_METHOD_FFT still selects them).
  * times_ms: host double [4] or NULL, receives {stencil f32, fft f32, stencil
  * f64, fft f64} in ms per field (the faster stencil tile; 0 where not
  * measured). */

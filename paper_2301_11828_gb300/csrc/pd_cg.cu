@@ -504,7 +504,9 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s, bool f
     const bool fuse = !(g->broken_total > 0 && !g->has_E) && !g->sc;
     // FP32: the difference form in 2D (fewer iterations for 25 % more stencil work); the 3D
     // stencil is ALU-bound and its difference form costs more time than it saves iterations
-    const uint32_t acc = g->dim == 2 ? PD_ACCURATE : 0u;
+    // the inner FP32 products: the difference form in 2D; the pair form in 3D (ALU-bound there;
+    // the FP64 refinement corrects its rounding)
+    const uint32_t acc = g->dim == 2 ? PD_ACCURATE : PD_PAIR_FORM;
     const uint32_t fl = (f64 ? PD_F64 : PD_F32 | acc) | PD_PROJECT | kInputProjected;
     void *p = f64 ? (void *)w->p64 : (void *)w->p32;
     void *q = f64 ? (void *)w->q64 : (void *)w->q32;

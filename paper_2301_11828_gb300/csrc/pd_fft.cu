@@ -12,7 +12,12 @@
 // for the whole grid.  HBM then sees u once (plus the halo) and K u once.
 //
 // Per tile:
-//   1. load z = u_x + i u_y (zero outside the grid, projected if asked);
+//   1. load z = u_x + i u_y - c (zero outside the grid, projected if asked),
+//      with c the value at one in-grid node of the window: K maps a constant
+//      field to zero on every row (the edge rows included), so K(u - c) = K u,
+//      and the transforms then round values of the size of u's variation over
+//      the tile instead of u's own (a field with a large constant part would
+//      otherwise carry that part's rounding into every output);
 //   2. 64-point FFTs along x, then along y (each as 8 x 8, in two register
 //      passes with the twiddles W64^(n2 k1) between them);
 //   3. for each frequency pair (k, -k): unpack U_x, U_y from Z(k), Z(-k)
@@ -156,6 +161,18 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
     const T *ub = u + b * 2 * N;
     T *ob = out + b * 2 * N;
     const int x0 = blockIdx.x * TO - M, y0 = blockIdx.y * TO - M;   // window origin
+    // the tile's reference value: the (projected) input at its first output node
+    T cx, cy;
+    {
+        const int64_t p0 = (int64_t)(y0 + M) * nx + (x0 + M);
+        cx = __ldg(ub + p0);
+        cy = __ldg(ub + N + p0);
+        if (project) {
+            const uint8_t m = __ldg(cons + p0);
+            if (m & 1) cx = T(0);
+            if (m & 2) cy = T(0);
+        }
+    }
 
     for (int t = threadIdx.x; t < P * P; t += kT) {
         const int a = t % P, r = t / P;
@@ -163,13 +180,14 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
         V z = {T(0), T(0)};
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
             const int64_t p = (int64_t)gy * nx + gx;
-            z.x = __ldg(ub + p);
-            z.y = __ldg(ub + N + p);
+            T vx = __ldg(ub + p), vy = __ldg(ub + N + p);
             if (project) {
                 const uint8_t m = __ldg(cons + p);
-                if (m & 1) z.x = T(0);
-                if (m & 2) z.y = T(0);
+                if (m & 1) vx = T(0);
+                if (m & 2) vy = T(0);
             }
+            z.x = vx - cx;
+            z.y = vy - cy;
         }
         Z[r * PS + a] = z;
     }
@@ -221,12 +239,13 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
             const uint8_t m = project ? __ldg(cons + p) : 0;
             if (m & 1) upx = T(0);
             if (m & 2) upy = T(0);
-            if (edge) {
+            if (edge) {   // the D^e term on the shifted field the transforms saw
                 const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
                 const T dxx = ctxx - __ldg(kd + 3 * cls), dxy = ctxy - __ldg(kd + 3 * cls + 1),
                         dyy = ctyy - __ldg(kd + 3 * cls + 2);
-                fx -= dxx * upx + dxy * upy;
-                fy -= dxy * upx + dyy * upy;
+                const T zx = upx - cx, zy = upy - cy;
+                fx -= dxx * zx + dxy * zy;
+                fy -= dxy * zx + dyy * zy;
             }
             if (m & 1) fx = T(0);
             if (m & 2) fy = T(0);

@@ -138,6 +138,21 @@ k_fft3d_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int n
     const int x0 = (tix % tx_n) * TO - M, y0 = ((tix / tx_n) % ty_n) * TO - M, z0 = (tix / (tx_n * ty_n)) * TO - M;
     const T *ub = u + b * 3 * N;
     T *ob = out + b * 3 * N;
+    // the tile's reference value (the projected input at its first output node): K maps a
+    // constant to zero on every row, so the transforms take u - c (see the 2D tile)
+    T c0v, c1v, c2v;
+    {
+        const int64_t p0 = ((int64_t)(z0 + M) * ny + (y0 + M)) * nx + (x0 + M);
+        c0v = __ldg(ub + p0);
+        c1v = __ldg(ub + N + p0);
+        c2v = __ldg(ub + 2 * N + p0);
+        if (project) {
+            const uint8_t m = __ldg(cons + p0);
+            if (m & 1) c0v = T(0);
+            if (m & 2) c1v = T(0);
+            if (m & 4) c2v = T(0);
+        }
+    }
 
     for (int t = threadIdx.x; t < P3 * P3 * P3; t += kT3) {
         const int x = t & 15, y = (t >> 4) & 15, z = t >> 8;
@@ -145,15 +160,16 @@ k_fft3d_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int n
         V v1 = {T(0), T(0)}, v2 = {T(0), T(0)};
         if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
             const int64_t p = ((int64_t)gz * ny + gy) * nx + gx;
-            v1.x = __ldg(ub + p);
-            v1.y = __ldg(ub + N + p);
-            v2.x = __ldg(ub + 2 * N + p);
+            T a0 = __ldg(ub + p), a1 = __ldg(ub + N + p), a2 = __ldg(ub + 2 * N + p);
             if (project) {
                 const uint8_t m = __ldg(cons + p);
-                if (m & 1) v1.x = T(0);
-                if (m & 2) v1.y = T(0);
-                if (m & 4) v2.x = T(0);
+                if (m & 1) a0 = T(0);
+                if (m & 2) a1 = T(0);
+                if (m & 4) a2 = T(0);
             }
+            v1.x = a0 - c0v;
+            v1.y = a1 - c1v;
+            v2.x = a2 - c2v;
         }
         const int e = z * PL3 + y * RS + x;
         Z1[e] = v1;
@@ -213,9 +229,10 @@ k_fft3d_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int n
                 const T *q = kd + 6 * cls;
                 const T dxx = ct[0] - q[0], dxy = ct[1] - q[1], dxz = ct[2] - q[2], dyy = ct[3] - q[3],
                         dyz = ct[4] - q[4], dzz = ct[5] - q[5];
-                f0 -= dxx * u0 + dxy * u1 + dxz * u2;
-                f1 -= dxy * u0 + dyy * u1 + dyz * u2;
-                f2 -= dxz * u0 + dyz * u1 + dzz * u2;
+                const T s0 = u0 - c0v, s1 = u1 - c1v, s2 = u2 - c2v;   // the shifted field of the transforms
+                f0 -= dxx * s0 + dxy * s1 + dxz * s2;
+                f1 -= dxy * s0 + dyy * s1 + dyz * s2;
+                f2 -= dxz * s0 + dyz * s1 + dzz * s2;
             }
             if (m & 1) f0 = T(0);
             if (m & 2) f1 = T(0);

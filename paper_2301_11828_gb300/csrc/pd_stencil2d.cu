@@ -1,42 +1,103 @@
-// pd_stencil2d.cu -- 2D stencil, TBT form (Sec. 3.2-3.4).
+// pd_stencil2d.cu -- 2D stencil (Eq. mat:f1; the TBT structure of Sec. 3.2-3.4),
+// FP64 and FP32 (the FP32 grids that the TMA-fed kernel does not take).
 //
-// With u~ the field zero-padded outside the grid,
-//     (K u)_p = Kd_p u_p - sum_{o != 0} c(o) u~_{p+o},   Kd_p = sum_{o: p+o in grid} c(o),
-// which is -A^ u (the Toeplitz-block-Toeplitz part) plus the edge self-term
-// -D^e u of Eq. tea:sc, folded into the diagonal block Kd_p.  Kd_p equals the
-// full-horizon sum in the interior and comes from the clipped-distance table
-// near the faces.  c(o) = c(-o), so the sum runs over offset pairs:
-//     sum_o c(o) u~_{p+o} = sum_{o in half} c(o) (u~_{p+o} + u~_{p-o}).
-//
-// In FP32 the same sum is evaluated as differences, (K u)_p = -sum_{o in half}
-// c(o) [m_{p+o} (u_{p+o} - u_p) + m_{p-o} (u_{p-o} - u_p)], m = 1 inside the
-// grid and 0 outside (the in-grid bond sum itself, with no diagonal term to
-// cancel against), so that the FP32 error stays relative to |K u| on smooth
-// fields and on fields with a large constant part.
+// The product is the in-grid bond sum taken as differences:
+//     (K u)_p = -sum_{o in half} c(o) [m_{p+o} (u_{p+o} - u_p) + m_{p-o} (u_{p-o} - u_p)],
+// m = 1 inside the grid and 0 outside.  It equals the TBT form
+// Kd_p u_p - sum_o c(o) u~_{p+o} (the diagonal block Kd_p = sum of c(o) over the
+// in-grid offsets, which folds in the edge self-term D^e of Eq. tea:sc), but
+// has no diagonal term to cancel against, so that the rounding error stays
+// relative to |K u| on smooth fields and on fields with a large constant part.
 //
 // Tiling: a CTA owns 64 x (4R) outputs; each of its 256 threads owns a column
 // of R consecutive y outputs.  The (64 + 2M) x (4R + 2M) halo box of both
-// components is staged in shared memory once.  For each x offset ox a thread
-// loads the y-windows (R + 2M values) of columns x + ox and x - ox into
-// registers and applies every (ox, oy) pair to its R outputs.  Block entries
+// components is staged in shared memory once; a thread walks its column offsets
+// and, for each, applies every (ox, oy) pair to its R outputs.  Block entries
 // that vanish by geometry (c_xy and c_yy of (ox, 0), c_xx and c_xy of (0, oy))
 // are skipped at compile time.
 #include "pd_stencil.cuh"
 
 namespace pd {
 
+// Pair blocks (xx, xy, yy) in pair_index2 order, then per k = 1..M the summed
+// vertical block Cbar(k) = sum of c(o) over the pairs with |oy| = k (xx, yy).
+template <typename T, int M>
+struct PlainTab {
+    static constexpr int kPairs = count_offsets(2, M) / 2;
+    T v[3 * kPairs + 2 * M];
+};
+
+// Interior outputs (every neighbour inside the grid): the sums regrouped as in
+// the FP32 TMA kernel's tile_eg -- per column offset ox the horizontal second
+// differences E(i) = (u(x+ox,i) - u(x,i)) + (u(x-ox,i) - u(x,i)) and central
+// differences G(i) = u(x+ox,i) - u(x-ox,i) of each window row, shared by the
+// thread's R outputs; pairs (ox, k) and (ox, -k) together as
+// cxx (E(r+k) + E(r-k)) + cxy (G(r+k) - G(r-k)) (x component; y alike); the
+// vertical second differences of the own column once per k with Cbar(k).
+template <typename T, int M, int R, int SX>
+__device__ __forceinline__ void plain_eg(const T *colx, const T *coly, const PlainTab<T, M> &tab, T (&ax)[R],
+                                         T (&ay)[R])
+{
+    constexpr int WL = R + 2 * M, NP = PlainTab<T, M>::kPairs;
+    T wx[WL], wy[WL];
+#pragma unroll
+    for (int i = 0; i < WL; ++i) {
+        wx[i] = colx[i * SX];
+        wy[i] = coly[i * SX];
+    }
+    static_for<1, M + 1>([&](auto K) {
+        constexpr int k = decltype(K)::value;
+        const T cxx = tab.v[3 * NP + 2 * (k - 1)], cyy = tab.v[3 * NP + 2 * (k - 1) + 1];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = r + M;
+            ax[r] = dfma(cxx, (wx[i + k] - wx[i]) + (wx[i - k] - wx[i]), ax[r]);
+            ay[r] = dfma(cyy, (wy[i + k] - wy[i]) + (wy[i - k] - wy[i]), ay[r]);
+        }
+    });
+    static_for<1, M + 1>([&](auto OX) {
+        constexpr int ox = decltype(OX)::value;
+        constexpr int My = isqrt_c(M * M - ox * ox);
+        const T c0 = tab.v[3 * pair_index2(M, ox, 0)];
+        T ex[WL], ey[WL], gx[WL], gy[WL];
+#pragma unroll
+        for (int i = M - My; i < R + M + My; ++i) {
+            const T px = colx[i * SX + ox], mx = colx[i * SX - ox];
+            ex[i] = (px - wx[i]) + (mx - wx[i]);
+            if constexpr (My > 0) {
+                const T py = coly[i * SX + ox], my = coly[i * SX - ox];
+                ey[i] = (py - wy[i]) + (my - wy[i]);
+                gx[i] = px - mx;
+                gy[i] = py - my;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) ax[r] = dfma(c0, ex[r + M], ax[r]);   // axis pair (ox, 0)
+        static_for<1, My + 1>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            constexpr int pi = pair_index2(M, ox, k);
+            const T cxx = tab.v[3 * pi], cxy = tab.v[3 * pi + 1], cyy = tab.v[3 * pi + 2];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = r + M;
+                ax[r] = dfma(cxx, ex[i + k] + ex[i - k], dfma(cxy, gy[i + k] - gy[i - k], ax[r]));
+                ay[r] = dfma(cyy, ey[i + k] + ey[i - k], dfma(cxy, gx[i + k] - gx[i - k], ay[r]));
+            }
+        });
+    });
+}
+
 template <typename T, int M>
 __global__ void __launch_bounds__(kThreads)
 k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
-        const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
-        PairTab<T, 2, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
+        const uint8_t *__restrict__ cons, int project, T scale,
+        PlainTab<T, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
         int in_row0, int64_t Nin, int out_row0, int out_end)
 {
     // Rows are grid rows; the input holds rows [in_row0, ...) with plane size Nin, the
     // output rows [out_row0, out_end) with plane size N (the whole grid: 0, N, 0, ny).
     constexpr int R = rows2d<T, M>();
-    constexpr int TX = kTX2, TY = kGY2 * R, SX = TX + 2 * M, SY = TY + 2 * M, WL = R + 2 * M;
-    constexpr int NP = PairTab<T, 2, M>::kPairs;
+    constexpr int TX = kTX2, TY = kGY2 * R, SX = TX + 2 * M, SY = TY + 2 * M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_x = reinterpret_cast<T *>(smem_raw);
     T *s_y = s_x + SX * SY;
@@ -71,10 +132,7 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
     T ax[R], ay[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) { ax[r] = T(0); ay[r] = T(0); }
-    constexpr bool DIFF = sizeof(T) == 4;
-    if constexpr (DIFF) {
-        // FP32: differences, terms with the neighbour outside the grid dropped.  The
-        // staged value there is zero, so m (v - u_p) = v - m u_p (one FMA).
+    {
         const int gxt = x0 + tx, gyw = y0 + ty * R - M;   // grid column, grid row of window row 0
         T ux[R], uy[R];
 #pragma unroll
@@ -82,7 +140,13 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
             ux[r] = colx[(r + M) * SX];
             uy[r] = coly[(r + M) * SX];
         }
-        static_for<0, M + 1>([&](auto OX) {
+        // warps whose outputs all keep their horizon inside the grid take the shared
+        // differences; the others the plain differences with out-of-grid terms dropped
+        const bool warp_in = __all_sync(0xffffffffu, gxt >= M && gxt < nx - M) && gyw >= 0 && gyw + R + 2 * M <= ny;
+        if (warp_in) plain_eg<T, M, R, SX>(colx, coly, tab, ax, ay);
+        // Differences, terms with the neighbour outside the grid dropped.  The
+        // staged value there is zero, so m (v - u_p) = v - m u_p (one FMA).
+        if (!warp_in) static_for<0, M + 1>([&](auto OX) {
             constexpr int ox = decltype(OX)::value;
             constexpr int My = isqrt_c(M * M - ox * ox);
             const bool cp = gxt + ox < nx, cm = gxt - ox >= 0;
@@ -97,12 +161,13 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
                         const T nm = (cm && gyw + im >= 0 && gyw + im < ny) ? T(-1) : T(0);
                         const T sx = dfma(np, ux[r], colx[ip * SX + ox]) + dfma(nm, ux[r], colx[im * SX - ox]);
                         const T sy = dfma(np, uy[r], coly[ip * SX + ox]) + dfma(nm, uy[r], coly[im * SX - ox]);
-                        const T cxx = tab.v[3 * pi], cxy = tab.v[3 * pi + 1], cyy = tab.v[3 * pi + 2];
+                        const T cxx = tab.v[3 * pi], cyy = tab.v[3 * pi + 2];
                         if constexpr (oy == 0) {
                             ax[r] = dfma(cxx, sx, ax[r]);   // axis pair (ox, 0): c_xy = c_yy = 0
                         } else if constexpr (ox == 0) {
                             ay[r] = dfma(cyy, sy, ay[r]);   // axis pair (0, oy): c_xx = c_xy = 0
                         } else {
+                            const T cxy = tab.v[3 * pi + 1];
                             ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
                             ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
                         }
@@ -133,99 +198,25 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
         if (dot_partial)
             finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
                              blockIdx.x + gridDim.x * blockIdx.y, b);
-        return;
     }
-
-    static_for<1, M + 1>([&](auto OX) {
-        constexpr int ox = decltype(OX)::value;
-        constexpr int My = isqrt_c(M * M - ox * ox);
-        T px[WL], py[WL], mx[WL], my[WL];
-#pragma unroll
-        for (int i = 0; i < WL; ++i) {
-            px[i] = colx[i * SX + ox];
-            py[i] = coly[i * SX + ox];
-            mx[i] = colx[i * SX - ox];
-            my[i] = coly[i * SX - ox];
-        }
-        static_for<-My, My + 1>([&](auto OY) {
-            constexpr int oy = decltype(OY)::value;
-            constexpr int pi = pair_index2(M, ox, oy);
-            const T cxx = tab.v[3 * pi], cxy = tab.v[3 * pi + 1], cyy = tab.v[3 * pi + 2];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const T sx = px[r + M + oy] + mx[r + M - oy];
-                if constexpr (oy == 0) {
-                    ax[r] = dfma(cxx, sx, ax[r]);   // axis pair: c_xy = c_yy = 0 exactly
-                } else {
-                    const T sy = py[r + M + oy] + my[r + M - oy];
-                    ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
-                    ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
-                }
-            }
-        });
-    });
-    T cx[WL], cy[WL];
-#pragma unroll
-    for (int i = 0; i < WL; ++i) {
-        cx[i] = colx[i * SX];
-        cy[i] = coly[i * SX];
-    }
-    static_for<1, M + 1>([&](auto OY) {
-        constexpr int oy = decltype(OY)::value;
-        constexpr int pi = pair_index2(M, 0, oy);
-        const T cyy = tab.v[3 * pi + 2];   // axis pair: c_xx = c_xy = 0 exactly
-#pragma unroll
-        for (int r = 0; r < R; ++r) ay[r] = dfma(cyy, cy[r + M + oy] + cy[r + M - oy], ay[r]);
-    });
-
-    T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
-    const int gx = x0 + tx;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int gy = y0 + ty * R + r;
-        if (gx < nx && gy < out_end) {
-            const int64_t p = (int64_t)gy * nx + gx;
-            const T upx = cx[r + M], upy = cy[r + M];
-            T kxx = tab.v[3 * NP], kxy = tab.v[3 * NP + 1], kyy = tab.v[3 * NP + 2];
-            const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
-            if (a0 != M || a1 != M || b0 != M || b1 != M) {
-                const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
-                kxx = __ldg(kd + 3 * cls);
-                kxy = __ldg(kd + 3 * cls + 1);
-                kyy = __ldg(kd + 3 * cls + 2);
-            }
-            T fx = dfma(kxx, upx, dfma(kxy, upy, -ax[r]));
-            T fy = dfma(kxy, upx, dfma(kyy, upy, -ay[r]));
-            if (project) {
-                const uint8_t m = __ldg(cons + p);
-                if (m & 1) fx = T(0);
-                if (m & 2) fy = T(0);
-            }
-            fx *= scale;
-            fy *= scale;
-            ob[p] = fx;
-            ob[N + p] = fy;
-            dot = dfma(upx, fx, dfma(upy, fy, dot));
-        }
-    }
-    if (dot_partial)
-        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
-                         blockIdx.x + gridDim.x * blockIdx.y, b);
 }
 
 namespace {
 
 template <typename T, int M>
-PairTab<T, 2, M> make_pairs2(const pd_grid *g)
+PlainTab<T, M> make_plain(const pd_grid *g)
 {
-    PairTab<T, 2, M> t{};
-    double c[6], tot[3] = {0, 0, 0};
+    PlainTab<T, M> t{};
+    constexpr int NP = PlainTab<T, M>::kPairs;
+    double c[6], wb[M + 1][2] = {};
     auto put = [&](int ox, int oy) {
         const int pi = pair_index2(M, ox, oy);
         coef_of(g, ox, oy, 0, false, c);
-        for (int i = 0; i < 3; ++i) {
-            t.v[3 * pi + i] = (T)c[i];
-            tot[i] += 2 * c[i];
+        for (int i = 0; i < 3; ++i) t.v[3 * pi + i] = (T)c[i];
+        const int k = oy < 0 ? -oy : oy;
+        if (k > 0) {
+            wb[k][0] += c[0];
+            wb[k][1] += c[2];
         }
     };
     for (int ox = 1; ox <= M; ++ox) {
@@ -233,8 +224,10 @@ PairTab<T, 2, M> make_pairs2(const pd_grid *g)
         for (int oy = -My; oy <= My; ++oy) put(ox, oy);
     }
     for (int oy = 1; oy <= M; ++oy) put(0, oy);
-    constexpr int NP = PairTab<T, 2, M>::kPairs;
-    for (int i = 0; i < 3; ++i) t.v[3 * NP + i] = (T)tot[i];
+    for (int k = 1; k <= M; ++k) {
+        t.v[3 * NP + 2 * (k - 1)] = (T)wb[k][0];
+        t.v[3 * NP + 2 * (k - 1) + 1] = (T)wb[k][1];
+    }
     return t;
 }
 
@@ -251,9 +244,8 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     if ((in_rows != ny || out_rows != ny) && a.dot_partial)
         return fail(PD_ERR_INVALID, "row windows take no fused dot");
     dim3 grid((unsigned)((nx + kTX2 - 1) / kTX2), (unsigned)((out_rows + TY - 1) / TY), (unsigned)a.batch);
-    const T *kd = sizeof(T) == 4 ? (const T *)g->d_kd32 : (const T *)g->d_kd64;
     kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)nx, (int)ny, out_rows * nx, g->d_cons,
-                                      a.project ? 1 : 0, kd, (T)a.scale, make_pairs2<T, M>(g), a.dot_partial,
+                                      a.project ? 1 : 0, (T)a.scale, make_plain<T, M>(g), a.dot_partial,
                                       a.dot_out, a.retire, (int)a.in_row0, in_rows * nx, (int)a.out_row0,
                                       (int)(a.out_row0 + out_rows));
     PD_CUDA(cudaGetLastError());

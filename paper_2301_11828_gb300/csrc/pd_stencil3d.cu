@@ -6,9 +6,10 @@
 // of R outputs.  The (32 + 2M) x (8 + 2M) x (R + 2M) halo box of the three
 // components is staged in shared memory; for each (ox, oy) column pair the
 // thread loads the z-windows of columns (x+ox, y+oy) and (x-ox, y-oy).
-// DIFF (FP32 with PD_ACCURATE) sums (u~_{p+o} - u_p) + (u~_{p-o} - u_p) instead
-// of u~_{p+o} + u~_{p-o}: the FP32 error is then relative to |K u| on smooth
-// fields too, and K u = (Kd_p - Kd_int) u_p - sum.
+// DIFF (the FP32 default; PD_PAIR_FORM selects the pair form) sums
+// (u_{p+o} - u_p) + (u_{p-o} - u_p) over the in-grid neighbours instead of
+// u~_{p+o} + u~_{p-o} against Kd u_p: the FP32 error is then relative to |K u|
+// on smooth fields too, and K u = -sum (no diagonal term to cancel against).
 #include "pd_stencil.cuh"
 
 namespace pd {
@@ -99,61 +100,90 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
             acc[c][r] = T(0);
             if constexpr (DIFF) ctr[c][r] = base[c * PL + (r + M) * SX * SY];
         }
-    // s for one offset pair: the pair sum, or the two differences to the output's own value
-    auto sum2 = [&](T a, T b, int c, int r) -> T {
-        if constexpr (DIFF)
-            return (a - ctr[c][r]) + (b - ctr[c][r]);
-        else
-            return a + b;
-    };
-
-    static_for<0, M + 1>([&](auto OYI) {
-        constexpr int oy = M - decltype(OYI)::value;
-        constexpr int Mx = isqrt_c(M * M - oy * oy);
-        static_for<-Mx, Mx + 1>([&](auto OX) {
-            constexpr int ox = decltype(OX)::value;
-            if constexpr (oy > 0 || ox > 0) {
-                constexpr int Mz = isqrt_c(M * M - ox * ox - oy * oy);
-                constexpr int pbase = pair_index3(M, ox, oy, 0);   // pairs of this column are consecutive in oz
-                T wp[3][SZ], wm[3][SZ];
+    // in-grid tests of the difference form: window plane i holds grid plane z0 - M + i
+    const int gxt = x0 + tx, gyt = y0 + ty;
+    uint32_t zok = 0;
+    if constexpr (DIFF) {
+        static_assert(SZ <= 32, "plane mask is one word");
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int i = 0; i < SZ; ++i) {
-                        wp[c][i] = base[c * PL + i * SX * SY + oy * SX + ox];
-                        wm[c][i] = base[c * PL + i * SX * SY - oy * SX - ox];
-                    }
-#pragma unroll
-                for (int oz = -Mz; oz <= Mz; ++oz) {
-                    const int pi = pbase + oz;
-                    const T *cf = tab.v + 6 * pi;
-                    const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        pair3(acc, r, ox != 0, oy != 0, oz != 0, cxx, cxy, cxz, cyy, cyz, czz,
-                              sum2(wp[0][r + M + oz], wm[0][r + M - oz], 0, r),
-                              sum2(wp[1][r + M + oz], wm[1][r + M - oz], 1, r),
-                              sum2(wp[2][r + M + oz], wm[2][r + M - oz], 2, r));
-                }
-            }
-        });
-    });
+        for (int i = 0; i < SZ; ++i)
+            if (z0 - M + i >= 0 && z0 - M + i < nz) zok |= 1u << i;
+    }
     T w0[3][SZ];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int i = 0; i < SZ; ++i) w0[c][i] = base[c * PL + i * SX * SY];
-    constexpr int pcentre = pair_index3(M, 0, 0, 1);
+    // s for one offset pair: the pair sum, or the two differences to the output's own
+    // value with every term whose neighbour lies outside the grid dropped (the staged
+    // value there is zero, so m (v - u_p) = v - m u_p: one FMA)
+    // (MASK: some neighbour of the warp's outputs lies outside the grid)
+    auto body = [&](auto MASKV) {
+        constexpr bool MASK = decltype(MASKV)::value;
+        auto sum2 = [&](T a, T b, int c, int r, bool cp, bool cm, int ip, int im) -> T {
+            if constexpr (DIFF && MASK) {
+                const T np = (cp && ((zok >> ip) & 1u)) ? T(-1) : T(0);
+                const T nm = (cm && ((zok >> im) & 1u)) ? T(-1) : T(0);
+                return dfma(np, ctr[c][r], a) + dfma(nm, ctr[c][r], b);
+            } else if constexpr (DIFF) {
+                return (a - ctr[c][r]) + (b - ctr[c][r]);
+            } else {
+                return a + b;
+            }
+        };
+
+        static_for<0, M + 1>([&](auto OYI) {
+            constexpr int oy = M - decltype(OYI)::value;
+            constexpr int Mx = isqrt_c(M * M - oy * oy);
+            static_for<-Mx, Mx + 1>([&](auto OX) {
+                constexpr int ox = decltype(OX)::value;
+                if constexpr (oy > 0 || ox > 0) {
+                    constexpr int Mz = isqrt_c(M * M - ox * ox - oy * oy);
+                    constexpr int pbase = pair_index3(M, ox, oy, 0);   // pairs of this column are consecutive in oz
+                    const bool cp = gxt + ox >= 0 && gxt + ox < nx && gyt + oy < ny;
+                    const bool cm = gxt - ox >= 0 && gxt - ox < nx && gyt - oy >= 0;
+                    T wp[3][SZ], wm[3][SZ];
 #pragma unroll
-    for (int oz = 1; oz <= M; ++oz) {
-        const int pi = pcentre + (oz - 1);
-        const T *cf = tab.v + 6 * pi;
-        const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+                    for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            pair3(acc, r, false, false, true, cxx, cxy, cxz, cyy, cyz, czz, T(0), T(0),
-                  sum2(w0[2][r + M + oz], w0[2][r + M - oz], 2, r));
-    }
+                        for (int i = 0; i < SZ; ++i) {
+                            wp[c][i] = base[c * PL + i * SX * SY + oy * SX + ox];
+                            wm[c][i] = base[c * PL + i * SX * SY - oy * SX - ox];
+                        }
+#pragma unroll
+                    for (int oz = -Mz; oz <= Mz; ++oz) {
+                        const int pi = pbase + oz;
+                        const T *cf = tab.v + 6 * pi;
+                        const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            pair3(acc, r, ox != 0, oy != 0, oz != 0, cxx, cxy, cxz, cyy, cyz, czz,
+                                  sum2(wp[0][r + M + oz], wm[0][r + M - oz], 0, r, cp, cm, r + M + oz, r + M - oz),
+                                  sum2(wp[1][r + M + oz], wm[1][r + M - oz], 1, r, cp, cm, r + M + oz, r + M - oz),
+                                  sum2(wp[2][r + M + oz], wm[2][r + M - oz], 2, r, cp, cm, r + M + oz, r + M - oz));
+                    }
+                }
+            });
+        });
+        constexpr int pcentre = pair_index3(M, 0, 0, 1);
+#pragma unroll
+        for (int oz = 1; oz <= M; ++oz) {
+            const int pi = pcentre + (oz - 1);
+            const T *cf = tab.v + 6 * pi;
+            const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                pair3(acc, r, false, false, true, cxx, cxy, cxz, cyy, cyz, czz, T(0), T(0),
+                      sum2(w0[2][r + M + oz], w0[2][r + M - oz], 2, r, true, true, r + M + oz, r + M - oz));
+        }
+    };
+    // warp-uniform: do the warp's 32 columns and R planes keep their whole horizon inside the grid?
+    const bool warp_in = __all_sync(0xffffffffu, gxt >= M && gxt < nx - M) && gyt >= M && gyt < ny - M &&
+                         zok == (SZ >= 32 ? 0xffffffffu : ((1u << SZ) - 1u));
+    if (!DIFF || warp_in)
+        body(std::false_type{});
+    else
+        body(std::true_type{});
 
     T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
     const int gx = x0 + tx, gy = y0 + ty;
@@ -166,7 +196,9 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
             T k0 = kk[0], k1 = kk[1], k2 = kk[2], k3 = kk[3], k4 = kk[4], k5 = kk[5];
             const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M),
                       c0 = min(gz, M), c1 = min(nz - 1 - gz, M);
-            if (a0 != M || a1 != M || b0 != M || b1 != M || c0 != M || c1 != M) {
+            if constexpr (DIFF) {   // the in-grid bond sum: no diagonal term
+                k0 = k1 = k2 = k3 = k4 = k5 = T(0);
+            } else if (a0 != M || a1 != M || b0 != M || b1 != M || c0 != M || c1 != M) {
                 const int cls =
                     ((((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1) * (M + 1) + c0) * (M + 1) + c1;
                 const T *q = kd + 6 * cls;
@@ -176,16 +208,6 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
                 k3 = __ldg(q + 3);
                 k4 = __ldg(q + 4);
                 k5 = __ldg(q + 5);
-                if constexpr (DIFF) {   // the difference sums already hold -Kd_int u_p
-                    k0 -= kk[0];
-                    k1 -= kk[1];
-                    k2 -= kk[2];
-                    k3 -= kk[3];
-                    k4 -= kk[4];
-                    k5 -= kk[5];
-                }
-            } else if constexpr (DIFF) {
-                k0 = k1 = k2 = k3 = k4 = k5 = T(0);
             }
             const T u0 = w0[0][r + M], u1 = w0[1][r + M], u2 = w0[2][r + M];
             T f0 = dfma(k0, u0, dfma(k1, u1, dfma(k2, u2, -acc[0][r])));
@@ -267,8 +289,8 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 template <typename T>
 int run_t(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
-    if constexpr (sizeof(T) == 4) {   // the difference form exists for FP32 only
-        if (a.accurate) {
+    if constexpr (sizeof(T) == 4) {   // FP32: the difference form unless the pair form is asked for
+        if (!a.pair_form) {
             switch (g->M) {
                 case 1: return run<T, 1, true>(g, a, s);
                 case 2: return run<T, 2, true>(g, a, s);
