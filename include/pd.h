@@ -321,10 +321,15 @@ int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const 
  * without a modulus field.  Host-only; no device work. */
 int pd_set_method(pd_grid *g, uint32_t method);
 
-/* Pins the tile height of the FP32 TMA-fed 2D stencil: 32 rows (64 x 32
- * outputs per tile, the default) or 16 (64 x 16; used at M <= 4).  Both give
- * identical results; only the speed differs.  Host-only.  Errors:
- * PD_ERR_INVALID (rows not 16 or 32). */
+/* Pins the layout of the FP32 TMA-fed 2D stencil (the bond sum of Eq. mat:f1
+ * taken as differences of nearby values): rows = 32 (64 x 32 output tiles, the
+ * default) or 16 (64 x 16 tiles; used at M <= 4) -- both give identical bits --
+ * or rows = 0, the column walk: each CTA walks down a strip of 128 columns and
+ * every input row is staged once (no vertical halo), used at M <= 3 for
+ * products without PD_PROJECT or a fused dot (the tile kernel serves the rest).
+ * The walk agrees with the tiles to FP32 rounding, not bit for bit; a band of
+ * rows (pd_matvec_rows) reproduces the whole-grid product of the same layout bit
+ * for bit.  Host-only.  Errors: PD_ERR_INVALID (rows not 0, 16 or 32). */
 int pd_set_stencil_tile_rows(pd_grid *g, int rows);
 
 /* Autotuner: measures the candidates of K u for the precision(s) in flags

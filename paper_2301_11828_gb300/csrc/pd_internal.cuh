@@ -121,7 +121,8 @@ struct pd_grid {
 
     // measured method choice cache: [dtype 0/1] -> 0 unknown, 1 stencil, 2 fft
     int auto_choice[2] = {0, 0};
-    // FP32 2D stencil tile height chosen by the autotuner: 32 (default) or 16 rows
+    // FP32 2D stencil layout chosen by the autotuner: 64 x 32 tiles (32), 64 x 16
+    // tiles (16) or the column walk (0)
     int stencil_tile_rows = 32;
     void *tune_ws = nullptr;         // autotuner scratch (two vectors), kept by the grid
 
@@ -171,6 +172,8 @@ int launch_stencil(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);
 int stencil_blocks(pd_grid *g, bool f64, bool direct);   // CTAs per field (for sizing partials)
 bool tma_stencil_eligible(const pd_grid *g, const MatvecArgs &a, bool f64);
 int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s);
+bool walk_stencil_eligible(const pd_grid *g, const MatvecArgs &a);
+int run_tbt2d_walk(pd_grid *g, const MatvecArgs &a, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers (pd_fft.cu)
 int launch_fft_tile(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s);

@@ -25,7 +25,10 @@ int launch_stencil(pd_grid *g, bool f64, const MatvecArgs &a, cudaStream_t s)
     if (a.batch < 1 || a.batch > 65535) return fail(PD_ERR_INVALID, "batch must be in [1, 65535]");
     if (g->dim == 2) {
         if (a.use_E || a.use_mu) return run_direct2d(g, f64, a, s);
-        if (!g->no_tma && !a.no_tma && tma_stencil_eligible(g, a, f64)) return run_tbt2d_tma(g, a, s);
+        if (!g->no_tma && !a.no_tma && tma_stencil_eligible(g, a, f64)) {
+            if (g->stencil_tile_rows == 0 && walk_stencil_eligible(g, a)) return run_tbt2d_walk(g, a, s);
+            return run_tbt2d_tma(g, a, s);
+        }
         return run_tbt2d(g, f64, a, s);
     }
     return run_tbt3d(g, f64, a, s);
@@ -39,7 +42,7 @@ int stencil_blocks(pd_grid *g, bool f64, bool direct)
         const int TY = kGY2 * R;
         return (int)(((g->n[0] + kTX2 - 1) / kTX2) * ((g->n[1] + TY - 1) / TY));
     }
-    const int R = f64 ? 4 : 8;
+    const int R = 4;   // the smaller of the 3D forms' z-rows per thread (the most CTAs)
     return (int)(((g->n[0] + kTX3 - 1) / kTX3) * ((g->n[1] + kTY3 - 1) / kTY3) * ((g->n[2] + R - 1) / R));
 }
 

@@ -37,8 +37,10 @@ template <typename T, int M>
 __host__ __device__ constexpr int rows2d() { return sizeof(T) == 4 ? 8 : (M <= 4 ? 4 : 2); }
 template <typename T, int M>
 __host__ __device__ constexpr int rows2d_direct() { return sizeof(T) == 4 ? 4 : 2; }
-template <typename T, int M>
-__host__ __device__ constexpr int rows3d() { return sizeof(T) == 4 ? 8 : 4; }
+// z-rows per thread of the 3D stencil: 8 for the FP32 pair form, 4 otherwise (the
+// difference form keeps the own column and the H windows in registers)
+template <typename T, int M, bool DIFF = false>
+__host__ __device__ constexpr int rows3d() { return (sizeof(T) == 4 && !DIFF) ? 8 : 4; }
 
 // ------------------------------------------------------------------ kernel walk orders
 // 2D TBT pairs: ox = 1..M (oy = -My..My), then ox = 0 (oy = 1..M).

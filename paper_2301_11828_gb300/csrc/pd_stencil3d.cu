@@ -44,8 +44,130 @@ __device__ __forceinline__ void pair3(T (&acc)[3][R], int r, bool nx_, bool ny_,
     }
 }
 
+// Accurate (difference) form of the bond sum for one thread's z-column of R
+// outputs.  For a column pair (ox, oy) let H+(i) = u(x+ox, y+oy, i) - u(x, y, i)
+// and H-(i) = u(x-ox, y-oy, i) - u(x, y, i) (plane i of the window), and in the
+// own column V_k(r) = u(r + k) - u(r).  The pair sum of offset (ox, oy, oz) is
+//   s = H+(r + oz) + H-(r - oz) + V_oz(r) + V_-oz(r),
+// so the windows of the column pair are turned into H+- once per plane and the
+// vertical parts of every pair with |oz| = k are summed once per output:
+//   Cbar(k) (V_k(r) + V_-k(r)),  Cbar(k) = c(0,0,k) + sum over column pairs of
+//   c(ox,oy,k) + c(ox,oy,-k)  (diagonal: xz, yz flip sign with oz, xy cancel
+//   between (ox, oy) and (-ox, oy)).
+// Every operand is a difference of nearby values, so the FP32 error stays
+// relative to |K u| on smooth fields.  MASK (some neighbour of the warp leaves the
+// grid): H+- carry the lane's in-grid flags m+- of the two columns, and for the
+// pairs (ox, oy, +-k) of one column pair the vertical parts combine to
+//   S (m+ + m-) (A + B) + Q (m+ - m-) (A - B),
+// A = v(r+k) V_k(r), B = v(r-k) V_-k(r) (v: the plane lies in the grid), S the
+// xx/xy/yy/zz and Q the xz/yz entries of c(ox, oy, k): per-lane coefficients
+// cb (xx, xy, yy, zz) and dq (xz, yz).  Out-of-grid planes are zero in the box,
+// so their H vanish by themselves.  acc receives sum c(o) s (K u = -acc).
+template <typename T, int M, bool MASK>
+__device__ __forceinline__ void diff3_column(const T *base, const PairTab<T, 3, M> &tab, int gx, int gy, int nx,
+                                             int ny, uint32_t zok, T (&acc)[3][rows3d<T, M, true>()])
+{
+    constexpr int R = rows3d<T, M, true>();
+    constexpr int SX = kTX3 + 2 * M, SY = kTY3 + 2 * M, SZ = R + 2 * M;
+    constexpr int PL = SX * SY * SZ;
+    T w0[3][SZ];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int i = 0; i < SZ; ++i) w0[c][i] = base[c * PL + i * SX * SY];
+    // per-lane vertical coefficients (all flags 1 on interior warps)
+    T cb[M][4], dq[M][2];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const T *cc = tab.v + 6 * pair_index3(M, 0, 0, k + 1);
+        cb[k][0] = cb[k][1] = cb[k][2] = T(0);
+        cb[k][3] = cc[5];
+        dq[k][0] = dq[k][1] = T(0);
+    }
+    static_for<0, M + 1>([&](auto OYI) {
+        constexpr int oy = M - decltype(OYI)::value;
+        constexpr int Mx = isqrt_c(M * M - oy * oy);
+        static_for<-Mx, Mx + 1>([&](auto OX) {
+            constexpr int ox = decltype(OX)::value;
+            if constexpr (oy > 0 || ox > 0) {
+                constexpr int Mz = isqrt_c(M * M - ox * ox - oy * oy);
+                T mp = T(1), mm = T(1);
+                if constexpr (MASK) {
+                    mp = (gx + ox >= 0 && gx + ox < nx && gy + oy < ny) ? T(1) : T(0);
+                    mm = (gx - ox >= 0 && gx - ox < nx && gy - oy >= 0) ? T(1) : T(0);
+                }
+                static_for<1, Mz + 1>([&](auto K) {
+                    constexpr int k = decltype(K)::value;
+                    const T *cc = tab.v + 6 * pair_index3(M, ox, oy, k);   // xx, xy, xz, yy, yz, zz
+                    const T sp = mp + mm, sq = mp - mm;
+                    cb[k - 1][0] = dfma(sp, cc[0], cb[k - 1][0]);
+                    cb[k - 1][1] = dfma(sp, cc[1], cb[k - 1][1]);
+                    cb[k - 1][2] = dfma(sp, cc[3], cb[k - 1][2]);
+                    cb[k - 1][3] = dfma(sp, cc[5], cb[k - 1][3]);
+                    dq[k - 1][0] = dfma(sq, cc[2], dq[k - 1][0]);
+                    dq[k - 1][1] = dfma(sq, cc[4], dq[k - 1][1]);
+                });
+                // H+- over the planes the pairs of this column reach, formed once per plane;
+                // outputs in the outer loop so that only 2 Mz + 1 planes of H are live at a time
+                constexpr int NW = R + 2 * Mz, I0 = M - Mz;
+                T hp[3][NW], hm[3][NW];
+                auto form = [&](int j) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int i = I0 + j;
+                        const T a = base[c * PL + i * SX * SY + oy * SX + ox] - w0[c][i];
+                        const T b = base[c * PL + i * SX * SY - oy * SX - ox] - w0[c][i];
+                        hp[c][j] = MASK ? mp * a : a;
+                        hm[c][j] = MASK ? mm * b : b;
+                    }
+                };
+#pragma unroll
+                for (int j = 0; j < 2 * Mz; ++j) form(j);
+                constexpr int pbase = pair_index3(M, ox, oy, 0);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    form(r + 2 * Mz);
+#pragma unroll
+                    for (int oz = -Mz; oz <= Mz; ++oz) {
+                        const T *cf = tab.v + 6 * (pbase + oz);
+                        pair3(acc, r, ox != 0, oy != 0, oz != 0, cf[0], cf[1], cf[2], cf[3], cf[4], cf[5],
+                              hp[0][r + Mz + oz] + hm[0][r + Mz - oz], hp[1][r + Mz + oz] + hm[1][r + Mz - oz],
+                              hp[2][r + Mz + oz] + hm[2][r + Mz - oz]);
+                    }
+                }
+            }
+        });
+    });
+    // vertical parts
+#pragma unroll
+    for (int k = 1; k <= M; ++k) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            T A[3], B[3];
+            const bool va = !MASK || ((zok >> (r + M + k)) & 1u), vb = !MASK || ((zok >> (r + M - k)) & 1u);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                A[c] = va ? w0[c][r + M + k] - w0[c][r + M] : T(0);
+                B[c] = vb ? w0[c][r + M - k] - w0[c][r + M] : T(0);
+            }
+            const T W0 = A[0] + B[0], W1 = A[1] + B[1], W2 = A[2] + B[2];
+            const T *q = cb[k - 1];
+            if constexpr (MASK) {
+                const T C0 = A[0] - B[0], C1 = A[1] - B[1], C2 = A[2] - B[2];
+                acc[0][r] = dfma(dq[k - 1][0], C2, dfma(q[1], W1, dfma(q[0], W0, acc[0][r])));
+                acc[1][r] = dfma(dq[k - 1][1], C2, dfma(q[1], W0, dfma(q[2], W1, acc[1][r])));
+                acc[2][r] = dfma(dq[k - 1][1], C1, dfma(dq[k - 1][0], C0, dfma(q[3], W2, acc[2][r])));
+            } else {   // the xy entry of Cbar is exactly zero on interior warps
+                acc[0][r] = dfma(q[0], W0, acc[0][r]);
+                acc[1][r] = dfma(q[2], W1, acc[1][r]);
+                acc[2][r] = dfma(q[3], W2, acc[2][r]);
+            }
+        }
+    }
+}
+
 template <typename T, int M, bool DIFF>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
         const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
         PairTab<T, 3, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
@@ -54,7 +176,7 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
     // Planes are grid planes; the input holds planes [in_z0, ...) with component size
     // Nin, the output planes [out_z0, out_zend) with component size N (the whole
     // grid: 0, N, 0, nz).
-    constexpr int R = rows3d<T, M>();
+    constexpr int R = rows3d<T, M, DIFF>();
     constexpr int TX = kTX3, TY = kTY3, SX = TX + 2 * M, SY = TY + 2 * M, SZ = R + 2 * M;
     constexpr int PL = SX * SY * SZ;
     constexpr int NP = PairTab<T, 3, M>::kPairs;
@@ -92,46 +214,37 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
 
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const T *base = s + (ty + M) * SX + (tx + M);   // column (x, y), plane 0
-    T acc[3][R], ctr[3][DIFF ? R : 1];
+    T acc[3][R];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            acc[c][r] = T(0);
-            if constexpr (DIFF) ctr[c][r] = base[c * PL + (r + M) * SX * SY];
-        }
-    // in-grid tests of the difference form: window plane i holds grid plane z0 - M + i
+        for (int r = 0; r < R; ++r) acc[c][r] = T(0);
     const int gxt = x0 + tx, gyt = y0 + ty;
+    // window plane i holds grid plane z0 - M + i
+    static_assert(SZ <= 32, "plane mask is one word");
     uint32_t zok = 0;
-    if constexpr (DIFF) {
-        static_assert(SZ <= 32, "plane mask is one word");
 #pragma unroll
-        for (int i = 0; i < SZ; ++i)
-            if (z0 - M + i >= 0 && z0 - M + i < nz) zok |= 1u << i;
-    }
+    for (int i = 0; i < SZ; ++i)
+        if (z0 - M + i >= 0 && z0 - M + i < nz) zok |= 1u << i;
     T w0[3][SZ];
+    if constexpr (DIFF) {
+        // warp-uniform: do the warp's 32 columns and R planes keep their whole horizon inside the grid?
+        const bool warp_in = __all_sync(0xffffffffu, gxt >= M && gxt < nx - M) && gyt >= M && gyt < ny - M &&
+                             zok == (SZ >= 32 ? 0xffffffffu : ((1u << SZ) - 1u));
+        if (warp_in)
+            diff3_column<T, M, false>(base, tab, gxt, gyt, nx, ny, zok, acc);
+        else
+            diff3_column<T, M, true>(base, tab, gxt, gyt, nx, ny, zok, acc);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int i = 0; i < SZ; ++i) w0[c][i] = base[c * PL + i * SX * SY];
-    // s for one offset pair: the pair sum, or the two differences to the output's own
-    // value with every term whose neighbour lies outside the grid dropped (the staged
-    // value there is zero, so m (v - u_p) = v - m u_p: one FMA)
-    // (MASK: some neighbour of the warp's outputs lies outside the grid)
-    auto body = [&](auto MASKV) {
-        constexpr bool MASK = decltype(MASKV)::value;
-        auto sum2 = [&](T a, T b, int c, int r, bool cp, bool cm, int ip, int im) -> T {
-            if constexpr (DIFF && MASK) {
-                const T np = (cp && ((zok >> ip) & 1u)) ? T(-1) : T(0);
-                const T nm = (cm && ((zok >> im) & 1u)) ? T(-1) : T(0);
-                return dfma(np, ctr[c][r], a) + dfma(nm, ctr[c][r], b);
-            } else if constexpr (DIFF) {
-                return (a - ctr[c][r]) + (b - ctr[c][r]);
-            } else {
-                return a + b;
-            }
-        };
-
+            for (int r = 0; r < R; ++r) w0[c][r + M] = base[c * PL + (r + M) * SX * SY];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < SZ; ++i) w0[c][i] = base[c * PL + i * SX * SY];
+        // pair form: acc[.][r] += c(o) (u~_{p+o} + u~_{p-o}), against Kd u_p below
         static_for<0, M + 1>([&](auto OYI) {
             constexpr int oy = M - decltype(OYI)::value;
             constexpr int Mx = isqrt_c(M * M - oy * oy);
@@ -140,8 +253,6 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
                 if constexpr (oy > 0 || ox > 0) {
                     constexpr int Mz = isqrt_c(M * M - ox * ox - oy * oy);
                     constexpr int pbase = pair_index3(M, ox, oy, 0);   // pairs of this column are consecutive in oz
-                    const bool cp = gxt + ox >= 0 && gxt + ox < nx && gyt + oy < ny;
-                    const bool cm = gxt - ox >= 0 && gxt - ox < nx && gyt - oy >= 0;
                     T wp[3][SZ], wm[3][SZ];
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
@@ -152,15 +263,13 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
                         }
 #pragma unroll
                     for (int oz = -Mz; oz <= Mz; ++oz) {
-                        const int pi = pbase + oz;
-                        const T *cf = tab.v + 6 * pi;
+                        const T *cf = tab.v + 6 * (pbase + oz);
                         const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
 #pragma unroll
                         for (int r = 0; r < R; ++r)
                             pair3(acc, r, ox != 0, oy != 0, oz != 0, cxx, cxy, cxz, cyy, cyz, czz,
-                                  sum2(wp[0][r + M + oz], wm[0][r + M - oz], 0, r, cp, cm, r + M + oz, r + M - oz),
-                                  sum2(wp[1][r + M + oz], wm[1][r + M - oz], 1, r, cp, cm, r + M + oz, r + M - oz),
-                                  sum2(wp[2][r + M + oz], wm[2][r + M - oz], 2, r, cp, cm, r + M + oz, r + M - oz));
+                                  wp[0][r + M + oz] + wm[0][r + M - oz], wp[1][r + M + oz] + wm[1][r + M - oz],
+                                  wp[2][r + M + oz] + wm[2][r + M - oz]);
                     }
                 }
             });
@@ -168,22 +277,14 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
         constexpr int pcentre = pair_index3(M, 0, 0, 1);
 #pragma unroll
         for (int oz = 1; oz <= M; ++oz) {
-            const int pi = pcentre + (oz - 1);
-            const T *cf = tab.v + 6 * pi;
-            const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+            const T *cf = tab.v + 6 * (pcentre + oz - 1);
+            const T czz = cf[5];
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                pair3(acc, r, false, false, true, cxx, cxy, cxz, cyy, cyz, czz, T(0), T(0),
-                      sum2(w0[2][r + M + oz], w0[2][r + M - oz], 2, r, true, true, r + M + oz, r + M - oz));
+                pair3(acc, r, false, false, true, T(0), T(0), T(0), T(0), T(0), czz, T(0), T(0),
+                      w0[2][r + M + oz] + w0[2][r + M - oz]);
         }
-    };
-    // warp-uniform: do the warp's 32 columns and R planes keep their whole horizon inside the grid?
-    const bool warp_in = __all_sync(0xffffffffu, gxt >= M && gxt < nx - M) && gyt >= M && gyt < ny - M &&
-                         zok == (SZ >= 32 ? 0xffffffffu : ((1u << SZ) - 1u));
-    if (!DIFF || warp_in)
-        body(std::false_type{});
-    else
-        body(std::true_type{});
+    }
 
     T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
     const int gx = x0 + tx, gy = y0 + ty;
@@ -265,7 +366,7 @@ PairTab<T, 3, M> make_pairs3(const pd_grid *g)
 template <typename T, int M, bool DIFF>
 int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
-    constexpr int R = rows3d<T, M>();
+    constexpr int R = rows3d<T, M, DIFF>();
     const size_t smem = sizeof(T) * 3 * (kTX3 + 2 * M) * (kTY3 + 2 * M) * (R + 2 * M);
     auto kern = k_tbt3d<T, M, DIFF>;
     allow_smem(kern, smem);
