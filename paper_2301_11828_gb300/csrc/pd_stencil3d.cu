@@ -167,7 +167,7 @@ __device__ __forceinline__ void diff3_column(const T *base, const PairTab<T, 3, 
 }
 
 template <typename T, int M, bool DIFF>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, (DIFF && M <= 3) ? 3 : 2)
 k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
         const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
         PairTab<T, 3, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
@@ -228,13 +228,9 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
         if (z0 - M + i >= 0 && z0 - M + i < nz) zok |= 1u << i;
     T w0[3][SZ];
     if constexpr (DIFF) {
-        // warp-uniform: do the warp's 32 columns and R planes keep their whole horizon inside the grid?
-        const bool warp_in = __all_sync(0xffffffffu, gxt >= M && gxt < nx - M) && gyt >= M && gyt < ny - M &&
-                             zok == (SZ >= 32 ? 0xffffffffu : ((1u << SZ) - 1u));
-        if (warp_in)
-            diff3_column<T, M, false>(base, tab, gxt, gyt, nx, ny, zok, acc);
-        else
-            diff3_column<T, M, true>(base, tab, gxt, gyt, nx, ny, zok, acc);
+        // one instantiation for every warp: the in-grid flags are 1 on interior lanes (half
+        // the code of a separate interior copy, which measured slower for its instruction-cache misses)
+        diff3_column<T, M, true>(base, tab, gxt, gyt, nx, ny, zok, acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
