@@ -41,13 +41,13 @@ BATCH = 32          # 32 fields x 2 comps x 1M nodes x 4 B = 268 MB of inputs (>
 # DRAM traffic of the dominant kernel per launch (ncu, dram__bytes_read.sum + dram__bytes_write.sum),
 # recorded with the hash of the kernel sources it was taken on; reported only while they match.
 TRAFFIC = {
-    "kernel": "k_tbt2d_acc<3> (difference form)",
+    "kernel": "k_tbt2d_acc<3, 8> (64 x 64 tiles, difference form)",
     "sources": ["paper_2301_11828_gb300/csrc/pd_stencil2d_tma.cu", "paper_2301_11828_gb300/csrc/pd_tma2d.cuh",
                 "paper_2301_11828_gb300/csrc/pd_stencil.cuh", "paper_2301_11828_gb300/csrc/pd_reduce.cuh"],
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch on 32 fields (the ncu capture
     # summarised under profiles/) divided by 32; valid while the sources hash to sha256
-    "sha256": "5e900be9a70708f5c9758961ea030231186ea704da1008efb95f02c8b3a6d5ef",
-    "bytes_per_field": 15637912,
+    "sha256": "3bcbc9f13d9aa152cd3985ed4356147885b2b0810ef576d0ed1416e2e62c2b34",
+    "bytes_per_field": 15321312,
 }
 
 
@@ -762,14 +762,14 @@ def _extras(torch, pd, syn, dev):
     return out
 
 
-CASES = ("fft2d", "stencil2d_f64", "stencil3d", "fft3d", "crack", "cg", "adr", "adr_mixed", "sc", "kw3d")
+CASES = ("fft2d", "stencil2d_f64", "walk2d", "stencil3d", "fft3d", "crack", "cg", "adr", "adr_mixed", "sc", "kw3d")
 
 
 def run_case(args):
     """One secondary workload in a loop (for ncu launch lists and captures); prints one JSON line.
 
     fft2d: K u, 1024^2 plate, M=3, FP32 FFT tiles, 8 fields.  stencil2d_f64: the same with the FP64
-    stencil, 4 fields.  stencil3d / fft3d: K u on the 128^3 cube, M=3, FP32.  crack: one Verlet step
+    stencil, 4 fields.  walk2d: the same with the FP32 column walk, 16 fields.  stencil3d / fft3d: K u on the 128^3 cube, M=3, FP32.  crack: one Verlet step
     with bond breaking on the pre-notched 512^2 plate.  cg: 64 iterations of the mixed CG on the
     1024^2 plate (graph-replayed inner loop).  adr / adr_mixed: 64 ADR iterations (Algorithm 1, FP64 /
     mixed) on that plate.  sc: K u with the surface correction, 1024^2, FP32, 8 fields.  kw3d: one Verlet
@@ -782,10 +782,14 @@ def run_case(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     case = args.case
-    if case in ("fft2d", "stencil2d_f64"):
+    if case in ("fft2d", "stencil2d_f64", "walk2d"):
         w = syn.large_plate(3)
         g = pd.Grid(2, w.n, w.h, w.M)
-        dt, B, meth = (torch.float32, 8, pd.PD_METHOD_FFT) if case == "fft2d" else (torch.float64, 4, pd.PD_METHOD_STENCIL)
+        dt, B, meth = {"fft2d": (torch.float32, 8, pd.PD_METHOD_FFT),
+                       "stencil2d_f64": (torch.float64, 4, pd.PD_METHOD_STENCIL),
+                       "walk2d": (torch.float32, 16, pd.PD_METHOD_STENCIL)}[case]
+        if case == "walk2d":
+            g.set_stencil_tile_rows(0)   # the column walk
         U = torch.rand((B, 2, NSIDE, NSIDE), dtype=dt, device=dev) * 2 - 1
         O = torch.empty_like(U)
         step, units = (lambda: g.matvec(U, O, flags=meth)), B * 2 * w.N

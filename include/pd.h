@@ -65,12 +65,13 @@ typedef enum {
 #define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
 #define PD_ACCURATE       0x800u /* accepted for compatibility: every FP32 stencil sums differences of
                                     nearby values by default (see PD_PAIR_FORM) */
-#define PD_PAIR_FORM      0x1000u /* FP32 stencils: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o)
+#define PD_PAIR_FORM      0x1000u /* stencils: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o)
                                     instead of the default difference form.  Less arithmetic, but its
-                                    FP32 error is relative to sum |c| |u|, not to |K u|: on smooth fields,
-                                    or fields with a large constant part, it exceeds 1e-4 relative
-                                    error (2D).  For comparison, and for inner solver products whose
-                                    rounding an FP64 refinement corrects */
+                                    error is relative to sum |c| |u|, not to |K u|: on smooth fields,
+                                    or fields with a large constant part, FP32 exceeds 1e-4 relative
+                                    error (2D) and FP64 reaches a few 1e-12.  For comparison, for inner
+                                    solver products whose rounding an FP64 refinement corrects, and
+                                    for the FP64 CG and ADR iterations (tolerance far above it) */
 
 /* ---- modes for pd_set_surface_correction ---- */
 #define PD_SC_NONE   0    /* the paper's operator A = A^ + D^e + D^f (default) */

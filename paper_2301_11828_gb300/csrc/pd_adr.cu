@@ -508,10 +508,12 @@ Dens recip(const Dens &D)
 }
 
 // One iteration on the force buffer `cur` (the other holds the previous force).
+// The FP64 product takes the pair form: its rounding (a few 1e-12 relative at most)
+// is far below the solver's tolerance, and the FP64 pipe bounds the product.
 int adr_iteration(pd_grid *g, AdrWs *w, double *u, const Dens &D, int cur, cudaStream_t s)
 {
     double *q = w->q[cur], *q_old = w->q[cur ^ 1];
-    int rc = matvec(g, 1, u, q, PD_F64 | PD_PROJECT | kInputProjected, s);
+    int rc = matvec(g, 1, u, q, PD_F64 | PD_PAIR_FORM | PD_PROJECT | kInputProjected, s);
     if (rc) return rc;
     k_adr_reduce<<<w->blocks, kBlk, 0, s>>>(u, w->v, q, q_old, w->pb, g->N, g->dim, D, w->sc, w->partial);
     k_adr_update<<<w->blocks, kBlk, 0, s>>>(u, w->v, q, w->pb, g->N, g->dim, recip(D), w->sc);

@@ -446,8 +446,8 @@ int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const 
 int pd_set_stencil_tile_rows(pd_grid *g, int rows)
 {
     if (!g) return fail(PD_ERR_INVALID, "grid is NULL");
-    if (rows != 32 && rows != 16 && rows != 0)
-        return fail(PD_ERR_INVALID, "tile rows must be 32, 16 or 0 (column walk)");
+    if (rows != 64 && rows != 32 && rows != 16 && rows != 0)
+        return fail(PD_ERR_INVALID, "tile rows must be 64, 32, 16 or 0 (column walk)");
     g->stencil_tile_rows = rows;
     ++g->op_stamp;
     return PD_OK;

@@ -502,12 +502,13 @@ int iteration(pd_grid *g, CgWs *w, bool f64, double *x64, cudaStream_t s, bool f
         return PD_OK;
     }
     const bool fuse = !(g->broken_total > 0 && !g->has_E) && !g->sc;
-    // FP32: the difference form in 2D (fewer iterations for 25 % more stencil work); the 3D
-    // stencil is ALU-bound and its difference form costs more time than it saves iterations
-    // the inner FP32 products: the difference form in 2D; the pair form in 3D (ALU-bound there;
-    // the FP64 refinement corrects its rounding)
+    // The inner FP32 products: the difference form in 2D (fewer iterations for 25 % more
+    // stencil work); the pair form in 3D (ALU-bound there; the FP64 refinement corrects its
+    // rounding).  Plain FP64 CG: the pair form (its rounding, a few 1e-12 relative at most,
+    // is far below the solver's tolerance; the FP64 pipe bounds the product and the pair
+    // form executes a fifth fewer FP64 operations than the difference form).
     const uint32_t acc = g->dim == 2 ? PD_ACCURATE : PD_PAIR_FORM;
-    const uint32_t fl = (f64 ? PD_F64 : PD_F32 | acc) | PD_PROJECT | kInputProjected;
+    const uint32_t fl = (f64 ? PD_F64 | PD_PAIR_FORM : PD_F32 | acc) | PD_PROJECT | kInputProjected;
     void *p = f64 ? (void *)w->p64 : (void *)w->p32;
     void *q = f64 ? (void *)w->q64 : (void *)w->q32;
     int rc;

@@ -121,9 +121,10 @@ struct pd_grid {
 
     // measured method choice cache: [dtype 0/1] -> 0 unknown, 1 stencil, 2 fft
     int auto_choice[2] = {0, 0};
-    // FP32 2D stencil layout chosen by the autotuner: 64 x 32 tiles (32), 64 x 16
-    // tiles (16) or the column walk (0)
-    int stencil_tile_rows = 32;
+    // FP32 2D stencil layout: 64 x 64 tiles (64, the default; used at M <= 3),
+    // 64 x 32 (32; beyond M = 3 the 64 setting falls back to it), 64 x 16 (16;
+    // used at M <= 4) or the column walk (0); set by the autotuner
+    int stencil_tile_rows = 64;
     void *tune_ws = nullptr;         // autotuner scratch (two vectors), kept by the grid
 
     void *cg = nullptr;        // CG workspace and captured graphs (pd_cg.cu)

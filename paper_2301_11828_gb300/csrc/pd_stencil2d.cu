@@ -14,7 +14,8 @@
 // components is staged in shared memory once; a thread walks its column offsets
 // and, for each, applies every (ox, oy) pair to its R outputs.  Block entries
 // that vanish by geometry (c_xy and c_yy of (ox, 0), c_xx and c_xy of (0, oy))
-// are skipped at compile time.
+// are skipped at compile time.  PD_PAIR_FORM selects the pair form
+// (k_tbt2d_pair, below).
 #include "pd_stencil.cuh"
 
 namespace pd {
@@ -201,6 +202,135 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
     }
 }
 
+
+// The pair form  (K u)_p = Kd_p u_p - sum_{o in half} c(o) (u~_{p+o} + u~_{p-o})
+// (PD_PAIR_FORM; u~ zero outside the grid, Kd_p the diagonal block over the
+// in-grid offsets from the clipped-distance table, which folds in the edge
+// self-term D^e of Eq. tea:sc).  Fewer operations than the difference form, but
+// its rounding error is relative to sum |c| |u| rather than |K u| (in FP64 at most
+// a few 1e-12 on smooth fields with a constant part): used where a solver's
+// own tolerance is far above that, e.g. the FP64 CG and ADR iterations.
+template <typename T, int M>
+__global__ void __launch_bounds__(kThreads)
+k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
+             const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
+             PairTab<T, 2, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
+             int in_row0, int64_t Nin, int out_row0, int out_end)
+{
+    constexpr int R = rows2d<T, M>();
+    constexpr int TX = kTX2, TY = kGY2 * R, SX = TX + 2 * M, SY = TY + 2 * M, WL = R + 2 * M;
+    constexpr int NP = PairTab<T, 2, M>::kPairs;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_x = reinterpret_cast<T *>(smem_raw);
+    T *s_y = s_x + SX * SY;
+
+    const int64_t b = blockIdx.z;
+    const T *ub = u + b * 2 * Nin - (int64_t)in_row0 * nx;   // indexed by grid node
+    T *ob = out + b * 2 * N - (int64_t)out_row0 * nx;
+    const int x0 = blockIdx.x * TX, y0 = out_row0 + blockIdx.y * TY;
+
+    for (int t = threadIdx.x; t < SX * SY; t += kThreads) {
+        const int r = t / SX, c = t - r * SX;
+        const int gx = x0 - M + c, gy = y0 - M + r;
+        T vx = T(0), vy = T(0);
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+            const int64_t p = (int64_t)gy * nx + gx;
+            vx = __ldg(ub + p);
+            vy = __ldg(ub + Nin + p);
+            if (project) {
+                const uint8_t m = __ldg(cons + p);
+                if (m & 1) vx = T(0);
+                if (m & 2) vy = T(0);
+            }
+        }
+        s_x[t] = vx;
+        s_y[t] = vy;
+    }
+    __syncthreads();
+
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const T *colx = s_x + (ty * R) * SX + tx + M;   // (row0, col) of this thread's column
+    const T *coly = s_y + (ty * R) * SX + tx + M;
+    T ax[R], ay[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) { ax[r] = T(0); ay[r] = T(0); }
+    static_for<1, M + 1>([&](auto OX) {
+        constexpr int ox = decltype(OX)::value;
+        constexpr int My = isqrt_c(M * M - ox * ox);
+        T px[WL], py[WL], mx[WL], my[WL];
+#pragma unroll
+        for (int i = 0; i < WL; ++i) {
+            px[i] = colx[i * SX + ox];
+            py[i] = coly[i * SX + ox];
+            mx[i] = colx[i * SX - ox];
+            my[i] = coly[i * SX - ox];
+        }
+        static_for<-My, My + 1>([&](auto OY) {
+            constexpr int oy = decltype(OY)::value;
+            constexpr int pi = pair_index2(M, ox, oy);
+            const T cxx = tab.v[3 * pi], cxy = tab.v[3 * pi + 1], cyy = tab.v[3 * pi + 2];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const T sx = px[r + M + oy] + mx[r + M - oy];
+                if constexpr (oy == 0) {
+                    ax[r] = dfma(cxx, sx, ax[r]);   // axis pair: c_xy = c_yy = 0 exactly
+                } else {
+                    const T sy = py[r + M + oy] + my[r + M - oy];
+                    ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
+                    ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
+                }
+            }
+        });
+    });
+    T cx[WL], cy[WL];
+#pragma unroll
+    for (int i = 0; i < WL; ++i) {
+        cx[i] = colx[i * SX];
+        cy[i] = coly[i * SX];
+    }
+    static_for<1, M + 1>([&](auto OY) {
+        constexpr int oy = decltype(OY)::value;
+        constexpr int pi = pair_index2(M, 0, oy);
+        const T cyy = tab.v[3 * pi + 2];   // axis pair: c_xx = c_xy = 0 exactly
+#pragma unroll
+        for (int r = 0; r < R; ++r) ay[r] = dfma(cyy, cy[r + M + oy] + cy[r + M - oy], ay[r]);
+    });
+
+    T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
+    const int gx = x0 + tx;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int gy = y0 + ty * R + r;
+        if (gx < nx && gy < out_end) {
+            const int64_t p = (int64_t)gy * nx + gx;
+            const T upx = cx[r + M], upy = cy[r + M];
+            T kxx = tab.v[3 * NP], kxy = tab.v[3 * NP + 1], kyy = tab.v[3 * NP + 2];
+            const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
+            if (a0 != M || a1 != M || b0 != M || b1 != M) {
+                const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
+                kxx = __ldg(kd + 3 * cls);
+                kxy = __ldg(kd + 3 * cls + 1);
+                kyy = __ldg(kd + 3 * cls + 2);
+            }
+            T fx = dfma(kxx, upx, dfma(kxy, upy, -ax[r]));
+            T fy = dfma(kxy, upx, dfma(kyy, upy, -ay[r]));
+            if (project) {
+                const uint8_t m = __ldg(cons + p);
+                if (m & 1) fx = T(0);
+                if (m & 2) fy = T(0);
+            }
+            fx *= scale;
+            fy *= scale;
+            ob[p] = fx;
+            ob[N + p] = fy;
+            dot = dfma(upx, fx, dfma(upy, fy, dot));
+        }
+    }
+    if (dot_partial)
+        finish_block_dot(dot, dot_partial, dot_out, retire, gridDim.x * gridDim.y,
+                         blockIdx.x + gridDim.x * blockIdx.y, b);
+}
+
 namespace {
 
 template <typename T, int M>
@@ -252,9 +382,68 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     return PD_OK;
 }
 
+
+template <typename T, int M>
+PairTab<T, 2, M> make_pairs2(const pd_grid *g)
+{
+    PairTab<T, 2, M> t{};
+    double c[6], tot[3] = {0, 0, 0};
+    auto put = [&](int ox, int oy) {
+        const int pi = pair_index2(M, ox, oy);
+        coef_of(g, ox, oy, 0, false, c);
+        for (int i = 0; i < 3; ++i) {
+            t.v[3 * pi + i] = (T)c[i];
+            tot[i] += 2 * c[i];
+        }
+    };
+    for (int ox = 1; ox <= M; ++ox) {
+        const int My = isqrt_c(M * M - ox * ox);
+        for (int oy = -My; oy <= My; ++oy) put(ox, oy);
+    }
+    for (int oy = 1; oy <= M; ++oy) put(0, oy);
+    constexpr int NP = PairTab<T, 2, M>::kPairs;
+    for (int i = 0; i < 3; ++i) t.v[3 * NP + i] = (T)tot[i];
+    return t;
+}
+
+template <typename T, int M>
+int run_pair(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
+{
+    constexpr int R = rows2d<T, M>();
+    constexpr int TY = kGY2 * R;
+    const size_t smem = sizeof(T) * 2 * (kTX2 + 2 * M) * (TY + 2 * M);
+    auto kern = k_tbt2d_pair<T, M>;
+    allow_smem(kern, smem);
+    const int64_t nx = g->n[0], ny = g->n[1];
+    const int64_t in_rows = a.in_rows < 0 ? ny : a.in_rows, out_rows = a.out_rows < 0 ? ny : a.out_rows;
+    if ((in_rows != ny || out_rows != ny) && a.dot_partial)
+        return fail(PD_ERR_INVALID, "row windows take no fused dot");
+    dim3 grid((unsigned)((nx + kTX2 - 1) / kTX2), (unsigned)((out_rows + TY - 1) / TY), (unsigned)a.batch);
+    const T *kd = sizeof(T) == 4 ? (const T *)g->d_kd32 : (const T *)g->d_kd64;
+    kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)nx, (int)ny, out_rows * nx, g->d_cons,
+                                      a.project ? 1 : 0, kd, (T)a.scale, make_pairs2<T, M>(g), a.dot_partial,
+                                      a.dot_out, a.retire, (int)a.in_row0, in_rows * nx, (int)a.out_row0,
+                                      (int)(a.out_row0 + out_rows));
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
 template <typename T>
 int run_t(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
+    if (a.pair_form) {
+        switch (g->M) {
+            case 1: return run_pair<T, 1>(g, a, s);
+            case 2: return run_pair<T, 2>(g, a, s);
+            case 3: return run_pair<T, 3>(g, a, s);
+            case 4: return run_pair<T, 4>(g, a, s);
+            case 5: return run_pair<T, 5>(g, a, s);
+            case 6: return run_pair<T, 6>(g, a, s);
+            case 7: return run_pair<T, 7>(g, a, s);
+            case 8: return run_pair<T, 8>(g, a, s);
+        }
+        return fail(PD_ERR_INVALID, "horizon M not compiled for 2D");
+    }
     switch (g->M) {
         case 1: return run<T, 1>(g, a, s);
         case 2: return run<T, 2>(g, a, s);

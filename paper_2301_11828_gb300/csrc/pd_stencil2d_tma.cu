@@ -323,13 +323,16 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
 // TMA pipeline, with the pair sums evaluated as differences (tile_eg for warps
 // whose outputs all have their whole horizon inside the grid, tile_diff with
 // out-of-grid terms dropped elsewhere), so that K u = -a with no diagonal term
-// to cancel against.  The coefficients carry -scale.  Two CTAs per SM up to
-// M = 4 (about 120 registers); one beyond, where the shared differences of the
-// interior form need up to 250 registers (measured faster than two CTAs with
-// spills, or the plain difference form).
+// to cancel against.  The coefficients carry -scale.  Tiles of 64 columns by
+// 8 GY rows (GY = 2, 4 or 8 warps' worth of rows; 64 x 64 the default at M <= 3,
+// measured 2 % faster than 64 x 32 there and slower at M = 4).  Two CTAs per SM
+// up to M = 4 with 64 x 32 or 64 x 16 tiles (about 120 registers); one with
+// 64 x 64 tiles (512 threads) and beyond M = 4, where the shared differences of
+// the interior form need up to 250 registers (measured faster than two CTAs
+// with spills, or the plain difference form).
 constexpr int kAccStages = 3;   // halo tiles in flight or in use per CTA
 template <int M, int GY>
-__global__ void __launch_bounds__(64 * GY, (M <= 4 ? 2 : 1))
+__global__ void __launch_bounds__(64 * GY, (M <= 4 && GY <= 4 ? 2 : 1))
 k_tbt2d_acc(const __grid_constant__ CUtensorMap map, float *__restrict__ out, int nx, int ny, int64_t N,
             int ybuf0, int ty0, int yend, int tiles_x, int tiles_y, FastDiv div_tx, FastDiv div_ty, int ntiles,
             const uint8_t *__restrict__ cons,
@@ -425,7 +428,11 @@ k_tbt2d_acc(const __grid_constant__ CUtensorMap map, float *__restrict__ out, in
         float *sx = sbase + 2 * PLANE * cur, *sy = sx + PLANE;
         bool pin = false, pout = false;
         if (project_in | project_out) {
-            const uint8_t tf = tflags ? __ldg(tflags + (y0 / kTYt) * tiles_x + x0 / kTXt) : 3;
+            // the flags are per 64 x 32 tile of the grid: a taller tile takes the union
+            uint8_t tf = tflags ? 0 : 3;
+            if (tflags)
+                for (int k = 0; k < (TYt + kTYt - 1) / kTYt && y0 + k * kTYt < ny; ++k)
+                    tf |= __ldg(tflags + (y0 / kTYt + k) * tiles_x + x0 / kTXt);
             pin = project_in && (tf & 2);
             pout = project_out && (tf & 1);
         }
@@ -622,6 +629,7 @@ int run_tbt2d_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     case m:                                                                                  \
         if (a.pair_form) return run<m, false>(g, a, s);                                      \
         if (m <= 4 && g->stencil_tile_rows == 16) return run<m, true, (m <= 4 ? 2 : kGY2)>(g, a, s); \
+        if (m <= 3 && g->stencil_tile_rows == 64) return run<m, true, (m <= 3 ? 8 : kGY2)>(g, a, s); \
         return run<m, true>(g, a, s);
     switch (g->M) {
         PD_TMA_CASE(1)

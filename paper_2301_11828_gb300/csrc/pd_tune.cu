@@ -20,7 +20,7 @@ namespace {
 
 struct Choice {
     int method = 0;        // PD_METHOD_STENCIL or PD_METHOD_FFT
-    int tile_rows = 32;    // FP32 2D stencil layout: tile height 32 or 16, 0 for the column walk
+    int tile_rows = 32;    // FP32 2D stencil layout: tile height 64, 32 or 16, 0 for the column walk
     double ms = 0.0;       // time per field of the chosen candidate
 };
 
@@ -39,7 +39,7 @@ std::string key_of(const pd_grid *g, int prec)
 }
 
 // The cache file: one JSON object of entries
-//   "<key>": {"method": "stencil"|"fft", "tile_rows": 32|16|0, "ms_per_field": t} (0: the column walk)
+//   "<key>": {"method": "stencil"|"fft", "tile_rows": 64|32|16|0, "ms_per_field": t} (0: the column walk)
 std::map<std::string, Choice> read_cache(const char *path)
 {
     std::map<std::string, Choice> out;
@@ -62,7 +62,7 @@ std::map<std::string, Choice> read_cache(const char *path)
         if (tr != std::string::npos) c.tile_rows = std::atoi(obj.c_str() + obj.find(':', tr) + 1);
         const size_t ms = obj.find("\"ms_per_field\"");
         if (ms != std::string::npos) c.ms = std::atof(obj.c_str() + obj.find(':', ms) + 1);
-        if (c.tile_rows != 16 && c.tile_rows != 0) c.tile_rows = 32;
+        if (c.tile_rows != 64 && c.tile_rows != 16 && c.tile_rows != 0) c.tile_rows = 32;
         out[key] = c;
         p = o1;
     }
@@ -140,12 +140,13 @@ extern "C" int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *s
             int rows;
             float best;
         };
-        Cand cand[4];
+        Cand cand[5];
         int nc = 0;
         cand[nc++] = {PD_METHOD_STENCIL, 32, 1e30f};
         MatvecArgs probe{};
         probe.u = u;
         if (prec == 0 && g->dim == 2 && g->M <= 4 && tma_stencil_eligible(g, probe, false)) {
+            if (g->M <= 3) cand[nc++] = {PD_METHOD_STENCIL, 64, 1e30f};
             cand[nc++] = {PD_METHOD_STENCIL, 16, 1e30f};
             if (walk_stencil_eligible(g, probe)) cand[nc++] = {PD_METHOD_STENCIL, 0, 1e30f};   // column walk
         }

@@ -458,3 +458,21 @@ def test_3d_products_on_smooth_fields(pd, offset):
         for meth in meths:
             out = g.matvec(ut, flags=meth).double().cpu().numpy()
             assert rel_l2(out, ref) <= tol, (str(dt), meth)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n,M", [((130, 97), 3), ((75, 66), 5), ((99, 53), 8)])
+def test_pair_form_plain_kernel(pd, dtype, n, M):
+    """PD_PAIR_FORM on the plain 2D kernel (FP64, and FP32 off the TMA path):
+    Kd_p u_p - sum c (u_p+o + u_p-o) with the clipped-distance diagonal, against
+    the oracle on random fields, with and without projection (the FP64 CG and
+    ADR iterations use this form)."""
+    h = 1.0 / 64
+    rng = np.random.default_rng(7 * M + n[0])
+    u_np = rng.uniform(-1, 1, (2, n[1], n[0]))
+    cons = syn.clamp_left(2, n, M)
+    g = pd.Grid(2, n, h, M, constrained=cons)
+    for proj in (0, pd.PD_PROJECT):
+        out, u_used = _run(pd, g, u_np, dtype, pd.PD_METHOD_STENCIL | pd.PD_PAIR_FORM | pd.PD_NO_TMA | proj)
+        ref = _oracle_K(2, n, h, M, u_used, cons=cons if proj else None)
+        assert rel_l2(out, ref) <= TOL[dtype]

@@ -28,14 +28,14 @@ def test_tuned_choice_is_the_fastest_and_is_cached(pd, tmp_path):
     t, hit = pd.pd_autotune_cached(g.handle, path)
     assert not hit
     info = pd.pd_get_info(g.handle)
-    assert info.stencil_tile_rows in (0, 16, 32)   # 0: the column walk
+    assert info.stencil_tile_rows in (0, 16, 32, 64)   # 0: the column walk
     for prec, (st, ff) in enumerate((("stencil_f32_ms", "fft_f32_ms"), ("stencil_f64_ms", "fft_f64_ms"))):
         assert t[st] > 0 and t[ff] > 0
         # FP32: the stencil (the FFT tiles miss the FP32 tolerance on smooth fields); FP64: the faster
         want = pd.PD_METHOD_FFT if (prec == 1 and t[ff] < t[st]) else pd.PD_METHOD_STENCIL
         assert info.auto_method[prec] == want
     entries = json.load(open(path))
-    assert len(entries) == 2 and all(e["tile_rows"] in (0, 16, 32) for e in entries.values())
+    assert len(entries) == 2 and all(e["tile_rows"] in (0, 16, 32, 64) for e in entries.values())
     # a second grid of the same geometry takes the recorded choice without measuring
     g2 = pd.Grid(2, w.n, w.h, w.M)
     t2, hit2 = pd.pd_autotune_cached(g2.handle, path)
@@ -51,23 +51,30 @@ def test_tuned_choice_is_the_fastest_and_is_cached(pd, tmp_path):
 
 
 @pytest.mark.parametrize("M", [2, 3, 4])
-def test_stencil_tile_height_changes_no_bit(pd, M):
-    """Both stencil tiles of the autotuner (64 x 32 and 64 x 16 outputs) give the
-    same bits: every output is formed by the same operations in either."""
+@pytest.mark.parametrize("patch", [False, True])
+def test_stencil_tile_height_changes_no_bit(pd, M, patch):
+    """The stencil tiles of the autotuner (64 x 64, 64 x 32 and 64 x 16 outputs)
+    give the same bits, with and without projection (a 64 x 64 tile takes the
+    union of the projection flags of its two 64 x 32 halves): every output is
+    formed by the same operations in each."""
     n = (200, 150)
     rng = np.random.default_rng(M)
     cons = syn.clamp_left(2, n, M)
+    if patch:   # constrained nodes only in the lower half of a 64-row tile (rows 40..50, 100..150)
+        cons = np.zeros_like(cons)
+        cons[:, 40:51, 70:90] = 1
+        cons[1, 100:151, 150:160] = 1
     g = pd.Grid(2, n, 1.0 / 200, M, constrained=cons)
     U = torch.tensor(rng.uniform(-1, 1, (3, 2, n[1], n[0])), dtype=torch.float32, device="cuda")
     outs = {}
-    path_rows = []
-    for rows in (32, 16):
+    for rows in (64, 32, 16):
         g.set_stencil_tile_rows(rows)
         assert pd.pd_get_info(g.handle).stencil_tile_rows == rows
         for proj in (0, pd.PD_PROJECT):
             outs[(rows, proj)] = g.matvec(U, flags=pd.PD_METHOD_STENCIL | proj)
     for proj in (0, pd.PD_PROJECT):
         assert torch.equal(outs[(32, proj)], outs[(16, proj)])
+        assert torch.equal(outs[(32, proj)], outs[(64, proj)])
         ref = oracle.stiffness(2, n, 1.0 / 200, M, oracle.alpha(2, 1.0, M / 200), U[1].double().cpu().numpy(),
                                cons=cons if proj else None)
         assert rel_l2(outs[(16, proj)][1].double().cpu().numpy(), ref) <= 2e-5
