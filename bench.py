@@ -527,7 +527,7 @@ def _extras(torch, pd, syn, dev):
     # measured arithmetic peaks (the denominators of the ALU-bound kernels)
     peaks = {"fp32_tflops": pd.pd_probe_fma_rate(pd.PD_F32) / 1e12, "fp64_tflops": pd.pd_probe_fma_rate(pd.PD_F64) / 1e12}
     out["alu_peaks_measured"] = {k: round(v, 2) for k, v in peaks.items()}
-    variants, verr, vfrac = {}, {}, {}
+    variants, verr, vfrac, vfrac32 = {}, {}, {}, {}
     for M in (3, 6):
         w = syn.large_plate(M)
         g = pd.Grid(2, w.n, w.h, w.M)
@@ -539,7 +539,7 @@ def _extras(torch, pd, syn, dev):
             ref0 = oracle.stiffness(2, w.n, w.h, w.M, al, U[0].double().cpu().numpy())
             for meth, mname in ((pd.PD_METHOD_STENCIL, "stencil"), (pd.PD_METHOD_STENCIL | pd.PD_PAIR_FORM, "stencil_pair"),
                                 (pd.PD_METHOD_STENCIL | pd.PD_NO_TMA, "stencil_plain"), (pd.PD_METHOD_FFT, "fft")):
-                if name == "f64" and mname in ("stencil_plain", "stencil_pair"):
+                if name == "f64" and mname == "stencil_plain":
                     continue
                 key = f"M{M}_{name}_{mname}"
                 try:
@@ -555,17 +555,23 @@ def _extras(torch, pd, syn, dev):
         npairs = oracle.offsets(2, M).shape[0] // 2
         gen = npairs - 2 * M
         f64_flops = (gen * 10 + 2 * M * 3 + 8) * w.N
-        if variants.get(f"M{M}_f64_stencil"):
-            vfrac[f"M{M}_f64_stencil"] = round(variants[f"M{M}_f64_stencil"] * 1e9 / 2 * (f64_flops / w.N)
-                                               / (peaks["fp64_tflops"] * 1e12), 3)
+        for key in (f"M{M}_f64_stencil", f"M{M}_f64_stencil_pair"):
+            if variants.get(key):
+                vfrac[key] = round(variants[key] * 1e9 / 2 * (f64_flops / w.N) / (peaks["fp64_tflops"] * 1e12), 3)
+        # FP32 stencils against the measured FP32 FMA rate with the same algorithmic FLOP count:
+        # beyond M = 3 the FP32 product is bound by the FMA pipe, not by HBM
+        for key in (f"M{M}_f32_stencil", f"M{M}_f32_stencil_pair"):
+            if variants.get(key):
+                vfrac32[key] = round(variants[key] * 1e9 / 2 * (f64_flops / w.N) / (peaks["fp32_tflops"] * 1e12), 3)
         g.close()
     out["variants_gdofs"] = variants
     out["variants_rel_l2_vs_oracle"] = {k: float(f"{v:.3e}") for k, v in verr.items()}
     out["variants_fp64_frac_of_measured_fp64_peak"] = vfrac
+    out["variants_fp32_frac_of_measured_fp32_peak"] = vfrac32
     out["cufft_comparison"] = _cufft_comparison(torch, pd, syn, dev, oracle)
     # the autotuner's choice (method; FP32 2D stencil tile height) per horizon and precision on
     # the 1024^2 plate and the 128^3 cube, with the time of each candidate; "fixed" is the
-    # untuned default (the 64 x 32 stencil tile)
+    # 64 x 32 stencil tile
     tune = {}
     for key, w in (("plate1024_M3", syn.large_plate(3)), ("plate1024_M4", syn.large_plate(4)),
                    ("plate1024_M6", syn.large_plate(6)), ("cube128_M3", syn.cube(128, 3))):

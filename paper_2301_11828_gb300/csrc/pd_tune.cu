@@ -130,11 +130,12 @@ extern "C" int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *s
     PD_CUDA(cudaEventCreate(&e0));
     PD_CUDA(cudaEventCreate(&e1));
     const bool fft_ok = !g->has_E;
-    const int saved_rows = g->stencil_tile_rows;
     int rc = PD_OK;
     for (int prec = 0; prec < 2 && rc == PD_OK; ++prec) {
         const uint32_t dt = prec ? PD_F64 : PD_F32;
         if (!(flags & dt)) continue;
+        // the layout before this precision's pass (the FP64 pass keeps the FP32 choice)
+        const int saved_rows = g->stencil_tile_rows;
         struct Cand {
             uint32_t method;
             int rows;

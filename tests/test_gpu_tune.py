@@ -101,3 +101,14 @@ def test_auto_method_meets_tolerance_on_smooth_fields(pd, n, M):
                      (pd.PD_METHOD_AUTO, pd.PD_METHOD_STENCIL, pd.PD_METHOD_FFT)):
             out = g.matvec(ut, flags=meth).double().cpu().numpy()
             assert rel_l2(out, ref) <= tol, (str(dt), meth)
+
+
+def test_tuned_layout_is_one_of_the_horizons_candidates(pd):
+    """The FP64 pass of the autotuner keeps the FP32 stencil layout the FP32 pass
+    chose (64-row tiles are a candidate at M <= 3 only, the walk at M <= 3)."""
+    for M, allowed in ((3, (0, 16, 32, 64)), (4, (16, 32))):
+        w = syn.plate_static(256, M, tag=3, u_amp=1.0)
+        g = pd.Grid(2, w.n, w.h, w.M)
+        g.autotune()
+        assert pd.pd_get_info(g.handle).stencil_tile_rows in allowed
+        g.close()
