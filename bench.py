@@ -768,14 +768,15 @@ def _extras(torch, pd, syn, dev):
     return out
 
 
-CASES = ("fft2d", "stencil2d_f64", "walk2d", "stencil3d", "fft3d", "crack", "cg", "adr", "adr_mixed", "sc", "kw3d")
+CASES = ("fft2d", "fft2d_f64", "stencil2d_f64", "walk2d", "stencil3d", "fft3d", "crack", "cg", "adr", "adr_mixed", "sc", "kw3d")
 
 
 def run_case(args):
     """One secondary workload in a loop (for ncu launch lists and captures); prints one JSON line.
 
     fft2d: K u, 1024^2 plate, M=3, FP32 FFT tiles, 8 fields.  stencil2d_f64: the same with the FP64
-    stencil, 4 fields.  walk2d: the same with the FP32 column walk, 16 fields.  stencil3d / fft3d: K u on the 128^3 cube, M=3, FP32.  crack: one Verlet step
+    stencil, 4 fields.  walk2d: the same with the FP32 column walk, 16 fields.  fft2d_f64: FP64 FFT
+    tiles at M=6, 2 fields.  stencil3d / fft3d: K u on the 128^3 cube, M=3, FP32.  crack: one Verlet step
     with bond breaking on the pre-notched 512^2 plate.  cg: 64 iterations of the mixed CG on the
     1024^2 plate (graph-replayed inner loop).  adr / adr_mixed: 64 ADR iterations (Algorithm 1, FP64 /
     mixed) on that plate.  sc: K u with the surface correction, 1024^2, FP32, 8 fields.  kw3d: one Verlet
@@ -788,10 +789,11 @@ def run_case(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     case = args.case
-    if case in ("fft2d", "stencil2d_f64", "walk2d"):
-        w = syn.large_plate(3)
+    if case in ("fft2d", "fft2d_f64", "stencil2d_f64", "walk2d"):
+        w = syn.large_plate(6 if case == "fft2d_f64" else 3)
         g = pd.Grid(2, w.n, w.h, w.M)
         dt, B, meth = {"fft2d": (torch.float32, 8, pd.PD_METHOD_FFT),
+                       "fft2d_f64": (torch.float64, 2, pd.PD_METHOD_FFT),
                        "stencil2d_f64": (torch.float64, 4, pd.PD_METHOD_STENCIL),
                        "walk2d": (torch.float32, 16, pd.PD_METHOD_STENCIL)}[case]
         if case == "walk2d":
