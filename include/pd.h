@@ -62,7 +62,7 @@ typedef enum {
 #define PD_METHOD_FFT     0x20u  /* TBT part by FFT with the symbol product fused (Algorithms 3/4) */
 #define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
-#define PD_NO_TMA         0x400u /* FP32 2D stencil: use the plain kernel, not the TMA-fed one */
+#define PD_NO_TMA         0x400u /* FP32 2D stencil and FFT tiles: use the plain-load kernels, not the TMA-fed ones */
 #define PD_ACCURATE       0x800u /* accepted for compatibility: every FP32 stencil sums differences of
                                     nearby values by default (see PD_PAIR_FORM) */
 #define PD_PAIR_FORM      0x1000u /* stencils: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o)

@@ -28,14 +28,17 @@
 //   4. inverse FFTs along y then x;
 //   5. epilogue: K u = Re/Im(w) - (Ctot - Kd_p) u_p on nodes near a face (the
 //      D^e term of Eq. tea:sc), projection, scale, optional fused dot.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
 
 #include "pd_internal.cuh"
 #include "pd_reduce.cuh"
+#include "pd_tma2d.cuh"
 
 namespace pd {
 
@@ -152,7 +155,7 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
     using V = typename C2<T>::t;
     constexpr int TO = P - 2 * M;   // outputs per tile edge
     constexpr int QH = P / 2 + 1;   // quarter symbol edge
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     V *Z = reinterpret_cast<V *>(smem_raw);   // [P][PS]
     T *sq = reinterpret_cast<T *>(Z + P * PS);   // quarter symbol [3][QH][QH]
     for (int t = threadIdx.x; t < 3 * QH * QH; t += kT) sq[t] = __ldg(sym + t);
@@ -272,6 +275,150 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
     }
 }
 
+// FP32 tiles fed by TMA (products without projection or a fused dot): persistent
+// CTAs, two per SM.  The window of the next tile is copied by the TMA engine
+// into a staging box while the current tile is transformed, so the plain
+// global loads of k_fft_tile -- the stall that bounds it -- leave the tile's
+// critical path.  The window's x origin is rounded down to a 16-byte boundary
+// (TMA rule) and the box is 4 columns wider.  The staging box holds zeros
+// outside the grid; z = u - c is formed only for in-grid nodes (the embedding
+// pads with zeros, not with -c).  Same arithmetic per tile as k_fft_tile.
+constexpr int kFBX = P + 4;   // staged columns (16-byte aligned start)
+template <int M>
+__global__ void __launch_bounds__(kT, 2)
+k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out, int nx, int ny, int64_t N,
+               int tiles_x, int tiles_y, int ntiles, const float *__restrict__ sym, const float *__restrict__ kd,
+               float ctxx, float ctxy, float ctyy, float scale, const float *__restrict__ u, int *err)
+{
+    using V = float2;
+    using namespace tma2d;
+    constexpr int TO = P - 2 * M;
+    constexpr int QH = P / 2 + 1;
+    constexpr uint32_t kBytes = 2u * kFBX * P * sizeof(float);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *const stg = reinterpret_cast<float *>(smem_raw);                  // [2][P][kFBX] staged window
+    V *const Z = reinterpret_cast<V *>(smem_raw + kBytes);                    // [P][PS]
+    float *const sq = reinterpret_cast<float *>(Z + P * PS);                  // quarter symbol [3][QH][QH]
+    __shared__ __align__(8) uint64_t full;
+    __shared__ int s_abort;
+    for (int t = threadIdx.x; t < 3 * QH * QH; t += kT) sq[t] = __ldg(sym + t);
+    if (threadIdx.x == 0) {
+        mbar_init(&full, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto coords = [&](int t, int &x0, int &y0, int &b) {
+        const int per = tiles_x * tiles_y;
+        b = t / per;
+        const int r = t - b * per;
+        y0 = (r / tiles_x) * TO - M;
+        x0 = (r % tiles_x) * TO - M;
+    };
+    auto issue = [&](int t) {
+        int x0, y0, b;
+        coords(t, x0, y0, b);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&full, kBytes);
+        tma_load_3d(stg, &map, x0 & ~3, y0, 2 * b, &full);
+    };
+    int it = 0;
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        int x0, y0, b;
+        coords(t, x0, y0, b);
+        const bool ok = mbar_wait(&full, it & 1);
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                s_abort = 1;
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const int d = x0 - (x0 & ~3);   // column of the window's origin in the staged box
+        const float *sx = stg, *sy = stg + P * kFBX;
+        // the tile's reference value: the input at its first output node (always in the grid)
+        const float cx = sx[M * kFBX + M + d], cy = sy[M * kFBX + M + d];
+        for (int e = threadIdx.x; e < P * P; e += kT) {
+            const int a = e % P, r = e / P;
+            const int gx = x0 + a, gy = y0 + r;
+            V z = {0.f, 0.f};
+            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+                z.x = sx[r * kFBX + a + d] - cx;
+                z.y = sy[r * kFBX + a + d] - cy;
+            }
+            Z[r * PS + a] = z;
+        }
+        __syncthreads();   // the staged box is free: the next tile's window is copied meanwhile
+        if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+
+        fft64_lines<false, float>(Z, 1, PS);
+        fft64_lines<false, float>(Z, PS, 1);
+        for (int e = threadIdx.x; e < P * P; e += kT) {
+            const int kx = e % P, ky = e / P;
+            const int mx = (P - kx) & (P - 1), my = (P - ky) & (P - 1);
+            const int t2 = my * P + mx;
+            if (t2 < e) continue;
+            const V zk = Z[ky * PS + kx], zm0 = Z[my * PS + mx];
+            const V zm = {zm0.x, -zm0.y};
+            const V ux = {0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y)};
+            const V uy = {0.5f * (zk.y - zm.y), -0.5f * (zk.x - zm.x)};
+            const int qx = kx <= P / 2 ? kx : P - kx, qy = ky <= P / 2 ? ky : P - ky;
+            const int qi = qy * QH + qx;
+            const float sgn = ((kx > P / 2) != (ky > P / 2)) ? -1.f : 1.f;
+            const float sxx = sq[qi], sxy = sgn * sq[QH * QH + qi], syy = sq[2 * QH * QH + qi];
+            const V hx = {sxx * ux.x + sxy * uy.x, sxx * ux.y + sxy * uy.y};
+            const V hy = {sxy * ux.x + syy * uy.x, sxy * ux.y + syy * uy.y};
+            Z[ky * PS + kx] = {hx.x - hy.y, hx.y + hy.x};
+            if (t2 != e) Z[my * PS + mx] = {hx.x + hy.y, hy.x - hx.y};
+        }
+        __syncthreads();
+        fft64_lines<true, float>(Z, PS, 1);
+        fft64_lines<true, float>(Z, 1, PS);
+
+        const float *ub = u + (int64_t)b * 2 * N;
+        float *ob = out + (int64_t)b * 2 * N;
+        for (int e = threadIdx.x; e < TO * TO; e += kT) {
+            const int a = M + e % TO, r = M + e / TO;
+            const int gx = x0 + a, gy = y0 + r;
+            if (gx >= nx || gy >= ny) continue;
+            const int64_t p = (int64_t)gy * nx + gx;
+            const V w = Z[r * PS + a];
+            float fx = w.x, fy = w.y;
+            const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
+            if (a0 != M || a1 != M || b0 != M || b1 != M) {   // the D^e term on the shifted field
+                const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
+                const float dxx = ctxx - __ldg(kd + 3 * cls), dxy = ctxy - __ldg(kd + 3 * cls + 1),
+                            dyy = ctyy - __ldg(kd + 3 * cls + 2);
+                const float zx = __ldg(ub + p) - cx, zy = __ldg(ub + N + p) - cy;
+                fx -= dxx * zx + dxy * zy;
+                fy -= dxy * zx + dyy * zy;
+            }
+            ob[p] = fx * scale;
+            ob[N + p] = fy * scale;
+        }
+        __syncthreads();   // Z is free for the next tile
+    }
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0) mbar_wait(&full, it & 1);   // let a copy still in flight land
+}
+
+// Tensor map over `batch` fields of two FP32 planes [2*batch][ny][nx] with the
+// staged-window box of k_fft_tile_tma; false if the driver rejects it.
+bool fft_map(CUtensorMap *map, const void *base, int nx, int ny, int64_t batch)
+{
+    tma2d::EncodeTiledFn enc = tma2d::encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)(2 * batch)};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kFBX, (cuuint32_t)P, 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 std::once_flag g_tw_once[64];
 int g_tw_status[64];
 
@@ -294,9 +441,49 @@ int upload_twiddles()
     return g_tw_status[dev] == 1 ? PD_OK : fail(PD_ERR_CUDA, "twiddle upload failed");
 }
 
+template <int M>
+int run_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
+{
+    constexpr int TO = P - 2 * M;
+    const int nx = (int)g->n[0], ny = (int)g->n[1];
+    CUtensorMap map;
+    if (!fft_map(&map, a.u, nx, ny, a.batch)) return fail(PD_ERR_CUDA, "tensor map encode failed");
+    const size_t smem = 2 * sizeof(float) * kFBX * P + sizeof(float2) * P * PS + sizeof(float) * 3 * (P / 2 + 1) * (P / 2 + 1);
+    auto kern = k_fft_tile_tma<M>;
+    static int attr_done[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        attr_done[dev] = 1;
+    }
+    const int tiles_x = (nx + TO - 1) / TO, tiles_y = (ny + TO - 1) / TO;
+    const int64_t nt = (int64_t)tiles_x * tiles_y * a.batch;
+    if (nt > (1ll << 30)) return fail(PD_ERR_INVALID, "too many tiles");
+    int occ = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kT, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (occ < 1) occ = 1;
+    const int blocks = (int)std::min<int64_t>(nt, (int64_t)occ * sms);
+    double ct[3] = {0, 0, 0};
+    for (int k = 0; k < g->nnb; ++k)
+        for (int c = 0; c < 3; ++c) ct[c] += g->coef1[3 * k + c] * g->E;
+    kern<<<blocks, kT, smem, s>>>(map, (float *)a.out, nx, ny, g->N, tiles_x, tiles_y, (int)nt, g->d_sym32, g->d_kd32,
+                                  (float)ct[0], (float)ct[1], (float)ct[2], (float)a.scale, (const float *)a.u,
+                                  g->d_err);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+}
+
 template <typename T, int M>
 int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (!a.project && !a.dot_partial && !a.no_tma && !g->no_tma && g->n[0] % 4 == 0 &&
+            ((uintptr_t)a.u & 15) == 0 && tma2d::encode_fn() != nullptr)
+            return run_tma<M>(g, a, s);
+    }
     constexpr int TO = P - 2 * M;
     const size_t smem = sizeof(typename C2<T>::t) * P * PS + sizeof(T) * 3 * (P / 2 + 1) * (P / 2 + 1);
     auto kern = k_fft_tile<T, M>;

@@ -144,3 +144,25 @@ def test_cufft_comparison_route_matches_oracle(dim, n, M):
         for b in range(2):
             ref = oracle.stiffness(dim, n, h, M, al, ut[b].double().cpu().numpy())
             assert rel_l2(out[b], ref) <= tol
+
+
+@pytest.mark.parametrize("n,M", [((132, 97), 3), ((100, 77), 4), ((4, 5), 3), ((64, 64), 2), ((260, 131), 6),
+                                 ((120, 58), 1), ((1024, 40), 8)])
+def test_fft_tma_tiles_match_oracle_and_plain_tiles(pd, n, M):
+    """FP32 FFT tiles fed by TMA (row length a multiple of 4 floats, no projection,
+    no fused dot): against the oracle, against the plain-load tiles (PD_NO_TMA)
+    to FP32 rounding, and a batch against single fields bit for bit."""
+    h = 1.0 / 64
+    rng = np.random.default_rng(3 * M + n[0])
+    U = torch.tensor(rng.uniform(-1, 1, (3, 2, n[1], n[0])), dtype=torch.float32, device="cuda")
+    g = pd.Grid(2, n, h, M, E=0.7)
+    tma = g.matvec(U, flags=pd.PD_METHOD_FFT)
+    plain = g.matvec(U, flags=pd.PD_METHOD_FFT | pd.PD_NO_TMA)
+    one = g.matvec(U[1].contiguous(), flags=pd.PD_METHOD_FFT)
+    torch.cuda.synchronize()
+    assert torch.equal(one, tma[1])
+    for b in range(3):
+        un = U[b].double().cpu().numpy()
+        ref = _K(2, n, h, M, un, E=0.7)
+        assert rel_l2(tma[b].double().cpu().numpy(), ref) <= 2e-5
+        assert rel_l2(tma[b].double().cpu().numpy(), plain[b].double().cpu().numpy()) <= 1e-6
