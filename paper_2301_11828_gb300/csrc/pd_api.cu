@@ -132,6 +132,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_sym3_32);
     cudaFree(g->d_ctot64);
     cudaFree(g->d_ctot32);
+    cudaFree(g->d_kt32);
     cudaFree(g->d_off);
     cudaFree(g->d_brk_thr);
     cudaFree(g->d_coef);

@@ -13,11 +13,13 @@
 //
 // Per tile:
 //   1. load z = u_x + i u_y - c (zero outside the grid, projected if asked),
-//      with c the value at one in-grid node of the window: K maps a constant
-//      field to zero on every row (the edge rows included), so K(u - c) = K u,
-//      and the transforms then round values of the size of u's variation over
-//      the tile instead of u's own (a field with a large constant part would
-//      otherwise carry that part's rounding into every output);
+//      with c the value at one in-grid node of the window (FP64) or the tile's
+//      least-squares plane (FP32, see tile_plane): K maps a constant field to
+//      zero on every row (the edge rows included) and a plane to zero at every
+//      full-horizon node, so K u = K(u - c), or K(u - L) + K L with K L from a
+//      first-moment table at the edge nodes, and the transforms then round
+//      values of the size of u's variation (FP64) or curvature (FP32) over the
+//      tile instead of u's own;
 //   2. 64-point FFTs along x, then along y (each as 8 x 8, in two register
 //      passes with the twiddles W64^(n2 k1) between them);
 //   3. for each frequency pair (k, -k): unpack U_x, U_y from Z(k), Z(-k)
@@ -146,11 +148,116 @@ __device__ __forceinline__ void fft64_lines(typename C2<T>::t *Z, int es, int ls
     __syncthreads();
 }
 
+// The tile's reference plane.  Subtracting a constant leaves the FP32
+// transforms rounding values of the size of u's variation over the tile, which
+// on a smooth field is its gradient times the tile width; subtracting the
+// least-squares plane of the tile leaves its curvature part instead.  K maps a
+// plane to zero at every node with a full horizon, and at a node near a face to
+// -sum_b (Tx_ab gx_b + Ty_ab gy_b), Tx_ab = sum of c_ab(o) o_x over the in-grid
+// offsets (and Ty with o_y): the first-moment table of the node's edge class.
+// The plane is quantised so that its value at every window node is exact in
+// FP32: L = q (L0 + Gx (a - ar) + Gy (r - rr)) with q a power of two and
+// integers |L0| + 64 (|Gx| + |Gy|) < 2^24 -- the transforms then see exactly
+// u - L, and K u = K (u - L) + K L holds to rounding.
+struct TilePlane {
+    int l0[2], gx[2], gy[2];
+    float q[2];
+    int ar, rr;
+};
+
+// Least-squares plane of both components over an 8 x 8 sample of the window's
+// in-grid rectangle [ax, bx) x [ay, by) (fetch(a, r, vx, vy) reads a node): any
+// plane serves, the fit only has to follow the field closely.  Warp 0 takes the
+// samples (two per lane), and every lane of it forms the same plane from the
+// butterfly sums; lane 0 publishes it.  The caller's next block barrier makes
+// *pl visible to every thread.
+template <typename F>
+__device__ __forceinline__ void tile_plane(F fetch, int ax, int bx, int ay, int by, TilePlane *pl)
+{
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const int wx = bx - ax, wy = by - ay;
+    // sample columns ax + (i (wx - 1)) / 7 and rows likewise, their means and spreads
+    float mx = 0.f, my = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        mx += (float)(ax + (i * (wx - 1)) / 7);
+        my += (float)(ay + (i * (wy - 1)) / 7);
+    }
+    mx *= 0.125f;
+    my *= 0.125f;
+    float sxx = 0.f, syy = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float dx = (float)(ax + (i * (wx - 1)) / 7) - mx, dy = (float)(ay + (i * (wy - 1)) / 7) - my;
+        sxx = fmaf(dx, dx, sxx);
+        syy = fmaf(dy, dy, syy);
+    }
+    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane & 7, j = (lane >> 3) + 4 * h;
+        const int a = ax + (i * (wx - 1)) / 7, r = ay + (j * (wy - 1)) / 7;
+        float vx, vy;
+        fetch(a, r, vx, vy);
+        const float dx = (float)a - mx, dy = (float)r - my;
+        s[0] += vx;
+        s[1] = fmaf(vx, dx, s[1]);
+        s[2] = fmaf(vx, dy, s[2]);
+        s[3] += vy;
+        s[4] = fmaf(vy, dx, s[4]);
+        s[5] = fmaf(vy, dy, s[5]);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    const float ix = sxx > 0.f ? 0.125f / sxx : 0.f, iy = syy > 0.f ? 0.125f / syy : 0.f;
+    const int ar = ax + (wx - 1) / 2, rr = ay + (wy - 1) / 2;
+    int l0[2], gxi[2], gyi[2];
+    float q[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float gx = s[3 * c + 1] * ix, gy = s[3 * c + 2] * iy;
+        const float l = s[3 * c] * (1.f / 64.f) + gx * ((float)ar - mx) + gy * ((float)rr - my);
+        const float bound = fabsf(l) + 64.f * (fabsf(gx) + fabsf(gy));
+        l0[c] = gxi[c] = gyi[c] = 0;
+        q[c] = 0.f;
+        // q = 2^(k - 23) with bound < 2^k (from the exponent field), and 1/q exactly
+        const int eb = (__float_as_int(bound) >> 23) & 0xff;   // biased exponent: bound < 2^(eb - 126)
+        if (bound > 1e-30f && eb < 254 && eb > 30) {
+            q[c] = __int_as_float((eb - 126 - 23 + 127) << 23);
+            const float iq = __int_as_float((127 - (eb - 126 - 23)) << 23);
+            l0[c] = __float2int_rn(l * iq);
+            gxi[c] = __float2int_rn(gx * iq);
+            gyi[c] = __float2int_rn(gy * iq);
+        }
+    }
+    if (lane == 0) {
+        pl->ar = ar;
+        pl->rr = rr;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            pl->l0[c] = l0[c];
+            pl->gx[c] = gxi[c];
+            pl->gy[c] = gyi[c];
+            pl->q[c] = q[c];
+        }
+    }
+}
+
+// The plane's value at window node (a, r), component c: exact in FP32.
+__device__ __forceinline__ float plane_at(const TilePlane &pl, int c, int a, int r)
+{
+    return pl.q[c] * __int2float_rn(pl.l0[c] + pl.gx[c] * (a - pl.ar) + pl.gy[c] * (r - pl.rr));
+}
+
 template <typename T, int M>
 __global__ void __launch_bounds__(kT)
 k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
            const uint8_t *__restrict__ cons, int project, const T *__restrict__ sym, const T *__restrict__ kd,
-           T ctxx, T ctxy, T ctyy, T scale, double *dot_partial, double *dot_out, unsigned int *retire)
+           const float *__restrict__ kt, T ctxx, T ctxy, T ctyy, T scale, double *dot_partial, double *dot_out,
+           unsigned int *retire)
 {
     using V = typename C2<T>::t;
     constexpr int TO = P - 2 * M;   // outputs per tile edge
@@ -177,20 +284,38 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
         }
     }
 
+    // FP32: the tile's reference plane (tile_plane) instead of the constant
+    constexpr bool PLANE = sizeof(T) == 4;
+    __shared__ TilePlane s_pl;
+    const int ax = max(0, -x0), bx = min(P, nx - x0), ay = max(0, -y0), by = min(P, ny - y0);
+    auto fetch = [&](int a, int r, T &vx, T &vy) {
+        const int64_t p = (int64_t)(y0 + r) * nx + (x0 + a);
+        vx = __ldg(ub + p);
+        vy = __ldg(ub + N + p);
+        if (project) {
+            const uint8_t m = __ldg(cons + p);
+            if (m & 1) vx = T(0);
+            if (m & 2) vy = T(0);
+        }
+    };
+    if constexpr (PLANE) {
+        tile_plane(fetch, ax, bx, ay, by, &s_pl);
+        __syncthreads();
+    }
+    TilePlane pl{};
+    if constexpr (PLANE) pl = s_pl;
+    auto ref = [&](int c, int a, int r) -> T {
+        if constexpr (PLANE) return plane_at(pl, c, a, r);
+        return c == 0 ? cx : cy;
+    };
     for (int t = threadIdx.x; t < P * P; t += kT) {
         const int a = t % P, r = t / P;
-        const int gx = x0 + a, gy = y0 + r;
         V z = {T(0), T(0)};
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-            const int64_t p = (int64_t)gy * nx + gx;
-            T vx = __ldg(ub + p), vy = __ldg(ub + N + p);
-            if (project) {
-                const uint8_t m = __ldg(cons + p);
-                if (m & 1) vx = T(0);
-                if (m & 2) vy = T(0);
-            }
-            z.x = vx - cx;
-            z.y = vy - cy;
+        if (a >= ax && a < bx && r >= ay && r < by) {
+            T vx, vy;
+            fetch(a, r, vx, vy);
+            z.x = vx - ref(0, a, r);
+            z.y = vy - ref(1, a, r);
         }
         Z[r * PS + a] = z;
     }
@@ -246,9 +371,16 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
                 const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
                 const T dxx = ctxx - __ldg(kd + 3 * cls), dxy = ctxy - __ldg(kd + 3 * cls + 1),
                         dyy = ctyy - __ldg(kd + 3 * cls + 2);
-                const T zx = upx - cx, zy = upy - cy;
+                const T zx = upx - ref(0, a, r), zy = upy - ref(1, a, r);
                 fx -= dxx * zx + dxy * zy;
                 fy -= dxy * zx + dyy * zy;
+                if constexpr (PLANE) {   // K of the plane (zero at full-horizon nodes)
+                    const float *t6 = kt + 6 * cls;
+                    const float gxx = pl.q[0] * (float)pl.gx[0], gyx = pl.q[0] * (float)pl.gy[0];
+                    const float gxy = pl.q[1] * (float)pl.gx[1], gyy = pl.q[1] * (float)pl.gy[1];
+                    fx -= __ldg(t6) * gxx + __ldg(t6 + 3) * gyx + __ldg(t6 + 1) * gxy + __ldg(t6 + 4) * gyy;
+                    fy -= __ldg(t6 + 1) * gxx + __ldg(t6 + 4) * gyx + __ldg(t6 + 2) * gxy + __ldg(t6 + 5) * gyy;
+                }
             }
             if (m & 1) fx = T(0);
             if (m & 2) fy = T(0);
@@ -288,7 +420,8 @@ template <int M>
 __global__ void __launch_bounds__(kT, 2)
 k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out, int nx, int ny, int64_t N,
                int tiles_x, int tiles_y, int ntiles, const float *__restrict__ sym, const float *__restrict__ kd,
-               float ctxx, float ctxy, float ctyy, float scale, const float *__restrict__ u, int *err)
+               const float *__restrict__ kt, float ctxx, float ctxy, float ctyy, float scale,
+               const float *__restrict__ u, int *err)
 {
     using V = float2;
     using namespace tma2d;
@@ -301,6 +434,7 @@ k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out,
     float *const sq = reinterpret_cast<float *>(Z + P * PS);                  // quarter symbol [3][QH][QH]
     __shared__ __align__(8) uint64_t full;
     __shared__ int s_abort;
+    __shared__ TilePlane s_pl;
     for (int t = threadIdx.x; t < 3 * QH * QH; t += kT) sq[t] = __ldg(sym + t);
     if (threadIdx.x == 0) {
         mbar_init(&full, 1);
@@ -338,17 +472,31 @@ k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out,
         if (s_abort) break;
         const int d = x0 - (x0 & ~3);   // column of the window's origin in the staged box
         const float *sx = stg, *sy = stg + P * kFBX;
-        // the tile's reference value: the input at its first output node (always in the grid)
-        const float cx = sx[M * kFBX + M + d], cy = sy[M * kFBX + M + d];
-        for (int e = threadIdx.x; e < P * P; e += kT) {
-            const int a = e % P, r = e / P;
-            const int gx = x0 + a, gy = y0 + r;
-            V z = {0.f, 0.f};
-            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-                z.x = sx[r * kFBX + a + d] - cx;
-                z.y = sy[r * kFBX + a + d] - cy;
+        // the window's in-grid rectangle and the tile's reference plane over it
+        const int ax = max(0, -x0), bx = min(P, nx - x0), ay = max(0, -y0), by = min(P, ny - y0);
+        tile_plane([&](int a, int r, float &vx, float &vy) {
+                       vx = sx[r * kFBX + a + d];
+                       vy = sy[r * kFBX + a + d];
+                   }, ax, bx, ay, by, &s_pl);
+        __syncthreads();
+        const TilePlane pl = s_pl;
+        {   // a thread keeps its column (kT is a multiple of P) and steps rows by kT / P: the
+            // plane's integers advance by a constant (exactly as plane_at would form them)
+            static_assert(kT % P == 0, "one column per thread");
+            constexpr int RS = kT / P;
+            const int a = threadIdx.x % P, r0 = threadIdx.x / P;
+            int lx = pl.l0[0] + pl.gx[0] * (a - pl.ar) + pl.gy[0] * (r0 - pl.rr);
+            int ly = pl.l0[1] + pl.gx[1] * (a - pl.ar) + pl.gy[1] * (r0 - pl.rr);
+            const int sx_ = RS * pl.gy[0], sy_ = RS * pl.gy[1];
+            const bool ain = a >= ax && a < bx;
+            for (int r = r0; r < P; r += RS, lx += sx_, ly += sy_) {
+                V z = {0.f, 0.f};
+                if (ain && r >= ay && r < by) {
+                    z.x = sx[r * kFBX + a + d] - pl.q[0] * __int2float_rn(lx);
+                    z.y = sy[r * kFBX + a + d] - pl.q[1] * __int2float_rn(ly);
+                }
+                Z[r * PS + a] = z;
             }
-            Z[r * PS + a] = z;
         }
         __syncthreads();   // the staged box is free: the next tile's window is copied meanwhile
         if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
@@ -387,13 +535,19 @@ k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out,
             const V w = Z[r * PS + a];
             float fx = w.x, fy = w.y;
             const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
-            if (a0 != M || a1 != M || b0 != M || b1 != M) {   // the D^e term on the shifted field
+            if (a0 != M || a1 != M || b0 != M || b1 != M) {
+                // the D^e term on the shifted field, and K of the plane (zero at full-horizon nodes)
                 const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
                 const float dxx = ctxx - __ldg(kd + 3 * cls), dxy = ctxy - __ldg(kd + 3 * cls + 1),
                             dyy = ctyy - __ldg(kd + 3 * cls + 2);
-                const float zx = __ldg(ub + p) - cx, zy = __ldg(ub + N + p) - cy;
+                const float zx = __ldg(ub + p) - plane_at(pl, 0, a, r), zy = __ldg(ub + N + p) - plane_at(pl, 1, a, r);
                 fx -= dxx * zx + dxy * zy;
                 fy -= dxy * zx + dyy * zy;
+                const float *t6 = kt + 6 * cls;   // Tx_xx, Tx_xy, Tx_yy, Ty_xx, Ty_xy, Ty_yy
+                const float gxx = pl.q[0] * (float)pl.gx[0], gyx = pl.q[0] * (float)pl.gy[0];
+                const float gxy = pl.q[1] * (float)pl.gx[1], gyy = pl.q[1] * (float)pl.gy[1];
+                fx -= __ldg(t6) * gxx + __ldg(t6 + 3) * gyx + __ldg(t6 + 1) * gxy + __ldg(t6 + 4) * gyy;
+                fy -= __ldg(t6 + 1) * gxx + __ldg(t6 + 4) * gyx + __ldg(t6 + 2) * gxy + __ldg(t6 + 5) * gyy;
             }
             ob[p] = fx * scale;
             ob[N + p] = fy * scale;
@@ -470,8 +624,8 @@ int run_tma(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     for (int k = 0; k < g->nnb; ++k)
         for (int c = 0; c < 3; ++c) ct[c] += g->coef1[3 * k + c] * g->E;
     kern<<<blocks, kT, smem, s>>>(map, (float *)a.out, nx, ny, g->N, tiles_x, tiles_y, (int)nt, g->d_sym32, g->d_kd32,
-                                  (float)ct[0], (float)ct[1], (float)ct[2], (float)a.scale, (const float *)a.u,
-                                  g->d_err);
+                                  g->d_kt32, (float)ct[0], (float)ct[1], (float)ct[2], (float)a.scale,
+                                  (const float *)a.u, g->d_err);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -497,8 +651,8 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     for (int k = 0; k < g->nnb; ++k)
         for (int c = 0; c < 3; ++c) ct[c] += g->coef1[3 * k + c] * g->E;
     kern<<<grid, kT, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], g->N, g->d_cons,
-                                a.project ? 1 : 0, sym, kd, (T)ct[0], (T)ct[1], (T)ct[2], (T)a.scale, a.dot_partial,
-                                a.dot_out, a.retire);
+                                a.project ? 1 : 0, sym, kd, g->d_kt32, (T)ct[0], (T)ct[1], (T)ct[2], (T)a.scale,
+                                a.dot_partial, a.dot_out, a.retire);
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -545,6 +699,25 @@ int fft_prepare(pd_grid *g)
             }
             for (int c = 0; c < 3; ++c) S[(size_t)c * QH * QH + ky * QH + kx] = acc[c] / ((double)P * P);
         }
+    // first moments per edge class (clipped face distances a0, a1, b0, b1 in [0, M]):
+    // Tx_ab = sum over in-grid offsets of c_ab(o) o_x, Ty_ab alike with o_y
+    const int B = g->M + 1;
+    std::vector<float> kt((size_t)B * B * B * B * 6, 0.f);
+    for (int e = 0; e < B * B * B * B; ++e) {
+        const int d0 = e / (B * B * B), d1 = (e / (B * B)) % B, d2 = (e / B) % B, d3 = e % B;
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = 0; k < g->nnb; ++k) {
+            const int ox = g->off[3 * k], oy = g->off[3 * k + 1];
+            if (!(-ox <= d0 && ox <= d1 && -oy <= d2 && oy <= d3)) continue;
+            for (int c = 0; c < 3; ++c) {
+                acc[c] += g->coef1[3 * k + c] * g->E * ox;
+                acc[3 + c] += g->coef1[3 * k + c] * g->E * oy;
+            }
+        }
+        for (int c = 0; c < 6; ++c) kt[(size_t)6 * e + c] = (float)acc[c];
+    }
+    if (!g->d_kt32) PD_CUDA(cudaMalloc(&g->d_kt32, sizeof(float) * kt.size()));
+    PD_CUDA(cudaMemcpy(g->d_kt32, kt.data(), sizeof(float) * kt.size(), cudaMemcpyHostToDevice));
     std::vector<float> S32(S.begin(), S.end());
     if (!g->d_sym64) {
         PD_CUDA(cudaMalloc(&g->d_sym64, sizeof(double) * S.size()));

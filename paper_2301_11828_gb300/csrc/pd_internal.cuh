@@ -109,6 +109,7 @@ struct pd_grid {
     float *d_sym3_32 = nullptr;
     double *d_ctot64 = nullptr;     // interior diagonal block (3D FFT epilogue)
     float *d_ctot32 = nullptr;
+    float *d_kt32 = nullptr;        // 2D FFT tiles: first moments sum_{in-grid o} c(o) o per edge class (6 floats)
     int64_t kd_entries = 0;
     int64_t broken_total = 0;
 

@@ -171,13 +171,14 @@ extern "C" int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *s
             }
         g->stencil_tile_rows = saved_rows;
         if (rc) break;
-        // In FP32 the FFT tiles are measured but never chosen: their rounding error is
-        // relative to |u| |K|, not to |K u| (the transforms carry the field's own
-        // magnitude), which misses the FP32 tolerance on smooth fields; the stencil
-        // sums differences.  PD_METHOD_FFT still selects them explicitly.
+        // In FP32 the FFT tiles round relative to |u - L| |K| (L the tile's plane), not to
+        // |K u|; |K| falls like 1/M^2 at a fixed modulus, so on smooth fields their error
+        // is within the FP32 tolerance with a margin only from M = 5 (at M = 3 it reaches
+        // the tolerance): below that they are measured but never chosen in FP32 (the
+        // stencils sum differences).  PD_METHOD_FFT still selects them explicitly.
         int best = 0, best_st = 0;
         for (int c = 1; c < nc; ++c) {
-            const bool eligible = !(prec == 0 && cand[c].method == PD_METHOD_FFT);
+            const bool eligible = !(prec == 0 && cand[c].method == PD_METHOD_FFT && g->M < 5);
             if (eligible && cand[c].best < cand[best].best) best = c;
             if (cand[c].method == PD_METHOD_STENCIL && cand[c].best < cand[best_st].best) best_st = c;
         }

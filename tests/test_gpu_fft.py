@@ -166,3 +166,41 @@ def test_fft_tma_tiles_match_oracle_and_plain_tiles(pd, n, M):
         ref = _K(2, n, h, M, un, E=0.7)
         assert rel_l2(tma[b].double().cpu().numpy(), ref) <= 2e-5
         assert rel_l2(tma[b].double().cpu().numpy(), plain[b].double().cpu().numpy()) <= 1e-6
+
+
+def _smooth(n, offset):
+    x = (np.arange(n[0]) + 0.5) / n[0]
+    y = (np.arange(n[1]) + 0.5) / n[1]
+    a = np.sin(2 * np.pi * x)[None, :] * np.cos(np.pi * y)[:, None]
+    b = np.cos(3 * np.pi * x)[None, :] * np.sin(2 * np.pi * y)[:, None]
+    if offset:
+        return np.stack([1.0 + 0.3 * a, 0.7 + 0.2 * b])
+    return np.stack([a, b])
+
+
+@pytest.mark.parametrize("n", [(512, 384), (1024, 1024), (510, 383)])
+@pytest.mark.parametrize("M", [3, 6])
+@pytest.mark.parametrize("offset", [False, True])
+def test_fft_f32_smooth_fields(pd, n, M, offset):
+    """FP32 FFT tiles subtract each tile's least-squares plane (quantised so that
+    it is exact in FP32) and add K of the plane back at the edge nodes: the
+    transforms round values of the size of the field's curvature over a tile, so
+    on smooth fields and on fields with a large constant part (whole field and
+    full-horizon interior; TMA path, plain-load path, projection) the error is
+    within the FP32 tolerance from M = 5 and reaches it at M = 3."""
+    h = 1.0 / n[0]
+    cons = syn.clamp_left(2, n, M)
+    g = pd.Grid(2, n, h, M, constrained=cons)
+    ut = torch.tensor(_smooth(n, offset), dtype=torch.float32, device="cuda")
+    un = ut.double().cpu().numpy()
+    inner = (slice(None), slice(M, n[1] - M), slice(M, n[0] - M))
+    for extra, proj in ((0, False), (pd.PD_NO_TMA, False), (0, True)):
+        fl = pd.PD_METHOD_FFT | extra | (pd.PD_PROJECT if proj else 0)
+        out = g.matvec(ut, flags=fl).double().cpu().numpy()
+        ref = _K(2, n, h, M, un, cons=cons if proj else None)
+        e, e_in = rel_l2(out, ref), rel_l2(out[inner], ref[inner])
+        print(f"fft f32 n={n} M={M} offset={offset} extra={extra} proj={proj}: {e:.3e} (interior {e_in:.3e})")
+        # |K| falls like 1/M^2 at a fixed modulus: from M = 5 (where the autotuner may pick the
+        # FP32 FFT) the error is well inside the tolerance; at M = 3 it reaches it
+        tol = 2e-5 if M >= 5 else 3e-5
+        assert e <= tol and e_in <= tol
