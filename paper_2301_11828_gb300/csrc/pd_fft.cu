@@ -21,13 +21,14 @@
 //      values of the size of u's variation (FP64) or curvature (FP32) over the
 //      tile instead of u's own;
 //   2. 64-point FFTs along x, then along y (each as 8 x 8, in two register
-//      passes with the twiddles W64^(n2 k1) between them);
+//      passes with the twiddles W64^(n2 k1) between them), leaving the
+//      spectrum in digit-reversed order along both axes;
 //   3. for each frequency pair (k, -k): unpack U_x, U_y from Z(k), Z(-k)
 //      (both components are real), multiply by the real 2x2 symbol
 //      S(k) = sum_o Kop(o) cos(2 pi k.o / P) / P^2 (Kop(0) = sum c, Kop(o) = -c(o);
 //      the kernel is even, so S is real; a quarter of it is staged in shared
 //      memory), repack W = H_x + i H_y;
-//   4. inverse FFTs along y then x;
+//   4. inverse FFTs along y then x, from that order back to natural order;
 //   5. epilogue: K u = Re/Im(w) - (Ctot - Kd_p) u_p on nodes near a face (the
 //      D^e term of Eq. tea:sc), projection, scale, optional fused dot.
 #include <cuda.h>
@@ -108,11 +109,19 @@ __device__ __forceinline__ void dft8(V (&x)[8])
     x[3] = cadd(e[3], t3);   x[7] = csub(e[3], t3);
 }
 
-// 64-point FFT of 64 lines (rows: es = 1, ls = PS; columns: es = PS, ls = 1).
+// 64-point FFTs of 64 lines (rows: es = 1, ls = PS; columns: es = PS, ls = 1),
+// as 8 x 8 with the twiddles W64^(n2 k1) between the two passes.  The forward
+// transform takes the line in natural order and leaves it digit-reversed: slot
+// 8 a + b holds frequency a + 8 b.  The inverse takes that order and returns the
+// line in natural order.  So every pass writes back the very slots its thread
+// read, and one block barrier per pass suffices (no transposing store that
+// would overwrite slots another thread has yet to read).
 // Thread mapping: lane -> line (and line + 32), warp -> the 8-point group index,
 // so every shared-memory access of a warp hits distinct banks.
-template <bool INV, typename T>
-__device__ __forceinline__ void fft64_lines(typename C2<T>::t *Z, int es, int ls)
+__device__ __forceinline__ int digrev64(int s) { return (s >> 3) | ((s & 7) << 3); }
+
+template <typename T>
+__device__ __forceinline__ void fft64_fwd(typename C2<T>::t *Z, int es, int ls)
 {
     using V = typename C2<T>::t;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;   // g in [0, 8)
@@ -123,27 +132,55 @@ __device__ __forceinline__ void fft64_lines(typename C2<T>::t *Z, int es, int ls
         V *line = Z + (lane + 32 * h) * ls;
 #pragma unroll
         for (int n1 = 0; n1 < 8; ++n1) v[h][n1] = line[(8 * n1 + g) * es];
-        dft8<INV, V, T>(v[h]);
+        dft8<false, V, T>(v[h]);
 #pragma unroll
-        for (int k1 = 1; k1 < 8; ++k1) v[h][k1] = cmulw<INV>(v[h][k1], tw<T>(g * k1));
+        for (int k1 = 1; k1 < 8; ++k1) v[h][k1] = cmulw<false>(v[h][k1], tw<T>(g * k1));
 #pragma unroll
         for (int k1 = 0; k1 < 8; ++k1) line[(8 * k1 + g) * es] = v[h][k1];
     }
     __syncthreads();
-    // pass 2: group g = k1; slots 8 k1 + n2 -> DFT over n2 -> X[k1 + 8 k2]
+    // pass 2: group g = k1; slots 8 k1 + n2 -> DFT over n2 -> X[k1 + 8 k2] at slot 8 k1 + k2
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         V *line = Z + (lane + 32 * h) * ls;
 #pragma unroll
         for (int n2 = 0; n2 < 8; ++n2) v[h][n2] = line[(8 * g + n2) * es];
+        dft8<false, V, T>(v[h]);
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) line[(8 * g + k2) * es] = v[h][k2];
     }
     __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void fft64_inv(typename C2<T>::t *Z, int es, int ls)
+{
+    using V = typename C2<T>::t;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    V v[2][8];
+    // pass A: group g = k1; slot 8 k1 + k2 holds X[k1 + 8 k2] -> inverse DFT over k2 -> * conj W64^(k1 n2)
+    // -> slot 8 k1 + n2
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         V *line = Z + (lane + 32 * h) * ls;
-        dft8<INV, V, T>(v[h]);
 #pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) line[(g + 8 * k2) * es] = v[h][k2];
+        for (int k2 = 0; k2 < 8; ++k2) v[h][k2] = line[(8 * g + k2) * es];
+        dft8<true, V, T>(v[h]);
+#pragma unroll
+        for (int n2 = 1; n2 < 8; ++n2) v[h][n2] = cmulw<true>(v[h][n2], tw<T>(g * n2));
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) line[(8 * g + n2) * es] = v[h][n2];
+    }
+    __syncthreads();
+    // pass B: group g = n2; slots 8 k1 + n2 -> inverse DFT over k1 -> x[8 n1 + n2] at slot 8 n1 + n2
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        V *line = Z + (lane + 32 * h) * ls;
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) v[h][k1] = line[(8 * k1 + g) * es];
+        dft8<true, V, T>(v[h]);
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) line[(8 * n1 + g) * es] = v[h][n1];
     }
     __syncthreads();
 }
@@ -321,16 +358,19 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
     }
     __syncthreads();
 
-    fft64_lines<false, T>(Z, 1, PS);    // rows (along x)
-    fft64_lines<false, T>(Z, PS, 1);    // columns (along y)
+    fft64_fwd<T>(Z, 1, PS);    // rows (along x)
+    fft64_fwd<T>(Z, PS, 1);    // columns (along y)
 
     // symbol product on frequency pairs (k, -k)
+    // the transforms left slot (sy, sx) holding frequency (digrev64(sy), digrev64(sx))
     for (int t = threadIdx.x; t < P * P; t += kT) {
-        const int kx = t % P, ky = t / P;
+        const int sx = t % P, sy = t / P;
+        const int kx = digrev64(sx), ky = digrev64(sy);
         const int mx = (P - kx) & (P - 1), my = (P - ky) & (P - 1);
-        const int t2 = my * P + mx;
+        const int smx = digrev64(mx), smy = digrev64(my);
+        const int t2 = smy * P + smx;
         if (t2 < t) continue;
-        const V zk = Z[ky * PS + kx], zm0 = Z[my * PS + mx];
+        const V zk = Z[sy * PS + sx], zm0 = Z[smy * PS + smx];
         const V zm = {zm0.x, -zm0.y};   // conj Z(-k)
         // U_x = (Z(k) + conj Z(-k)) / 2,  U_y = -i (Z(k) - conj Z(-k)) / 2
         const V ux = {T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y + zm.y)};
@@ -344,13 +384,13 @@ k_fft_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
         const V hx = {sxx * ux.x + sxy * uy.x, sxx * ux.y + sxy * uy.y};
         const V hy = {sxy * ux.x + syy * uy.x, sxy * ux.y + syy * uy.y};
         // W(k) = H_x + i H_y ; W(-k) = conj H_x + i conj H_y
-        Z[ky * PS + kx] = {hx.x - hy.y, hx.y + hy.x};
-        if (t2 != t) Z[my * PS + mx] = {hx.x + hy.y, hy.x - hx.y};
+        Z[sy * PS + sx] = {hx.x - hy.y, hx.y + hy.x};
+        if (t2 != t) Z[smy * PS + smx] = {hx.x + hy.y, hy.x - hx.y};
     }
     __syncthreads();
 
-    fft64_lines<true, T>(Z, PS, 1);     // columns
-    fft64_lines<true, T>(Z, 1, PS);     // rows
+    fft64_inv<T>(Z, PS, 1);     // columns
+    fft64_inv<T>(Z, 1, PS);     // rows
 
     T dot = T(0);
     for (int t = threadIdx.x; t < TO * TO; t += kT) {
@@ -501,14 +541,16 @@ k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out,
         __syncthreads();   // the staged box is free: the next tile's window is copied meanwhile
         if (threadIdx.x == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
 
-        fft64_lines<false, float>(Z, 1, PS);
-        fft64_lines<false, float>(Z, PS, 1);
+        fft64_fwd<float>(Z, 1, PS);
+        fft64_fwd<float>(Z, PS, 1);
         for (int e = threadIdx.x; e < P * P; e += kT) {
-            const int kx = e % P, ky = e / P;
+            const int sx = e % P, sy = e / P;   // slot (sy, sx) holds frequency (digrev64(sy), digrev64(sx))
+            const int kx = digrev64(sx), ky = digrev64(sy);
             const int mx = (P - kx) & (P - 1), my = (P - ky) & (P - 1);
-            const int t2 = my * P + mx;
+            const int smx = digrev64(mx), smy = digrev64(my);
+            const int t2 = smy * P + smx;
             if (t2 < e) continue;
-            const V zk = Z[ky * PS + kx], zm0 = Z[my * PS + mx];
+            const V zk = Z[sy * PS + sx], zm0 = Z[smy * PS + smx];
             const V zm = {zm0.x, -zm0.y};
             const V ux = {0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y)};
             const V uy = {0.5f * (zk.y - zm.y), -0.5f * (zk.x - zm.x)};
@@ -518,12 +560,12 @@ k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out,
             const float sxx = sq[qi], sxy = sgn * sq[QH * QH + qi], syy = sq[2 * QH * QH + qi];
             const V hx = {sxx * ux.x + sxy * uy.x, sxx * ux.y + sxy * uy.y};
             const V hy = {sxy * ux.x + syy * uy.x, sxy * ux.y + syy * uy.y};
-            Z[ky * PS + kx] = {hx.x - hy.y, hx.y + hy.x};
-            if (t2 != e) Z[my * PS + mx] = {hx.x + hy.y, hy.x - hx.y};
+            Z[sy * PS + sx] = {hx.x - hy.y, hx.y + hy.x};
+            if (t2 != e) Z[smy * PS + smx] = {hx.x + hy.y, hy.x - hx.y};
         }
         __syncthreads();
-        fft64_lines<true, float>(Z, PS, 1);
-        fft64_lines<true, float>(Z, 1, PS);
+        fft64_inv<float>(Z, PS, 1);
+        fft64_inv<float>(Z, 1, PS);
 
         const float *ub = u + (int64_t)b * 2 * N;
         float *ob = out + (int64_t)b * 2 * N;
