@@ -543,25 +543,31 @@ k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out,
 
         fft64_fwd<float>(Z, 1, PS);
         fft64_fwd<float>(Z, PS, 1);
-        for (int e = threadIdx.x; e < P * P; e += kT) {
-            const int sx = e % P, sy = e / P;   // slot (sy, sx) holds frequency (digrev64(sy), digrev64(sx))
-            const int kx = digrev64(sx), ky = digrev64(sy);
-            const int mx = (P - kx) & (P - 1), my = (P - ky) & (P - 1);
-            const int smx = digrev64(mx), smy = digrev64(my);
+        {   // a thread keeps one slot column sx (kT is a multiple of P): its frequency, partner
+            // column and quarter-symbol column are formed once; slot (sy, sx) holds frequency
+            // (digrev64(sy), digrev64(sx))
+            const int sx = threadIdx.x % P;
+            const int kx = digrev64(sx), smx = digrev64((P - kx) & (P - 1));
+            const int qx = kx <= P / 2 ? kx : P - kx;
+            const bool hx = kx > P / 2;
+            for (int sy = threadIdx.x / P; sy < P; sy += kT / P) {
+            const int e = sy * P + sx;
+            const int ky = digrev64(sy), smy = digrev64((P - ky) & (P - 1));
             const int t2 = smy * P + smx;
             if (t2 < e) continue;
             const V zk = Z[sy * PS + sx], zm0 = Z[smy * PS + smx];
             const V zm = {zm0.x, -zm0.y};
             const V ux = {0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y)};
             const V uy = {0.5f * (zk.y - zm.y), -0.5f * (zk.x - zm.x)};
-            const int qx = kx <= P / 2 ? kx : P - kx, qy = ky <= P / 2 ? ky : P - ky;
+            const int qy = ky <= P / 2 ? ky : P - ky;
             const int qi = qy * QH + qx;
-            const float sgn = ((kx > P / 2) != (ky > P / 2)) ? -1.f : 1.f;
+            const float sgn = (hx != (ky > P / 2)) ? -1.f : 1.f;
             const float sxx = sq[qi], sxy = sgn * sq[QH * QH + qi], syy = sq[2 * QH * QH + qi];
-            const V hx = {sxx * ux.x + sxy * uy.x, sxx * ux.y + sxy * uy.y};
-            const V hy = {sxy * ux.x + syy * uy.x, sxy * ux.y + syy * uy.y};
-            Z[sy * PS + sx] = {hx.x - hy.y, hx.y + hy.x};
-            if (t2 != e) Z[smy * PS + smx] = {hx.x + hy.y, hy.x - hx.y};
+            const V hx_ = {sxx * ux.x + sxy * uy.x, sxx * ux.y + sxy * uy.y};
+            const V hy_ = {sxy * ux.x + syy * uy.x, sxy * ux.y + syy * uy.y};
+            Z[sy * PS + sx] = {hx_.x - hy_.y, hx_.y + hy_.x};
+            if (t2 != e) Z[smy * PS + smx] = {hx_.x + hy_.y, hy_.x - hx_.y};
+            }
         }
         __syncthreads();
         fft64_inv<float>(Z, PS, 1);
@@ -569,10 +575,11 @@ k_fft_tile_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ out,
 
         const float *ub = u + (int64_t)b * 2 * N;
         float *ob = out + (int64_t)b * 2 * N;
-        for (int e = threadIdx.x; e < TO * TO; e += kT) {
-            const int a = M + e % TO, r = M + e / TO;
+        const int ea = threadIdx.x % P;   // a thread keeps a window column (outputs: M <= a, r < P - M)
+        for (int r = M + ((threadIdx.x / P) - M % (kT / P) + (kT / P)) % (kT / P); r < P - M; r += kT / P) {
+            const int a = ea;
             const int gx = x0 + a, gy = y0 + r;
-            if (gx >= nx || gy >= ny) continue;
+            if (a < M || a >= P - M || gx >= nx || gy >= ny) continue;
             const int64_t p = (int64_t)gy * nx + gx;
             const V w = Z[r * PS + a];
             float fx = w.x, fy = w.y;
