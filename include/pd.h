@@ -63,13 +63,18 @@ typedef enum {
 #define PD_PROJECT        0x100u /* return P K P u: P zeroes the constrained components */
 #define PD_IGNORE_BROKEN  0x200u /* use the intact operator A^ + D^e (skip mu / D^f) */
 #define PD_NO_TMA         0x400u /* FP32 2D stencil and FFT tiles: use the plain-load kernels, not the TMA-fed ones */
-#define PD_ACCURATE       0x800u /* accepted for compatibility: every FP32 stencil sums differences of
-                                    nearby values by default (see PD_PAIR_FORM) */
-#define PD_PAIR_FORM      0x1000u /* stencils: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o)
-                                    instead of the default difference form.  Less arithmetic, but its
+#define PD_ACCURATE       0x800u /* FP64 2D stencil: the difference form (below) instead of the default
+                                    pair form on u minus each tile's plane (both keep the error relative
+                                    to |K u|); FP32 stencils sum differences by default (no effect) */
+#define PD_PAIR_FORM      0x1000u /* stencils: the pair form Kd_p u_p - sum c(o) (u_p+o + u_p-o) on u
+                                    itself instead of the default difference form (FP32, 3D) or the
+                                    pair form on u minus each tile's least-squares plane, exact in FP64,
+                                    plus K of the plane at the faces (FP64 2D; the difference form with
+                                    a fused dot).  Less arithmetic, but its
                                     error is relative to sum |c| |u|, not to |K u|: on smooth fields,
                                     or fields with a large constant part, FP32 exceeds 1e-4 relative
-                                    error (2D) and FP64 reaches a few 1e-12.  For comparison, for inner
+                                    error (2D) and FP64 a few 1e-12 over the field (3e-10 on the
+                                    interior of a field with a large gradient).  For comparison, for inner
                                     solver products whose rounding an FP64 refinement corrects, and
                                     for the FP64 CG and ADR iterations (tolerance far above it) */
 
@@ -308,8 +313,12 @@ int pd_break_segment(pd_grid *g, const int64_t seg[4], int64_t den, int64_t *n_b
  * ext_rows), which must contain [row0 - M, row0 + rows + M) clipped to the
  * grid; out: DEVICE [batch][dim][rows][...] receives rows [row0, row0 + rows)
  * of K u (P K P u with PD_PROJECT).  In 2D row0 must be a multiple of 32 (the
- * stencil tile height).  Every output is then computed exactly as by
- * pd_matvec: the slabs of a split give the whole-grid product bit for bit.
+ * stencil tile height).  Every output of a band whose row count is a multiple
+ * of 32, or which ends at the grid's last row, is then computed exactly as by
+ * pd_matvec: the slabs of a split give the whole-grid product bit for bit.  (A
+ * ragged band inside the grid agrees to rounding in the FP64 2D default form,
+ * whose tiles fit their plane over the rows the band holds; bit for bit in the
+ * other forms.)
  * Stencil form, intact bonds, constant modulus, no surface correction.
  * Errors: PD_ERR_INVALID (shape, alignment, unsupported state), PD_ERR_CUDA. */
 int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const void *u_ext, int64_t ext_row0,
@@ -323,26 +332,28 @@ int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const 
 int pd_set_method(pd_grid *g, uint32_t method);
 
 /* Pins the layout of the FP32 TMA-fed 2D stencil (the bond sum of Eq. mat:f1
- * taken as differences of nearby values): rows = 32 (64 x 32 output tiles, the
- * default) or 16 (64 x 16 tiles; used at M <= 4) -- both give identical bits --
- * or rows = 0, the column walk: each CTA walks down a strip of 128 columns and
+ * taken as differences of nearby values): rows = 64 (64 x 64 output tiles, the
+ * default; M <= 3, 64 x 32 beyond), 32 (64 x 32 tiles) or 16 (64 x 16 tiles;
+ * M <= 4) -- all give identical bits -- or rows = 0, the column walk: each CTA walks down a strip of 128 columns and
  * every input row is staged once (no vertical halo), used at M <= 3 for
  * products without PD_PROJECT or a fused dot (the tile kernel serves the rest).
  * The walk agrees with the tiles to FP32 rounding, not bit for bit; a band of
  * rows (pd_matvec_rows) reproduces the whole-grid product of the same layout bit
- * for bit.  Host-only.  Errors: PD_ERR_INVALID (rows not 0, 16 or 32). */
+ * for bit.  Host-only.  Errors: PD_ERR_INVALID (rows not 0, 16, 32 or 64). */
 int pd_set_stencil_tile_rows(pd_grid *g, int rows);
 
 /* Autotuner: measures the candidates of K u for the precision(s) in flags
  * (PD_F32 and/or PD_F64) -- the direct stencil and, without a modulus field,
  * the FFT tiles; for FP32 2D grids on the TMA-fed stencil at M <= 4 also the
- * stencil's tile height (64 x 32 or 64 x 16 outputs) -- on scratch vectors the
+ * stencil's layout (64 x 64 tiles at M <= 3, 64 x 32, 64 x 16, and the column
+ * walk where it applies) -- on scratch vectors the
  * grid keeps (allocated on the first call), CUDA events on `stream`: three
  * warm-up launches each, then five rounds of ten launches per candidate in
  * turn, each keeping its fastest round.  Records the fastest candidate for
- * PD_METHOD_AUTO and the faster stencil tile for every stencil product.  In
- * FP32 the FFT tiles are timed but not chosen: their rounding error is relative
- * to |u| |K| rather than |K u|, over the FP32 tolerance on smooth fields
+ * PD_METHOD_AUTO and the faster stencil layout for every stencil product.  In
+ * FP32 below M = 5 the FFT tiles are timed but not chosen: their rounding error
+ * is relative to |u - L| |K| (L the tile's plane) rather than |K u|, which
+ * reaches the FP32 tolerance on smooth fields at small horizons
  * (PD_METHOD_FFT still selects them).
  * times_ms: host double [4] or NULL, receives {stencil f32, fft f32, stencil
  * f64, fft f64} in ms per field (the faster stencil tile; 0 where not
@@ -350,7 +361,7 @@ int pd_set_stencil_tile_rows(pd_grid *g, int rows);
 int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream);
 
 /* pd_autotune with a cache: cache_path names a JSON file of entries
- *   "<key>": {"method": "stencil"|"fft", "tile_rows": 32|16, "ms_per_field": t}
+ *   "<key>": {"method": "stencil"|"fft", "tile_rows": 64|32|16|0, "ms_per_field": t}
  * keyed by dimension, extents, delta/h, precision (and a modulus field), device
  * name and SM count.  When the file holds an entry for every precision in
  * flags, the recorded choice is applied without measuring (*from_cache = 1);

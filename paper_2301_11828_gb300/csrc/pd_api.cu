@@ -103,6 +103,31 @@ static int build_kd(pd_grid *g)
             for (int c = 0; c < nc; ++c) kd[(size_t)e * nc + c] += g->coef1[(size_t)k * nc + c] * g->E;
         }
     }
+    if (g->dim == 2) {
+        // first moments per edge class: T^x_ab = sum over in-grid offsets of c_ab(o) o_x, T^y_ab
+        // alike with o_y (layout Tx_xx, Tx_xy, Tx_yy, Ty_xx, Ty_xy, Ty_yy): K of a plane at an edge
+        // node (the FFT tiles and the FP64 stencil subtract a plane per tile)
+        std::vector<double> kt((size_t)entries * 6, 0.0);
+        for (int64_t e = 0; e < entries; ++e) {
+            const int d0 = (int)(e / (B * B * B)), d1 = (int)((e / (B * B)) % B), d2 = (int)((e / B) % B),
+                      d3 = (int)(e % B);
+            for (int k = 0; k < g->nnb; ++k) {
+                const int ox = g->off[3 * k], oy = g->off[3 * k + 1];
+                if (!(-ox <= d0 && ox <= d1 && -oy <= d2 && oy <= d3)) continue;
+                for (int c = 0; c < 3; ++c) {
+                    kt[(size_t)6 * e + c] += g->coef1[3 * k + c] * g->E * ox;
+                    kt[(size_t)6 * e + 3 + c] += g->coef1[3 * k + c] * g->E * oy;
+                }
+            }
+        }
+        std::vector<float> kt32(kt.begin(), kt.end());
+        if (!g->d_kt64) {
+            PD_CUDA(cudaMalloc(&g->d_kt64, kt.size() * sizeof(double)));
+            PD_CUDA(cudaMalloc(&g->d_kt32, kt.size() * sizeof(float)));
+        }
+        PD_CUDA(cudaMemcpy(g->d_kt64, kt.data(), kt.size() * sizeof(double), cudaMemcpyHostToDevice));
+        PD_CUDA(cudaMemcpy(g->d_kt32, kt32.data(), kt32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     std::vector<float> kd32(kd.begin(), kd.end());
     if (!g->d_kd64) {
         PD_CUDA(cudaMalloc(&g->d_kd64, kd.size() * sizeof(double)));
@@ -133,6 +158,7 @@ static void free_grid(pd_grid *g)
     cudaFree(g->d_ctot64);
     cudaFree(g->d_ctot32);
     cudaFree(g->d_kt32);
+    cudaFree(g->d_kt64);
     cudaFree(g->d_off);
     cudaFree(g->d_brk_thr);
     cudaFree(g->d_coef);
@@ -436,6 +462,7 @@ int pd_matvec_rows(pd_grid *g, int64_t batch, int64_t row0, int64_t rows, const 
     a.batch = batch;
     a.project = (flags & PD_PROJECT) && g->has_cons;
     a.no_tma = (flags & PD_NO_TMA) != 0;
+    a.accurate = (flags & PD_ACCURATE) != 0;
     a.scale = 1.0;
     a.in_row0 = ext_row0;
     a.in_rows = ext_rows;

@@ -748,25 +748,6 @@ int fft_prepare(pd_grid *g)
             }
             for (int c = 0; c < 3; ++c) S[(size_t)c * QH * QH + ky * QH + kx] = acc[c] / ((double)P * P);
         }
-    // first moments per edge class (clipped face distances a0, a1, b0, b1 in [0, M]):
-    // Tx_ab = sum over in-grid offsets of c_ab(o) o_x, Ty_ab alike with o_y
-    const int B = g->M + 1;
-    std::vector<float> kt((size_t)B * B * B * B * 6, 0.f);
-    for (int e = 0; e < B * B * B * B; ++e) {
-        const int d0 = e / (B * B * B), d1 = (e / (B * B)) % B, d2 = (e / B) % B, d3 = e % B;
-        double acc[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = 0; k < g->nnb; ++k) {
-            const int ox = g->off[3 * k], oy = g->off[3 * k + 1];
-            if (!(-ox <= d0 && ox <= d1 && -oy <= d2 && oy <= d3)) continue;
-            for (int c = 0; c < 3; ++c) {
-                acc[c] += g->coef1[3 * k + c] * g->E * ox;
-                acc[3 + c] += g->coef1[3 * k + c] * g->E * oy;
-            }
-        }
-        for (int c = 0; c < 6; ++c) kt[(size_t)6 * e + c] = (float)acc[c];
-    }
-    if (!g->d_kt32) PD_CUDA(cudaMalloc(&g->d_kt32, sizeof(float) * kt.size()));
-    PD_CUDA(cudaMemcpy(g->d_kt32, kt.data(), sizeof(float) * kt.size(), cudaMemcpyHostToDevice));
     std::vector<float> S32(S.begin(), S.end());
     if (!g->d_sym64) {
         PD_CUDA(cudaMalloc(&g->d_sym64, sizeof(double) * S.size()));

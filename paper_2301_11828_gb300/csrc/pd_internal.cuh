@@ -109,7 +109,8 @@ struct pd_grid {
     float *d_sym3_32 = nullptr;
     double *d_ctot64 = nullptr;     // interior diagonal block (3D FFT epilogue)
     float *d_ctot32 = nullptr;
-    float *d_kt32 = nullptr;        // 2D FFT tiles: first moments sum_{in-grid o} c(o) o per edge class (6 floats)
+    double *d_kt64 = nullptr;       // 2D: first moments sum_{in-grid o} c(o) o per edge class (6 values)
+    float *d_kt32 = nullptr;        //     (K of a plane at an edge node), FP64 and FP32 copies
     int64_t kd_entries = 0;
     int64_t broken_total = 0;
 
@@ -158,7 +159,7 @@ struct MatvecArgs {
     bool use_E;           // per-node modulus (direct form)
     bool input_projected; // the caller guarantees P u = u (skip the input projection)
     bool no_tma;          // force the plain FP32 2D stencil
-    bool accurate;        // FP32 3D stencil: difference form (PD_ACCURATE)
+    bool accurate;        // FP64 2D stencil: difference form instead of the plane-subtracted pair form
     bool pair_form;       // FP32 TMA 2D stencil: the cancelling pair form (PD_PAIR_FORM)
     double scale;         // multiplies the whole operator (1 = K u)
     // row window (2D stencils; pd_matvec_rows): the input holds grid rows

@@ -15,7 +15,14 @@
 // and, for each, applies every (ox, oy) pair to its R outputs.  Block entries
 // that vanish by geometry (c_xy and c_yy of (ox, 0), c_xx and c_xy of (0, oy))
 // are skipped at compile time.  PD_PAIR_FORM selects the pair form
-// (k_tbt2d_pair, below).
+// (k_tbt2d_pair, below).  The default FP64 product without a fused dot is the
+// pair form on u minus the box's plane (k_tbt2d_pair<double, M, true>), which
+// keeps the rounding relative to |K u| at less arithmetic than the difference
+// form (PD_ACCURATE selects the latter in FP64).
+//
+// Row windows (pd_matvec_rows): the staged rows are those the input holds,
+// [in_row0, in_end); rows of the grid outside them enter only outputs that the
+// launch does not write.
 #include "pd_stencil.cuh"
 
 namespace pd {
@@ -93,10 +100,10 @@ __global__ void __launch_bounds__(kThreads)
 k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
         const uint8_t *__restrict__ cons, int project, T scale,
         PlainTab<T, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
-        int in_row0, int64_t Nin, int out_row0, int out_end)
+        int in_row0, int in_end, int64_t Nin, int out_row0, int out_end)
 {
-    // Rows are grid rows; the input holds rows [in_row0, ...) with plane size Nin, the
-    // output rows [out_row0, out_end) with plane size N (the whole grid: 0, N, 0, ny).
+    // Rows are grid rows; the input holds rows [in_row0, in_end) with plane size Nin, the
+    // output rows [out_row0, out_end) with plane size N (the whole grid: 0, ny, N, 0, ny).
     constexpr int R = rows2d<T, M>();
     constexpr int TX = kTX2, TY = kGY2 * R, SX = TX + 2 * M, SY = TY + 2 * M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -112,7 +119,7 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
         const int r = t / SX, c = t - r * SX;
         const int gx = x0 - M + c, gy = y0 - M + r;
         T vx = T(0), vy = T(0);
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        if (gx >= 0 && gx < nx && gy >= in_row0 && gy < in_end) {
             const int64_t p = (int64_t)gy * nx + gx;
             vx = __ldg(ub + p);
             vy = __ldg(ub + Nin + p);
@@ -203,20 +210,110 @@ k_tbt2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
 }
 
 
+// The box's reference plane (k_tbt2d_pair<double, M, true>).  The pair form's
+// rounding error is relative to the staged values, so a field with a large
+// constant part or gradient loses digits of K u; the box's least-squares plane
+// L is subtracted first, leaving the field's curvature part.  K maps a plane to
+// zero at every node with a full horizon, and at a node near a face to
+// -sum_b (Tx_ab gx_b + Ty_ab gy_b), Tx_ab = sum of c_ab(o) o_x over the in-grid
+// offsets (Ty alike with o_y): the first-moment table of the node's edge class.
+// L is quantised so that its value at every box node is exact in FP64:
+// L = q (L0 + Gx (c - ar) + Gy (r - rr)) with q a power of two and integers
+// below 2^53 -- the kernel then forms K (u - L) from exactly u - L (rounded
+// once), and K u = K (u - L) + K L holds to rounding.
+//
+// Warp 0 fits the plane in FP32 to an 8 x 8 sample of the box's in-window
+// rectangle [ca, cb) x [ra, rb) (box coordinates; fetch(c, r, vx, vy) reads a
+// node; any plane serves, the fit only has to follow the field closely),
+// quantises it in FP64 and writes the plane's row and column parts:
+// lr[c][r] = q (L0 + Gy (r - rr)), lc[c][k] = q Gx (k - ar), whose sums are exact,
+// and the per-node gradients g = (q Gx_x, q Gy_x, q Gx_y, q Gy_y).  The caller's
+// next block barrier makes them visible to every thread.
+template <int SX, int SY, typename F>
+__device__ __forceinline__ void box_plane(F fetch, int ca, int cb, int ra, int rb,
+                                          double (*lr)[SY], double (*lc)[SX], double *g)
+{
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x, wx = cb - ca, wy = rb - ra;
+    float mx = 0.f, my = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        mx += (float)(ca + (i * (wx - 1)) / 7);
+        my += (float)(ra + (i * (wy - 1)) / 7);
+    }
+    mx *= 0.125f;
+    my *= 0.125f;
+    float sxx = 0.f, syy = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float dx = (float)(ca + (i * (wx - 1)) / 7) - mx, dy = (float)(ra + (i * (wy - 1)) / 7) - my;
+        sxx = fmaf(dx, dx, sxx);
+        syy = fmaf(dy, dy, syy);
+    }
+    float sm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane & 7, j = (lane >> 3) + 4 * h;
+        const int c = ca + (i * (wx - 1)) / 7, r = ra + (j * (wy - 1)) / 7;
+        float vx, vy;
+        fetch(c, r, vx, vy);
+        const float dx = (float)c - mx, dy = (float)r - my;
+        sm[0] += vx;
+        sm[1] = fmaf(vx, dx, sm[1]);
+        sm[2] = fmaf(vx, dy, sm[2]);
+        sm[3] += vy;
+        sm[4] = fmaf(vy, dx, sm[4]);
+        sm[5] = fmaf(vy, dy, sm[5]);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sm[k] += __shfl_xor_sync(0xffffffffu, sm[k], o);
+    const float ix = sxx > 0.f ? 0.125f / sxx : 0.f, iy = syy > 0.f ? 0.125f / syy : 0.f;
+    const int ar = ca + (wx - 1) / 2, rr = ra + (wy - 1) / 2;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const double gx = (double)(sm[3 * c + 1] * ix), gy = (double)(sm[3 * c + 2] * iy);
+        const double l = (double)(sm[3 * c] * (1.f / 64.f) + (float)gx * ((float)ar - mx) + (float)gy * ((float)rr - my));
+        const double bound = fabs(l) + 64.0 * (fabs(gx) + fabs(gy));
+        double Q0 = 0.0, Gx = 0.0, Gy = 0.0;
+        // q = 2^(k - 50) with bound < 2^k (from the exponent field), and 1/q exactly; box
+        // offsets from (ar, rr) are below 80, so |L0| + 80 (|Gx| + |Gy|) < 2^53
+        const long long eb = (__double_as_longlong(bound) >> 52) & 0x7ff;
+        if (bound > 1e-280 && eb < 2000) {
+            const double q = __longlong_as_double((eb - 49) << 52);
+            const double iq = __longlong_as_double((2095 - eb) << 52);
+            Q0 = q * rint(l * iq);
+            Gx = q * rint(gx * iq);
+            Gy = q * rint(gy * iq);
+        }
+        for (int k = lane; k < SX; k += 32) lc[c][k] = Gx * (double)(k - ar);
+        for (int k = lane; k < SY; k += 32) lr[c][k] = fma(Gy, (double)(k - rr), Q0);
+        if (lane == 0) {
+            g[2 * c] = Gx;
+            g[2 * c + 1] = Gy;
+        }
+    }
+}
+
 // The pair form  (K u)_p = Kd_p u_p - sum_{o in half} c(o) (u~_{p+o} + u~_{p-o})
-// (PD_PAIR_FORM; u~ zero outside the grid, Kd_p the diagonal block over the
-// in-grid offsets from the clipped-distance table, which folds in the edge
-// self-term D^e of Eq. tea:sc).  Fewer operations than the difference form, but
-// its rounding error is relative to sum |c| |u| rather than |K u| (in FP64 at most
-// a few 1e-12 on smooth fields with a constant part): used where a solver's
-// own tolerance is far above that, e.g. the FP64 CG and ADR iterations.
-template <typename T, int M>
+// (u~ zero outside the grid, Kd_p the diagonal block over the in-grid offsets
+// from the clipped-distance table, which folds in the edge self-term D^e of
+// Eq. tea:sc).  Fewer operations than the difference form.  On u itself
+// (PD_PAIR_FORM, PLANE false) its rounding error is relative to sum |c| |u|
+// rather than |K u| (in FP64, on the full-horizon interior of smooth 1024^2
+// fields, 1e-11 with a large constant part and 3e-10 with a large gradient):
+// used where a solver's own tolerance is far above that, e.g.
+// the FP64 CG and ADR iterations.  On u minus the box's plane (PLANE, FP64, no
+// fused dot; box_plane) it is the default FP64 product.
+template <typename T, int M, bool PLANE>
 __global__ void __launch_bounds__(kThreads)
 k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
-             const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
-             PairTab<T, 2, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
-             int in_row0, int64_t Nin, int out_row0, int out_end)
+             const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, const T *__restrict__ kt,
+             T scale, PairTab<T, 2, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
+             int in_row0, int in_end, int64_t Nin, int out_row0, int out_end)
 {
+    static_assert(!PLANE || sizeof(T) == 8, "the box plane is formed in FP64");
     constexpr int R = rows2d<T, M>();
     constexpr int TX = kTX2, TY = kGY2 * R, SX = TX + 2 * M, SY = TY + 2 * M, WL = R + 2 * M;
     constexpr int NP = PairTab<T, 2, M>::kPairs;
@@ -229,11 +326,30 @@ k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64
     T *ob = out + b * 2 * N - (int64_t)out_row0 * nx;
     const int x0 = blockIdx.x * TX, y0 = out_row0 + blockIdx.y * TY;
 
+    constexpr int PX = PLANE ? SX : 1, PY = PLANE ? SY : 1;
+    __shared__ double s_lr[2][PY], s_lc[2][PX], s_g[4];
+    if constexpr (PLANE) {
+        // the plane from the box's in-window rectangle, before staging
+        const int ca = max(0, M - x0), cb = min(SX, nx - x0 + M);
+        const int ra = max(0, in_row0 - y0 + M), rb = min(SY, in_end - y0 + M);
+        box_plane<SX, SY>([&](int c, int r, float &fx, float &fy) {
+            const int64_t p = (int64_t)(y0 - M + r) * nx + (x0 - M + c);
+            T vx = __ldg(ub + p), vy = __ldg(ub + Nin + p);
+            if (project) {
+                const uint8_t m = __ldg(cons + p);
+                if (m & 1) vx = T(0);
+                if (m & 2) vy = T(0);
+            }
+            fx = (float)vx;
+            fy = (float)vy;
+        }, ca, cb, ra, rb, s_lr, s_lc, s_g);
+        __syncthreads();
+    }
     for (int t = threadIdx.x; t < SX * SY; t += kThreads) {
         const int r = t / SX, c = t - r * SX;
         const int gx = x0 - M + c, gy = y0 - M + r;
         T vx = T(0), vy = T(0);
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
+        if (gx >= 0 && gx < nx && gy >= in_row0 && gy < in_end) {
             const int64_t p = (int64_t)gy * nx + gx;
             vx = __ldg(ub + p);
             vy = __ldg(ub + Nin + p);
@@ -242,11 +358,20 @@ k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64
                 if (m & 1) vx = T(0);
                 if (m & 2) vy = T(0);
             }
+            if constexpr (PLANE) {
+                vx -= s_lr[0][r] + s_lc[0][c];
+                vy -= s_lr[1][r] + s_lc[1][c];
+            }
         }
         s_x[t] = vx;
         s_y[t] = vy;
     }
     __syncthreads();
+    [[maybe_unused]] T pg[4];   // the plane's per-node gradients (PLANE)
+    if constexpr (PLANE) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pg[k] = s_g[k];
+    }
 
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const T *colx = s_x + (ty * R) * SX + tx + M;   // (row0, col) of this thread's column
@@ -306,14 +431,22 @@ k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64
             const T upx = cx[r + M], upy = cy[r + M];
             T kxx = tab.v[3 * NP], kxy = tab.v[3 * NP + 1], kyy = tab.v[3 * NP + 2];
             const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
-            if (a0 != M || a1 != M || b0 != M || b1 != M) {
-                const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
+            const bool edge = a0 != M || a1 != M || b0 != M || b1 != M;
+            const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
+            if (edge) {
                 kxx = __ldg(kd + 3 * cls);
                 kxy = __ldg(kd + 3 * cls + 1);
                 kyy = __ldg(kd + 3 * cls + 2);
             }
             T fx = dfma(kxx, upx, dfma(kxy, upy, -ax[r]));
             T fy = dfma(kxy, upx, dfma(kyy, upy, -ay[r]));
+            if constexpr (PLANE) {
+                if (edge) {   // K L at a node near a face
+                    const T *t6 = kt + 6 * cls;   // Tx_xx, Tx_xy, Tx_yy, Ty_xx, Ty_xy, Ty_yy
+                    fx -= __ldg(t6) * pg[0] + __ldg(t6 + 3) * pg[1] + __ldg(t6 + 1) * pg[2] + __ldg(t6 + 4) * pg[3];
+                    fy -= __ldg(t6 + 1) * pg[0] + __ldg(t6 + 4) * pg[1] + __ldg(t6 + 2) * pg[2] + __ldg(t6 + 5) * pg[3];
+                }
+            }
             if (project) {
                 const uint8_t m = __ldg(cons + p);
                 if (m & 1) fx = T(0);
@@ -376,8 +509,8 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     dim3 grid((unsigned)((nx + kTX2 - 1) / kTX2), (unsigned)((out_rows + TY - 1) / TY), (unsigned)a.batch);
     kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)nx, (int)ny, out_rows * nx, g->d_cons,
                                       a.project ? 1 : 0, (T)a.scale, make_plain<T, M>(g), a.dot_partial,
-                                      a.dot_out, a.retire, (int)a.in_row0, in_rows * nx, (int)a.out_row0,
-                                      (int)(a.out_row0 + out_rows));
+                                      a.dot_out, a.retire, (int)a.in_row0, (int)(a.in_row0 + in_rows), in_rows * nx,
+                                      (int)a.out_row0, (int)(a.out_row0 + out_rows));
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -406,13 +539,14 @@ PairTab<T, 2, M> make_pairs2(const pd_grid *g)
     return t;
 }
 
-template <typename T, int M>
+template <typename T, int M, bool PLANE>
 int run_pair(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
     constexpr int R = rows2d<T, M>();
     constexpr int TY = kGY2 * R;
     const size_t smem = sizeof(T) * 2 * (kTX2 + 2 * M) * (TY + 2 * M);
-    auto kern = k_tbt2d_pair<T, M>;
+    auto kern = k_tbt2d_pair<T, M, PLANE>;
+    if (PLANE && a.dot_partial) return fail(PD_ERR_INVALID, "internal: the box plane takes no fused dot");
     allow_smem(kern, smem);
     const int64_t nx = g->n[0], ny = g->n[1];
     const int64_t in_rows = a.in_rows < 0 ? ny : a.in_rows, out_rows = a.out_rows < 0 ? ny : a.out_rows;
@@ -420,10 +554,11 @@ int run_pair(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
         return fail(PD_ERR_INVALID, "row windows take no fused dot");
     dim3 grid((unsigned)((nx + kTX2 - 1) / kTX2), (unsigned)((out_rows + TY - 1) / TY), (unsigned)a.batch);
     const T *kd = sizeof(T) == 4 ? (const T *)g->d_kd32 : (const T *)g->d_kd64;
+    const T *kt = sizeof(T) == 4 ? (const T *)g->d_kt32 : (const T *)g->d_kt64;
     kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)nx, (int)ny, out_rows * nx, g->d_cons,
-                                      a.project ? 1 : 0, kd, (T)a.scale, make_pairs2<T, M>(g), a.dot_partial,
-                                      a.dot_out, a.retire, (int)a.in_row0, in_rows * nx, (int)a.out_row0,
-                                      (int)(a.out_row0 + out_rows));
+                                      a.project ? 1 : 0, kd, kt, (T)a.scale, make_pairs2<T, M>(g), a.dot_partial,
+                                      a.dot_out, a.retire, (int)a.in_row0, (int)(a.in_row0 + in_rows), in_rows * nx,
+                                      (int)a.out_row0, (int)(a.out_row0 + out_rows));
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }
@@ -433,16 +568,33 @@ int run_t(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 {
     if (a.pair_form) {
         switch (g->M) {
-            case 1: return run_pair<T, 1>(g, a, s);
-            case 2: return run_pair<T, 2>(g, a, s);
-            case 3: return run_pair<T, 3>(g, a, s);
-            case 4: return run_pair<T, 4>(g, a, s);
-            case 5: return run_pair<T, 5>(g, a, s);
-            case 6: return run_pair<T, 6>(g, a, s);
-            case 7: return run_pair<T, 7>(g, a, s);
-            case 8: return run_pair<T, 8>(g, a, s);
+            case 1: return run_pair<T, 1, false>(g, a, s);
+            case 2: return run_pair<T, 2, false>(g, a, s);
+            case 3: return run_pair<T, 3, false>(g, a, s);
+            case 4: return run_pair<T, 4, false>(g, a, s);
+            case 5: return run_pair<T, 5, false>(g, a, s);
+            case 6: return run_pair<T, 6, false>(g, a, s);
+            case 7: return run_pair<T, 7, false>(g, a, s);
+            case 8: return run_pair<T, 8, false>(g, a, s);
         }
         return fail(PD_ERR_INVALID, "horizon M not compiled for 2D");
+    }
+    if constexpr (sizeof(T) == 8) {
+        // FP64 default: the pair form on u minus the box's plane; the difference form
+        // with a fused dot or on request (PD_ACCURATE)
+        if (!a.dot_partial && !a.accurate) {
+            switch (g->M) {
+                case 1: return run_pair<T, 1, true>(g, a, s);
+                case 2: return run_pair<T, 2, true>(g, a, s);
+                case 3: return run_pair<T, 3, true>(g, a, s);
+                case 4: return run_pair<T, 4, true>(g, a, s);
+                case 5: return run_pair<T, 5, true>(g, a, s);
+                case 6: return run_pair<T, 6, true>(g, a, s);
+                case 7: return run_pair<T, 7, true>(g, a, s);
+                case 8: return run_pair<T, 8, true>(g, a, s);
+            }
+            return fail(PD_ERR_INVALID, "horizon M not compiled for 2D");
+        }
     }
     switch (g->M) {
         case 1: return run<T, 1>(g, a, s);

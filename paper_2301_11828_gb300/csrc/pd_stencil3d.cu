@@ -171,11 +171,12 @@ __global__ void __launch_bounds__(kThreads, (DIFF && M <= 3) ? 3 : 2)
 k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
         const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, T scale,
         PairTab<T, 3, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
-        int in_z0, int64_t Nin, int out_z0, int out_zend)
+        int in_z0, int in_zend, int64_t Nin, int out_z0, int out_zend)
 {
-    // Planes are grid planes; the input holds planes [in_z0, ...) with component size
-    // Nin, the output planes [out_z0, out_zend) with component size N (the whole
-    // grid: 0, N, 0, nz).
+    // Planes are grid planes; the input holds planes [in_z0, in_zend) with component
+    // size Nin, the output planes [out_z0, out_zend) with component size N (the whole
+    // grid: 0, nz, N, 0, nz).  Planes of the grid outside the input enter only
+    // outputs that the launch does not write.
     constexpr int R = rows3d<T, M, DIFF>();
     constexpr int TX = kTX3, TY = kTY3, SX = TX + 2 * M, SY = TY + 2 * M, SZ = R + 2 * M;
     constexpr int PL = SX * SY * SZ;
@@ -194,7 +195,7 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
         const int yy = rem / SX, xx = rem - yy * SX;
         const int gx = x0 - M + xx, gy = y0 - M + yy, gz = z0 - M + zz;
         T v0 = T(0), v1 = T(0), v2 = T(0);
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= in_z0 && gz < in_zend) {
             const int64_t p = ((int64_t)gz * ny + gy) * nx + gx;
             v0 = __ldg(ub + p);
             v1 = __ldg(ub + Nin + p);
@@ -378,7 +379,8 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], (int)nz, nzt,
                                       out_planes * plane, g->d_cons, a.project ? 1 : 0, kd, (T)a.scale,
                                       make_pairs3<T, M>(g), a.dot_partial, a.dot_out, a.retire, (int)a.in_row0,
-                                      in_planes * plane, (int)a.out_row0, (int)(a.out_row0 + out_planes));
+                                      (int)(a.in_row0 + in_planes), in_planes * plane, (int)a.out_row0,
+                                      (int)(a.out_row0 + out_planes));
     PD_CUDA(cudaGetLastError());
     return PD_OK;
 }

@@ -103,10 +103,12 @@ void apply(pd_grid *g, int prec, const Choice &c)
 using namespace pd;
 
 // Candidates per precision: the stencil (FP32 2D grids that take the TMA-fed
-// kernel at M <= 4: tiles of 64 x 32 and 64 x 16 outputs) and, without a
-// modulus field, the FFT tiles (FP64 only; see below).  Three warm-up products each, then five rounds
-// of ten products per candidate in turn, each candidate keeping its fastest
-// round (a clock ramp or a neighbour's burst does not decide).
+// kernel at M <= 4: tiles of 64 x 64 (M <= 3), 64 x 32 and 64 x 16 outputs and
+// the column walk where it applies) and, without a modulus field, the FFT tiles
+// (in FP32 chosen only from M = 5; see below).  Three warm-up products each,
+// then five rounds of ten products per candidate in turn, each candidate
+// keeping its fastest round (a clock ramp or a neighbour's burst does not
+// decide).
 extern "C" int pd_autotune(pd_grid *g, uint32_t flags, double *times_ms, void *stream)
 {
     if (!g) return fail(PD_ERR_INVALID, "grid is NULL");

@@ -85,3 +85,51 @@ def test_plane_slabs_3d_reassemble_the_product_bit_for_bit(pd, n, M):
                 pieces.append(out)
             torch.cuda.synchronize()
             assert torch.equal(torch.cat(pieces, dim=2), whole), (str(dt), proj)
+
+
+def test_ragged_band_inside_the_grid(pd):
+    """A band whose row count is not a multiple of the tile height and which
+    ends inside the grid: the kernels stage only the rows the input holds (the
+    rows past it enter no written output).  FP32 bit for bit with the whole-grid
+    product; FP64 bit for bit in the difference form (PD_ACCURATE), and within
+    rounding in the default form, which subtracts a plane per tile fitted over
+    what the tile stages."""
+    n, M = (96, 160), 3
+    nx, ny = n
+    rng = np.random.default_rng(11)
+    g = pd.Grid(2, n, 1.0 / nx, M)
+    row0, rows = 32, 23
+    lo, ext = row0 - M, rows + 2 * M
+    for dt in (torch.float32, torch.float64):
+        U = torch.tensor(rng.uniform(-1, 1, (1, 2, ny, nx)), dtype=dt, device="cuda")
+        for extra in ((0, pd.PD_NO_TMA) if dt == torch.float32 else (0, pd.PD_ACCURATE)):
+            fl = pd.PD_METHOD_STENCIL | extra
+            whole = g.matvec(U, flags=fl)[:, :, row0:row0 + rows]
+            out = torch.empty((1, 2, rows, nx), dtype=dt, device="cuda")
+            pd.pd_matvec_rows(g.handle, 1, row0, rows, U[:, :, lo:lo + ext].contiguous(), lo, ext, out,
+                              fl | (pd.PD_F32 if dt == torch.float32 else pd.PD_F64))
+            torch.cuda.synchronize()
+            if dt == torch.float32 or extra:
+                assert torch.equal(out, whole), (str(dt), extra)
+            else:
+                d = (out - whole).norm() / whole.norm()
+                assert float(d) <= 1e-14
+
+
+def test_ragged_plane_band_3d(pd):
+    """3D: a band of planes that is not a multiple of the tile depth, inside
+    the grid, bit for bit."""
+    n, M = (40, 33, 60), 3
+    nx, ny, nz = n
+    rng = np.random.default_rng(12)
+    g = pd.Grid(3, n, 1.0 / 64, M)
+    z0, planes = 21, 13
+    lo, ext = z0 - M, planes + 2 * M
+    for dt in (torch.float32, torch.float64):
+        U = torch.tensor(rng.uniform(-1, 1, (1, 3, nz, ny, nx)), dtype=dt, device="cuda")
+        whole = g.matvec(U, flags=pd.PD_METHOD_STENCIL)[:, :, z0:z0 + planes]
+        out = torch.empty((1, 3, planes, ny, nx), dtype=dt, device="cuda")
+        pd.pd_matvec_rows(g.handle, 1, z0, planes, U[:, :, lo:lo + ext].contiguous(), lo, ext, out,
+                          pd.PD_METHOD_STENCIL | (pd.PD_F32 if dt == torch.float32 else pd.PD_F64))
+        torch.cuda.synchronize()
+        assert torch.equal(out, whole), str(dt)
