@@ -537,9 +537,12 @@ def _extras(torch, pd, syn, dev):
             U = torch.rand((B, 2, NSIDE, NSIDE), dtype=dt, device=dev) * 2 - 1
             O = torch.empty_like(U)
             ref0 = oracle.stiffness(2, w.n, w.h, w.M, al, U[0].double().cpu().numpy())
+            # FP64 "stencil": the pair form on u minus each tile's plane (the default);
+            # "stencil_difference": the difference form; "stencil_pair": the pair form on u
             for meth, mname in ((pd.PD_METHOD_STENCIL, "stencil"), (pd.PD_METHOD_STENCIL | pd.PD_PAIR_FORM, "stencil_pair"),
+                                (pd.PD_METHOD_STENCIL | pd.PD_ACCURATE, "stencil_difference"),
                                 (pd.PD_METHOD_STENCIL | pd.PD_NO_TMA, "stencil_plain"), (pd.PD_METHOD_FFT, "fft")):
-                if name == "f64" and mname == "stencil_plain":
+                if (name == "f64" and mname == "stencil_plain") or (name == "f32" and mname == "stencil_difference"):
                     continue
                 key = f"M{M}_{name}_{mname}"
                 try:
@@ -555,7 +558,7 @@ def _extras(torch, pd, syn, dev):
         npairs = oracle.offsets(2, M).shape[0] // 2
         gen = npairs - 2 * M
         f64_flops = (gen * 10 + 2 * M * 3 + 8) * w.N
-        for key in (f"M{M}_f64_stencil", f"M{M}_f64_stencil_pair"):
+        for key in (f"M{M}_f64_stencil", f"M{M}_f64_stencil_pair", f"M{M}_f64_stencil_difference"):
             if variants.get(key):
                 vfrac[key] = round(variants[key] * 1e9 / 2 * (f64_flops / w.N) / (peaks["fp64_tflops"] * 1e12), 3)
         # FP32 stencils against the measured FP32 FMA rate with the same algorithmic FLOP count:

@@ -421,42 +421,61 @@ k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64
         for (int r = 0; r < R; ++r) ay[r] = dfma(cyy, cy[r + M + oy] + cy[r + M - oy], ay[r]);
     });
 
-    T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
     const int gx = x0 + tx;
+    T fx[R], fy[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int gy = y0 + ty * R + r;
+        const T upx = cx[r + M], upy = cy[r + M];
+        T kxx = tab.v[3 * NP], kxy = tab.v[3 * NP + 1], kyy = tab.v[3 * NP + 2];
+        const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
+        if ((a0 != M || a1 != M || b0 != M || b1 != M) && gx < nx && gy < out_end) {
+            const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
+            kxx = __ldg(kd + 3 * cls);
+            kxy = __ldg(kd + 3 * cls + 1);
+            kyy = __ldg(kd + 3 * cls + 2);
+        }
+        fx[r] = dfma(kxx, upx, dfma(kxy, upy, -ax[r]));
+        fy[r] = dfma(kxy, upx, dfma(kyy, upy, -ay[r]));
+    }
+    if constexpr (PLANE) {
+        // K L at the nodes near a face, on the tiles that hold some (a block-uniform branch,
+        // so that interior tiles do not execute it under a predicate)
+        if (x0 < M || x0 + TX > nx - M || y0 < M || y0 + TY > ny - M) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int gy = y0 + ty * R + r;
+                const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
+                if ((a0 != M || a1 != M || b0 != M || b1 != M) && gx < nx && gy < out_end) {
+                    const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
+                    const T *t6 = kt + 6 * cls;   // Tx_xx, Tx_xy, Tx_yy, Ty_xx, Ty_xy, Ty_yy
+                    fx[r] -= __ldg(t6) * pg[0] + __ldg(t6 + 3) * pg[1] + __ldg(t6 + 1) * pg[2] + __ldg(t6 + 4) * pg[3];
+                    fy[r] -= __ldg(t6 + 1) * pg[0] + __ldg(t6 + 4) * pg[1] + __ldg(t6 + 2) * pg[2] + __ldg(t6 + 5) * pg[3];
+                }
+            }
+        }
+    }
+
+    T dot = T(0);   // per-thread partial in the kernel's precision; FP64 only across threads
+    const bool scaled = scale != T(1);   // a product by one is exact: skipped
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int gy = y0 + ty * R + r;
         if (gx < nx && gy < out_end) {
             const int64_t p = (int64_t)gy * nx + gx;
-            const T upx = cx[r + M], upy = cy[r + M];
-            T kxx = tab.v[3 * NP], kxy = tab.v[3 * NP + 1], kyy = tab.v[3 * NP + 2];
-            const int a0 = min(gx, M), a1 = min(nx - 1 - gx, M), b0 = min(gy, M), b1 = min(ny - 1 - gy, M);
-            const bool edge = a0 != M || a1 != M || b0 != M || b1 != M;
-            const int cls = ((a0 * (M + 1) + a1) * (M + 1) + b0) * (M + 1) + b1;
-            if (edge) {
-                kxx = __ldg(kd + 3 * cls);
-                kxy = __ldg(kd + 3 * cls + 1);
-                kyy = __ldg(kd + 3 * cls + 2);
-            }
-            T fx = dfma(kxx, upx, dfma(kxy, upy, -ax[r]));
-            T fy = dfma(kxy, upx, dfma(kyy, upy, -ay[r]));
-            if constexpr (PLANE) {
-                if (edge) {   // K L at a node near a face
-                    const T *t6 = kt + 6 * cls;   // Tx_xx, Tx_xy, Tx_yy, Ty_xx, Ty_xy, Ty_yy
-                    fx -= __ldg(t6) * pg[0] + __ldg(t6 + 3) * pg[1] + __ldg(t6 + 1) * pg[2] + __ldg(t6 + 4) * pg[3];
-                    fy -= __ldg(t6 + 1) * pg[0] + __ldg(t6 + 4) * pg[1] + __ldg(t6 + 2) * pg[2] + __ldg(t6 + 5) * pg[3];
-                }
-            }
+            T ox = fx[r], oy = fy[r];
             if (project) {
                 const uint8_t m = __ldg(cons + p);
-                if (m & 1) fx = T(0);
-                if (m & 2) fy = T(0);
+                if (m & 1) ox = T(0);
+                if (m & 2) oy = T(0);
             }
-            fx *= scale;
-            fy *= scale;
-            ob[p] = fx;
-            ob[N + p] = fy;
-            dot = dfma(upx, fx, dfma(upy, fy, dot));
+            if (scaled) {
+                ox *= scale;
+                oy *= scale;
+            }
+            ob[p] = ox;
+            ob[N + p] = oy;
+            dot = dfma(cx[r + M], ox, dfma(cy[r + M], oy, dot));
         }
     }
     if (dot_partial)
