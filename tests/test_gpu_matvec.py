@@ -534,3 +534,24 @@ def test_f64_plane_pair_form_matches_difference_form(pd, n, M):
     assert rel_l2(a.cpu().numpy(), d.cpu().numpy()) <= 1e-14
     ref = _oracle_K(2, n, 1.0 / 64, M, U[2].cpu().numpy())
     assert rel_l2(a[2].cpu().numpy(), ref) <= 1e-13
+
+
+@pytest.mark.parametrize("method", ["stencil", "fft"])
+def test_modulus_change_rebuilds_plane_tables(pd, method):
+    """The first-moment tables that give K of a tile's plane at the faces
+    (FP64 stencil, FP32 FFT tiles) scale with the modulus: after
+    pd_set_material changes E, products of a field with a large gradient
+    still match the oracle at the new modulus."""
+    n, h = (200, 150), 1.0 / 200
+    M = 3 if method == "stencil" else 6   # the FP32 FFT tiles serve the larger horizons
+    g = pd.Grid(2, n, h, M)
+    u_np = _smooth_field(n, True) + np.stack([_linear_part(n, 40.0, -25.0, 5.0), _linear_part(n, -30.0, 60.0, -3.0)])
+    meth = pd.PD_METHOD_STENCIL if method == "stencil" else pd.PD_METHOD_FFT
+    dt = torch.float64 if method == "stencil" else torch.float32
+    tol = 1e-12 if method == "stencil" else 2e-5
+    for E in (1.0, 3.5):
+        g.set_material(E=E)
+        ut = torch.tensor(u_np, dtype=dt, device="cuda")
+        out = g.matvec(ut, flags=meth).double().cpu().numpy()
+        ref = _oracle_K(2, n, h, M, ut.double().cpu().numpy(), E=E)
+        assert rel_l2(out, ref) <= tol, (E, rel_l2(out, ref))
