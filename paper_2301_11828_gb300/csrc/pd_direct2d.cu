@@ -5,19 +5,35 @@
 // set, else w_pq = 1 with the coefficients at the grid's modulus.  Used by the
 // dynamic crack loop and by every operator application with a modulus field.
 //
-// The shared-memory box carries a third plane holding E (or 1) inside the grid
-// and 0 outside, so "q outside the grid" is "E_q == 0" (moduli are validated
-// positive).  Each thread owns R consecutive y outputs of one column and reads
-// their bond-mask words once.
+// The shared-memory box carries a third plane holding E/2 (or 1/2) inside the
+// grid and 0 outside, so "q outside the grid" is "E_q == 0" (moduli are
+// validated positive) and w_pq is one addition.  Each thread owns R consecutive
+// y outputs of one column and reads their bond-mask words once.
+//
+// A bond's block is rank one, c(o) = kappa(o) o o^T (Eq. frb:e1), so an
+// offset with both components nonzero applies it as kappa o (o . d) with
+// d = u_p - u_q: one dot product with the integer offset and two FMAs, instead
+// of the four products of the 2 x 2 block.
 #include "pd_stencil.cuh"
 
 namespace pd {
+
+// Per offset in canonical order: (kappa ox, kappa oy) for offsets with both
+// components nonzero, (c_xx, 0) for (ox, 0) and (0, c_yy) for (0, oy).
+template <typename T, int M>
+struct BondTab2 {
+    static constexpr int kN = count_offsets(2, M);
+    T v[kN * 2];
+};
+
+__device__ __forceinline__ bool nonzero_bits(double v) { return __double_as_longlong(v) != 0; }
+__device__ __forceinline__ bool nonzero_bits(float v) { return __float_as_int(v) != 0; }
 
 template <typename T, int M>
 __global__ void __launch_bounds__(kThreads)
 k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
            const uint8_t *__restrict__ cons, int project, const double *__restrict__ Ef,
-           const uint32_t *__restrict__ mask, T scale, CanonTab2<T, M> tab, double *dot_partial, double *dot_out,
+           const uint32_t *__restrict__ mask, T scale, BondTab2<T, M> tab, double *dot_partial, double *dot_out,
            unsigned int *retire)
 {
     constexpr int R = rows2d_direct<T, M>();
@@ -42,7 +58,7 @@ k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
             const int64_t p = (int64_t)gy * nx + gx;
             vx = __ldg(ub + p);
             vy = __ldg(ub + N + p);
-            ve = Ef ? (T)__ldg(Ef + p) : T(1);
+            ve = Ef ? T(0.5) * (T)__ldg(Ef + p) : T(0.5);   // halved: exact
             if (project) {
                 const uint8_t m = __ldg(cons + p);
                 if (m & 1) vx = T(0);
@@ -87,22 +103,23 @@ k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
             constexpr int oy = decltype(OY)::value;
             if constexpr (ox != 0 || oy != 0) {
                 constexpr int k = canon_index(2, M, ox, oy, 0);
-                const T cxx = tab.v[3 * k], cxy = tab.v[3 * k + 1], cyy = tab.v[3 * k + 2];
+                const T ka = tab.v[2 * k], kb = tab.v[2 * k + 1];
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const T eq = we[r + M + oy];
-                    const bool on = ((mk[r][k >> 5] >> (k & 31)) & 1u) && (eq != T(0));
-                    const T wgt = on ? T(0.5) * (ep[r] + eq) : T(0);
+                    const bool on = ((mk[r][k >> 5] >> (k & 31)) & 1u) && nonzero_bits(eq);
+                    const T wgt = on ? ep[r] + eq : T(0);   // (E_p + E_q)/2 from the halved planes
                     // c_xy and c_yy vanish for (ox, 0), c_xx and c_xy for (0, oy)
                     if constexpr (oy == 0) {
-                        ax[r] = dfma(wgt, cxx * (upx[r] - wx[r + M]), ax[r]);
+                        ax[r] = dfma(wgt, ka * (upx[r] - wx[r + M]), ax[r]);
                     } else if constexpr (ox == 0) {
-                        ay[r] = dfma(wgt, cyy * (upy[r] - wy[r + M + oy]), ay[r]);
+                        ay[r] = dfma(wgt, kb * (upy[r] - wy[r + M + oy]), ay[r]);
                     } else {
                         const T dx = upx[r] - wx[r + M + oy];
                         const T dy = upy[r] - wy[r + M + oy];
-                        ax[r] = dfma(wgt, dfma(cxx, dx, cxy * dy), ax[r]);
-                        ay[r] = dfma(wgt, dfma(cxy, dx, cyy * dy), ay[r]);
+                        const T t = wgt * dfma(T(oy), dy, T(ox) * dx);   // w_pq (o . d)
+                        ax[r] = dfma(t, ka, ax[r]);
+                        ay[r] = dfma(t, kb, ay[r]);
                     }
                 }
             }
@@ -135,13 +152,21 @@ k_direct2d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t
 namespace {
 
 template <typename T, int M>
-CanonTab2<T, M> make_canon2(const pd_grid *g)
+BondTab2<T, M> make_bond2(const pd_grid *g)
 {
-    CanonTab2<T, M> t{};
+    BondTab2<T, M> t{};
     double c[6];
     for (int k = 0; k < g->nnb; ++k) {
-        coef_of(g, g->off[3 * k], g->off[3 * k + 1], 0, g->has_E, c);
-        for (int i = 0; i < 3; ++i) t.v[3 * k + i] = (T)c[i];
+        const int ox = g->off[3 * k], oy = g->off[3 * k + 1];
+        coef_of(g, ox, oy, 0, g->has_E, c);
+        if (ox != 0 && oy != 0) {   // c_xx = kappa ox^2: kappa ox = c_xx / ox, kappa oy = kappa ox * oy / ox
+            const double kappa = c[0] / ((double)ox * ox);
+            t.v[2 * k] = (T)(kappa * ox);
+            t.v[2 * k + 1] = (T)(kappa * oy);
+        } else {
+            t.v[2 * k] = (T)c[0];
+            t.v[2 * k + 1] = (T)c[2];
+        }
     }
     return t;
 }
@@ -157,7 +182,7 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     dim3 grid((unsigned)((g->n[0] + kTX2 - 1) / kTX2), (unsigned)((g->n[1] + TY - 1) / TY), (unsigned)a.batch);
     kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], g->N, g->d_cons,
                                       a.project ? 1 : 0, g->has_E ? g->d_E : nullptr,
-                                      a.use_mu ? g->d_mask : nullptr, (T)a.scale, make_canon2<T, M>(g),
+                                      a.use_mu ? g->d_mask : nullptr, (T)a.scale, make_bond2<T, M>(g),
                                       a.dot_partial, a.dot_out, a.retire);
     PD_CUDA(cudaGetLastError());
     return PD_OK;

@@ -154,6 +154,8 @@ k_fft3d_tile(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int n
         }
     }
 
+    // fully unrolled: the window's loads are all in flight before the first store
+#pragma unroll
     for (int t = threadIdx.x; t < P3 * P3 * P3; t += kT3) {
         const int x = t & 15, y = (t >> 4) & 15, z = t >> 8;
         const int gx = x0 + x, gy = y0 + y, gz = z0 + z;
