@@ -27,6 +27,8 @@
 
 namespace pd {
 
+constexpr int gcd_c(int a, int b) { return b == 0 ? (a < 0 ? -a : a) : gcd_c(b, a % b); }
+
 // Pair blocks (xx, xy, yy) in pair_index2 order, then per k = 1..M the summed
 // vertical block Cbar(k) = sum of c(o) over the pairs with |oy| = k (xx, yy).
 template <typename T, int M>
@@ -307,7 +309,7 @@ __device__ __forceinline__ void box_plane(F fetch, int ca, int cb, int ra, int r
 // the FP64 CG and ADR iterations.  On u minus the box's plane (PLANE, FP64, no
 // fused dot; box_plane) it is the default FP64 product.
 template <typename T, int M, bool PLANE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (PLANE && M <= 4) ? 3 : 1)
 k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64_t N,
              const uint8_t *__restrict__ cons, int project, const T *__restrict__ kd, const T *__restrict__ kt,
              T scale, PairTab<T, 2, M> tab, double *dot_partial, double *dot_out, unsigned int *retire,
@@ -393,16 +395,23 @@ k_tbt2d_pair(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int64
         static_for<-My, My + 1>([&](auto OY) {
             constexpr int oy = decltype(OY)::value;
             constexpr int pi = pair_index2(M, ox, oy);
-            const T cxx = tab.v[3 * pi], cxy = tab.v[3 * pi + 1], cyy = tab.v[3 * pi + 2];
+            // rank-one block c(o) = kappa o o^T with o = g (ax_, ay_), g = gcd: the pair adds
+            // (kappa g o) (ax_ sx + ay_ sy); the table holds kappa g o (the axis pair: c_xx)
+            constexpr int gd = gcd_c(ox, oy), ax_ = ox / gd, ay_ = oy / gd;
+            const T ka = tab.v[3 * pi], kb = tab.v[3 * pi + 1];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const T sx = px[r + M + oy] + mx[r + M - oy];
                 if constexpr (oy == 0) {
-                    ax[r] = dfma(cxx, sx, ax[r]);   // axis pair: c_xy = c_yy = 0 exactly
+                    ax[r] = dfma(ka, sx, ax[r]);   // axis pair: c_xy = c_yy = 0 exactly
                 } else {
                     const T sy = py[r + M + oy] + my[r + M - oy];
-                    ax[r] = dfma(cxx, sx, dfma(cxy, sy, ax[r]));
-                    ay[r] = dfma(cxy, sx, dfma(cyy, sy, ay[r]));
+                    T d;
+                    if constexpr (ax_ == 1) d = dfma(T(ay_), sy, sx);
+                    else if constexpr (ay_ == 1 || ay_ == -1) d = dfma(T(ax_), sx, T(ay_) * sy);
+                    else d = dfma(T(ay_), sy, T(ax_) * sx);
+                    ax[r] = dfma(ka, d, ax[r]);
+                    ay[r] = dfma(kb, d, ay[r]);
                 }
             }
         });
@@ -535,6 +544,10 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
 }
 
 
+// The pair form's table: per pair (ox > 0, or ox = 0 < oy) kappa g (ox, oy) for pairs with
+// both components nonzero (c(o) = kappa o o^T, g = gcd(ox, |oy|); k_tbt2d_pair applies it as
+// kappa g o (o / g . s)), c_xx for (ox, 0) and c_yy (third slot) for (0, oy); then the
+// interior diagonal Kd (sum of all c).
 template <typename T, int M>
 PairTab<T, 2, M> make_pairs2(const pd_grid *g)
 {
@@ -546,6 +559,12 @@ PairTab<T, 2, M> make_pairs2(const pd_grid *g)
         for (int i = 0; i < 3; ++i) {
             t.v[3 * pi + i] = (T)c[i];
             tot[i] += 2 * c[i];
+        }
+        if (ox != 0 && oy != 0) {
+            const double kg = c[0] / ((double)ox * ox) * gcd_c(ox, oy);   // kappa g
+            t.v[3 * pi] = (T)(kg * ox);
+            t.v[3 * pi + 1] = (T)(kg * oy);
+            t.v[3 * pi + 2] = T(0);
         }
     };
     for (int ox = 1; ox <= M; ++ox) {
