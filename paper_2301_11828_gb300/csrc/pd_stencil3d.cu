@@ -44,6 +44,44 @@ __device__ __forceinline__ void pair3(T (&acc)[3][R], int r, bool nx_, bool ny_,
     }
 }
 
+// Rank-one application of a pair's block (FP64 pair form): c(o) = kappa o o^T, so for an
+// offset with two or three nonzero components acc += (kappa g o) d with d = (o / g) . s
+// (g the gcd of the components): the reduced dot product takes one operation per nonzero
+// component after the first (additions for components +-1), then one FMA per nonzero
+// component, instead of the block's products.  k[] holds kappa g o.
+constexpr int gcd3_c(int a, int b) { return b == 0 ? (a < 0 ? -a : a) : gcd3_c(b, a % b); }
+
+template <int A, typename T> __device__ __forceinline__ T rk_first(T s)
+{
+    if constexpr (A == 1) return s;
+    else if constexpr (A == -1) return -s;
+    else return T(A) * s;
+}
+template <int A, typename T> __device__ __forceinline__ T rk_add(T s, T d)
+{
+    if constexpr (A == 1) return d + s;
+    else if constexpr (A == -1) return d - s;
+    else return dfma(T(A), s, d);
+}
+
+template <int OX, int OY, int OZ, typename T, int R>
+__device__ __forceinline__ void pair3_rank1(T (&acc)[3][R], int r, const T *k, T s0, T s1, T s2)
+{
+    constexpr int g = gcd3_c(gcd3_c(OX, OY), OZ), ax = OX / g, ay = OY / g, az = OZ / g;
+    T d;
+    if constexpr (ax != 0) {
+        d = rk_first<ax>(s0);
+        if constexpr (ay != 0) d = rk_add<ay>(s1, d);
+        if constexpr (az != 0) d = rk_add<az>(s2, d);
+    } else {
+        d = rk_first<ay>(s1);
+        d = rk_add<az>(s2, d);
+    }
+    if constexpr (ax != 0) acc[0][r] = dfma(k[0], d, acc[0][r]);
+    if constexpr (ay != 0) acc[1][r] = dfma(k[1], d, acc[1][r]);
+    if constexpr (az != 0) acc[2][r] = dfma(k[2], d, acc[2][r]);
+}
+
 // Accurate (difference) form of the bond sum for one thread's z-column of R
 // outputs.  For a column pair (ox, oy) let H+(i) = u(x+ox, y+oy, i) - u(x, y, i)
 // and H-(i) = u(x-ox, y-oy, i) - u(x, y, i) (plane i of the window), and in the
@@ -166,6 +204,10 @@ __device__ __forceinline__ void diff3_column(const T *base, const PairTab<T, 3, 
     }
 }
 
+// the pair form's table carries kappa g o for offsets with two or three nonzero components
+// (pair3_rank1) in FP64; FP32 and the difference form keep the block entries
+template <typename T, bool DIFF> constexpr bool kRank1() { return sizeof(T) == 8 && !DIFF; }
+
 template <typename T, int M, bool DIFF>
 __global__ void __launch_bounds__(kThreads, (DIFF && M <= 3) ? 3 : 2)
 k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, int nzt, int64_t N,
@@ -258,16 +300,25 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
                             wp[c][i] = base[c * PL + i * SX * SY + oy * SX + ox];
                             wm[c][i] = base[c * PL + i * SX * SY - oy * SX - ox];
                         }
-#pragma unroll
-                    for (int oz = -Mz; oz <= Mz; ++oz) {
+                    static_for<-Mz, Mz + 1>([&](auto OZ) {
+                        constexpr int oz = decltype(OZ)::value;
                         const T *cf = tab.v + 6 * (pbase + oz);
-                        const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+                        constexpr int nzc = (ox != 0) + (oy != 0) + (oz != 0);
+                        if constexpr (kRank1<T, DIFF>() && nzc >= 2) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r)
-                            pair3(acc, r, ox != 0, oy != 0, oz != 0, cxx, cxy, cxz, cyy, cyz, czz,
-                                  wp[0][r + M + oz] + wm[0][r + M - oz], wp[1][r + M + oz] + wm[1][r + M - oz],
-                                  wp[2][r + M + oz] + wm[2][r + M - oz]);
-                    }
+                            for (int r = 0; r < R; ++r)
+                                pair3_rank1<ox, oy, oz>(acc, r, cf, wp[0][r + M + oz] + wm[0][r + M - oz],
+                                                        wp[1][r + M + oz] + wm[1][r + M - oz],
+                                                        wp[2][r + M + oz] + wm[2][r + M - oz]);
+                        } else {
+                            const T cxx = cf[0], cxy = cf[1], cxz = cf[2], cyy = cf[3], cyz = cf[4], czz = cf[5];
+#pragma unroll
+                            for (int r = 0; r < R; ++r)
+                                pair3(acc, r, ox != 0, oy != 0, oz != 0, cxx, cxy, cxz, cyy, cyz, czz,
+                                      wp[0][r + M + oz] + wm[0][r + M - oz], wp[1][r + M + oz] + wm[1][r + M - oz],
+                                      wp[2][r + M + oz] + wm[2][r + M - oz]);
+                        }
+                    });
                 }
             });
         });
@@ -334,7 +385,7 @@ k_tbt3d(const T *__restrict__ u, T *__restrict__ out, int nx, int ny, int nz, in
 namespace {
 
 template <typename T, int M>
-PairTab<T, 3, M> make_pairs3(const pd_grid *g)
+PairTab<T, 3, M> make_pairs3(const pd_grid *g, bool rank1)
 {
     PairTab<T, 3, M> t{};
     double c[6], tot[6] = {0, 0, 0, 0, 0, 0};
@@ -344,6 +395,15 @@ PairTab<T, 3, M> make_pairs3(const pd_grid *g)
         for (int i = 0; i < 6; ++i) {
             t.v[6 * pi + i] = (T)c[i];
             tot[i] += 2 * c[i];
+        }
+        if (rank1 && (ox != 0) + (oy != 0) + (oz != 0) >= 2) {
+            // c_aa = kappa o_a^2 (entries xx, yy, zz at 0, 3, 5): kappa from a nonzero component
+            const int o[3] = {ox, oy, oz};
+            const int a = ox != 0 ? 0 : 1;
+            const double kappa = c[a == 0 ? 0 : 3] / ((double)o[a] * o[a]);
+            const double kg = kappa * gcd3_c(gcd3_c(ox, oy), oz);
+            for (int i = 0; i < 3; ++i) t.v[6 * pi + i] = (T)(kg * o[i]);
+            for (int i = 3; i < 6; ++i) t.v[6 * pi + i] = T(0);
         }
     };
     for (int oy = M; oy >= 0; --oy) {
@@ -378,7 +438,7 @@ int run(pd_grid *g, const MatvecArgs &a, cudaStream_t s)
     const T *kd = sizeof(T) == 4 ? (const T *)g->d_kd32 : (const T *)g->d_kd64;
     kern<<<grid, kThreads, smem, s>>>((const T *)a.u, (T *)a.out, (int)g->n[0], (int)g->n[1], (int)nz, nzt,
                                       out_planes * plane, g->d_cons, a.project ? 1 : 0, kd, (T)a.scale,
-                                      make_pairs3<T, M>(g), a.dot_partial, a.dot_out, a.retire, (int)a.in_row0,
+                                      make_pairs3<T, M>(g, kRank1<T, DIFF>()), a.dot_partial, a.dot_out, a.retire, (int)a.in_row0,
                                       (int)(a.in_row0 + in_planes), in_planes * plane, (int)a.out_row0,
                                       (int)(a.out_row0 + out_planes));
     PD_CUDA(cudaGetLastError());
