@@ -165,13 +165,21 @@ int pd_set_material(pd_grid *g, double E, double rho, double thickness, double s
 int pd_set_surface_correction(pd_grid *g, int mode);
 
 /* out = K u = -A u (or P K P u with PD_PROJECT), u and out DEVICE [dim][N] of
- * the dtype in flags; u and out must not overlap.  Broken bonds are honoured
- * unless PD_IGNORE_BROKEN.  Errors: PD_ERR_INVALID (dtype flag missing, FFT
- * with a modulus field). */
+ * the dtype in flags; u and out must not overlap.  A = A^ + D^e + D^f is the
+ * bond sum of Eq. mat:f1 split as in Sec. 3 (2D) and Sec. 4 (3D): the Toeplitz
+ * part A^ by the direct stencil or by per-tile FFTs with the block symbol
+ * (Algorithms 3 and 4; PD_METHOD_* picks, AUTO the measured faster one), the
+ * edge term D^e (Eq. tea:sc) and the broken-bond term D^f (Eq. df).  The
+ * stencils keep the rounding relative to |K u|: FP32 sums differences of
+ * nearby values, FP64 2D sums pairs of u minus each tile's plane (see
+ * PD_ACCURATE, PD_PAIR_FORM).  Broken bonds are honoured unless
+ * PD_IGNORE_BROKEN.  Errors: PD_ERR_INVALID (dtype flag missing or both, u
+ * aliasing out, two methods, FFT with a modulus field). */
 int pd_matvec(pd_grid *g, const void *u, void *out, uint32_t flags, void *stream);
 
 /* The same for `batch` independent vectors stored back to back:
- * u[b * dim * N + c * N + p].  One launch serves the whole batch. */
+ * u[b * dim * N + c * N + p].  One launch serves the whole batch; batch in
+ * [1, 65535] (PD_ERR_INVALID otherwise, nothing written). */
 int pd_matvec_batch(pd_grid *g, int64_t batch, const void *u, void *out, uint32_t flags,
                     void *stream);
 
