@@ -203,11 +203,14 @@ int pd_matvec_batch_host(pd_grid *g, int64_t batch, const void *u_host, void *ou
  * ||P(b - K u)|| <= rtol ||P b|| in FP64.  stats may be NULL.  Returns
  * PD_ERR_NOT_CONVERGED after max_iter inner iterations with u holding the last
  * iterate and stats filled.  On a 2D grid with a constant modulus, no broken
- * bonds and a row length that is a multiple of 4, the FP32 inner loop of
- * PD_CG_MIXED runs as one persistent cooperative kernel (all CTAs resident,
- * grid barriers with bounded waits; PD_ERR_TIMEOUT if a wait gives up);
- * elsewhere, or with PD_CG_GRAPH, as chunks of 32 iterations replayed from a
- * CUDA graph.  Both give the same iterates up to FP32 rounding order. */
+ * bonds, no surface correction and a row length that is a multiple of 4, the
+ * FP32 inner loop of PD_CG_MIXED runs as one persistent cooperative kernel
+ * when all its 64 x 32 tiles fit one wave of resident CTAs (grid barriers with
+ * bounded waits; PD_ERR_TIMEOUT if a wait gives up); on larger such grids, or
+ * with PD_CG_GRAPH, as chunks of 32 iterations replayed from a CUDA graph, two
+ * launches per iteration (the direction formed inside the operator kernel);
+ * elsewhere as graph-replayed chunks of the separate kernels.  All give the
+ * same iterates up to FP32 rounding order. */
 int pd_cg_solve(pd_grid *g, const double *b, double *u, double rtol, int max_iter,
                 uint32_t mode, pd_cg_stats *stats, void *stream);
 
